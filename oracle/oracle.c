@@ -1,0 +1,926 @@
+/*
+ * FP64 CPU oracle of the Hermite-spline MPPI hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg load this file's library. The product (the CUDA library) shares no
+ * code with it and never calls it.
+ *
+ * Plain, slow, obviously correct: every quantity in double precision, 6x6 spatial
+ * matrices written out densely, no blocking or fusion beyond what the method states.
+ * Sections follow the paper ("Reference-Free Sampling-Based Model Predictive
+ * Control", arXiv 2511.19204):
+ *
+ *   noise      Sec. III-B Eq. (overall-noise-kernel) as a per-knot std-dev table and
+ *              Alg. 1 sampling step: theta_n = theta + sigma_k * scale * eps, n >= 1;
+ *              sample 0 is the unperturbed nominal. eps from Philox4x32-10 (Salmon et
+ *              al., SC'11) and the Box-Muller transform (Box & Muller 1958).
+ *   clamp      Sec. III-A Eq. (vel-clamp).
+ *   spline     Sec. III-A Eq. (hermite_segment) and the Hermite basis; the velocity
+ *              setpoint is the analytic time derivative of the position spline.
+ *   PD         Sec. III-C Eq. (pd-controller), torques clipped to actuator limits.
+ *   dynamics   floating-base articulated-body algorithm (Featherstone, Rigid Body
+ *              Dynamics Algorithms, 2008, ch. 7 and 9) with soft spring-damper ground
+ *              contact and smooth Coulomb friction, semi-implicit Euler; these stand in
+ *              for the paper's simulator (Sec. III-C, Sec. IV-A).
+ *              CRBA + RNEA (ibid. ch. 5-6) are here only as an independent check.
+ *   cost       Sec. IV-A cost sum S = sum_{h<H} c(x_h, u_h) (+ zero terminal cost) with
+ *              the quadratic running cost of the synthetic workloads.
+ *   weights    Sec. III-C Eq. (omega-weights) and the min-max normalised
+ *              Eq. (softmax_minmax), evaluated as a log-sum-exp.
+ *   average    Sec. III-C Eq. (update-nominal) on the knots.
+ *   solve      Alg. 1 iterations with best-trajectory tracking (Sec. III-D).
+ *
+ * Parity of the whole solve against the paper is unpinned (the paper's simulator and
+ * robots are not available); each part above is pinned by the tests separately.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXB 64
+#define ORC_MAXNV (6 + ORC_MAXB)
+
+typedef struct {
+    int32_t nb, nc, fixed_base, cost_body;
+    const int32_t* parent;     /* [nb] */
+    const double* axis;        /* [nb][3] */
+    const double* jpos;        /* [nb][3] */
+    const double* mass;        /* [nb] */
+    const double* com;         /* [nb][3] */
+    const double* inertia;     /* [nb][6] Ixx Iyy Izz Ixy Ixz Iyz about the com */
+    const double* armature;    /* [nb] */
+    const double* q_min;       /* [nb-1] */
+    const double* q_max;       /* [nb-1] */
+    const double* kp;          /* [nb-1] */
+    const double* kd;          /* [nb-1] */
+    const double* tau_max;     /* [nb-1] */
+    const int32_t* contact_body; /* [nc] */
+    const double* contact_pos;   /* [nc][3] */
+    double contact_k, contact_c, mu, eps_f, gravity;
+    double z_des, vx_des, w_z, w_vx, w_tilt, w_tau;
+} orc_model;
+
+/* ------------------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11).           */
+/* ------------------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Box-Muller on two 32-bit words: u1 in (0,1], u2 in [0,1). */
+static void box_muller(uint32_t wa, uint32_t wb, double* ea, double* eb) {
+    const double two_m24 = 1.0 / 16777216.0;
+    double u1 = ((double)(wa >> 8) + 1.0) * two_m24;
+    double u2 = (double)(wb >> 8) * two_m24;
+    double r = sqrt(-2.0 * log(u1));
+    double ang = 2.0 * M_PI * u2;
+    *ea = r * cos(ang);
+    *eb = r * sin(ang);
+}
+
+/* Standard normal eps for one element e of sample n (n >= 1):
+ * counter = (e/4, n, iteration counter, instance), key = (seed lo, seed hi);
+ * element pairs (2m, 2m+1) share one Box-Muller draw from words (e%4 & ~1, +1). */
+double orc_normal(uint64_t seed, uint32_t iter_ctr, uint32_t inst, uint32_t n, uint32_t e) {
+    uint32_t ctr[4] = {e / 4u, n, iter_ctr, inst};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox(ctr, key, w);
+    uint32_t j = (e % 4u) & ~1u;
+    double ea, eb;
+    box_muller(w[j], w[j + 1], &ea, &eb);
+    return (e & 1u) ? eb : ea;
+}
+
+/* Knot spacing of nk uniform knots over H steps of dt, both endpoints included. */
+static double knot_dt(int nk, int H, double dt) { return (double)H * dt / (double)(nk - 1); }
+
+/* Sec. III-A Eq. (vel-clamp): clip theta^q into the limits, then bound |theta^v| by the
+ * distance to the nearest limit over half a knot interval. Only joints with a finite
+ * limit are clamped. knots: [nk][2][nu]. */
+void orc_clamp(int nu, int nk, double dtk, const double* qmin, const double* qmax, double* kn) {
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nu; ++j) {
+            double lo = qmin[j], hi = qmax[j];
+            if (!isfinite(lo) && !isfinite(hi)) continue;
+            double* q = &kn[(k * 2 + 0) * nu + j];
+            double* v = &kn[(k * 2 + 1) * nu + j];
+            if (*q < lo) *q = lo;
+            if (*q > hi) *q = hi;
+            double room = fmin(hi - *q, *q - lo);
+            double vmax = room / (dtk / 2.0);
+            if (*v > vmax) *v = vmax;
+            if (*v < -vmax) *v = -vmax;
+        }
+}
+
+/* Alg. 1 sampling: theta_{n,k} ~ N(theta_k, sigma_k * scale) for n in [1, N), sample 0
+ * is the nominal itself; then the clamp (when the model has finite limits).
+ * nominal [E], sigma_row [nk], out [N][E], E = nk*2*nu.
+ * scale_v <= 0 selects the default 1/knot-spacing. */
+void orc_sample_knots(int nu, int nk, int N, int H, double dt, const double* nominal,
+                      const double* sigma_row, double scale_q, double scale_v, uint64_t seed,
+                      uint32_t iter_ctr, uint32_t inst, const double* qmin, const double* qmax,
+                      double* out) {
+    const int E = nk * 2 * nu;
+    const double dtk = knot_dt(nk, H, dt);
+    if (scale_v <= 0.0) scale_v = 1.0 / dtk;
+    for (int n = 0; n < N; ++n) {
+        double* kn = out + (size_t)n * E;
+        for (int e = 0; e < E; ++e) {
+            int k = e / (2 * nu);
+            int p = (e / nu) % 2;
+            double eps = (n == 0) ? 0.0 : orc_normal(seed, iter_ctr, inst, (uint32_t)n, (uint32_t)e);
+            kn[e] = nominal[e] + sigma_row[k] * (p == 0 ? scale_q : scale_v) * eps;
+        }
+        if (qmin && qmax) orc_clamp(nu, nk, dtk, qmin, qmax, kn);
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Cubic Hermite spline (Sec. III-A Eq. hermite_segment).                               */
+/* ------------------------------------------------------------------------------------ */
+/* Segment and local time for step h: r = h*(nk-1); k = floor(r/H) (<= nk-2);
+ * s = (r - k*H)/H = (t_h - t_k)/knot spacing, t_h = h*dt. */
+void orc_segment(int h, int H, int nk, int* k_out, double* s_out) {
+    long r = (long)h * (long)(nk - 1);
+    long k = r / H;
+    if (k > nk - 2) k = nk - 2;
+    *k_out = (int)k;
+    *s_out = (double)(r - k * (long)H) / (double)H;
+}
+
+/* q(s) and dq/dt on one segment with knot spacing dtk. */
+void orc_hermite(double s, double dtk, double q0, double v0, double q1, double v1,
+                 double* q, double* qdot) {
+    double s2 = s * s, s3 = s2 * s;
+    double h00 = 2 * s3 - 3 * s2 + 1, h10 = s3 - 2 * s2 + s;
+    double h01 = -2 * s3 + 3 * s2, h11 = s3 - s2;
+    double d00 = 6 * s2 - 6 * s, d10 = 3 * s2 - 4 * s + 1;
+    double d01 = -6 * s2 + 6 * s, d11 = 3 * s2 - 2 * s;
+    *q = h00 * q0 + h10 * dtk * v0 + h01 * q1 + h11 * dtk * v1;
+    *qdot = (d00 * q0 + d01 * q1) / dtk + d10 * v0 + d11 * v1;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Small dense linear algebra                                                            */
+/* ------------------------------------------------------------------------------------ */
+typedef double m3[3][3];
+typedef double m6[6][6];
+
+static void m3_mul(const m3 a, const m3 b, m3 c) {
+    m3 t;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            t[i][j] = 0;
+            for (int k = 0; k < 3; ++k) t[i][j] += a[i][k] * b[k][j];
+        }
+    memcpy(c, t, sizeof(m3));
+}
+static void m3_vec(const m3 a, const double* x, double* y) {
+    double t[3];
+    for (int i = 0; i < 3; ++i) t[i] = a[i][0] * x[0] + a[i][1] * x[1] + a[i][2] * x[2];
+    memcpy(y, t, sizeof t);
+}
+static void m3_tvec(const m3 a, const double* x, double* y) {
+    double t[3];
+    for (int i = 0; i < 3; ++i) t[i] = a[0][i] * x[0] + a[1][i] * x[1] + a[2][i] * x[2];
+    memcpy(y, t, sizeof t);
+}
+static void cross3(const double* a, const double* b, double* c) {
+    double t[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    memcpy(c, t, sizeof t);
+}
+static void skew(const double* a, m3 s) {
+    s[0][0] = 0; s[0][1] = -a[2]; s[0][2] = a[1];
+    s[1][0] = a[2]; s[1][1] = 0; s[1][2] = -a[0];
+    s[2][0] = -a[1]; s[2][1] = a[0]; s[2][2] = 0;
+}
+/* Rodrigues: rotation about unit axis a by angle t (child -> parent coordinates). */
+static void axis_angle(const double* a, double t, m3 R) {
+    m3 K, K2;
+    skew(a, K);
+    m3_mul(K, K, K2);
+    double s = sin(t), c = cos(t);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = (i == j ? 1.0 : 0.0) + s * K[i][j] + (1 - c) * K2[i][j];
+}
+static void quat_to_R(const double* q, m3 R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z); R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
+}
+static void m6_zero(m6 a) { memset(a, 0, sizeof(m6)); }
+static void m6_mul(const m6 a, const m6 b, m6 c) {
+    m6 t;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) s += a[i][k] * b[k][j];
+            t[i][j] = s;
+        }
+    memcpy(c, t, sizeof(m6));
+}
+static void m6_tmul(const m6 a, const m6 b, m6 c) { /* c = a^T b */
+    m6 t;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) s += a[k][i] * b[k][j];
+            t[i][j] = s;
+        }
+    memcpy(c, t, sizeof(m6));
+}
+static void m6_vec(const m6 a, const double* x, double* y) {
+    double t[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = 0;
+        for (int k = 0; k < 6; ++k) s += a[i][k] * x[k];
+        t[i] = s;
+    }
+    memcpy(y, t, sizeof t);
+}
+static void m6_tvec(const m6 a, const double* x, double* y) {
+    double t[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = 0;
+        for (int k = 0; k < 6; ++k) s += a[k][i] * x[k];
+        t[i] = s;
+    }
+    memcpy(y, t, sizeof t);
+}
+/* Solve A x = b for a symmetric positive definite n x n matrix (Cholesky). */
+static int spd_solve(int n, const double* A, const double* b, double* x) {
+    double L[ORC_MAXNV * ORC_MAXNV];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0)) return -1;
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    double y[ORC_MAXNV];
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Spatial algebra (Featherstone): motion (w, v), force (n, f), body coordinates.       */
+/* ------------------------------------------------------------------------------------ */
+/* Plucker transform parent -> child: X = [E 0; -E [r]x  E], E = rotation parent->child
+ * coordinates, r = child origin in parent coordinates. */
+static void plucker(const m3 E, const double* r, m6 X) {
+    m3 S, ES;
+    skew(r, S);
+    m3_mul(E, S, ES);
+    m6_zero(X);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            X[i][j] = E[i][j];
+            X[3 + i][3 + j] = E[i][j];
+            X[3 + i][j] = -ES[i][j];
+        }
+}
+/* Rigid-body spatial inertia about the body origin. */
+static void body_inertia(const orc_model* m, int b, m6 I) {
+    const double* c = &m->com[3 * b];
+    const double* ic = &m->inertia[6 * b];
+    double mass = m->mass[b];
+    m3 Ic = {{ic[0], ic[3], ic[4]}, {ic[3], ic[1], ic[5]}, {ic[4], ic[5], ic[2]}};
+    m3 C, CCt;
+    skew(c, C);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += C[i][k] * C[j][k]; /* C C^T */
+            CCt[i][j] = s;
+        }
+    m6_zero(I);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            I[i][j] = Ic[i][j] + mass * CCt[i][j];
+            I[i][3 + j] = mass * C[i][j];
+            I[3 + i][j] = mass * C[j][i];
+            I[3 + i][3 + j] = (i == j) ? mass : 0.0;
+        }
+}
+static void crm(const double* a, const double* b, double* c) { /* motion x motion */
+    double t[6], u[3];
+    cross3(a, b, t);
+    cross3(a, b + 3, t + 3);
+    cross3(a + 3, b, u);
+    t[3] += u[0]; t[4] += u[1]; t[5] += u[2];
+    memcpy(c, t, sizeof t);
+}
+static void crf(const double* a, const double* f, double* c) { /* motion x* force */
+    double t[6], u[3];
+    cross3(a, f, t);
+    cross3(a + 3, f + 3, u);
+    t[0] += u[0]; t[1] += u[1]; t[2] += u[2];
+    cross3(a, f + 3, t + 3);
+    memcpy(c, t, sizeof t);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Kinematics, contact forces                                                            */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    m6 X[ORC_MAXB];          /* parent -> body transform */
+    m3 R[ORC_MAXB];          /* body -> world rotation */
+    double p[ORC_MAXB][3];   /* body origin, world */
+    double v[ORC_MAXB][6];   /* spatial velocity, body coordinates */
+    double fext[ORC_MAXB][6];/* external spatial force, body coordinates */
+} orc_kin;
+
+static void kinematics(const orc_model* m, const double* x, orc_kin* K) {
+    const int nb = m->nb, nj = nb - 1, nq = 7 + nj;
+    const double* q = x + 7;
+    const double* vb = x + nq;       /* v_lin(3), omega(3), body frame */
+    const double* qd = x + nq + 6;
+    quat_to_R(x + 3, K->R[0]);
+    memcpy(K->p[0], x, 3 * sizeof(double));
+    K->v[0][0] = vb[3]; K->v[0][1] = vb[4]; K->v[0][2] = vb[5];
+    K->v[0][3] = vb[0]; K->v[0][4] = vb[1]; K->v[0][5] = vb[2];
+    if (m->fixed_base) memset(K->v[0], 0, 6 * sizeof(double));
+    for (int i = 1; i < nb; ++i) {
+        int l = m->parent[i];
+        m3 Rj, E;
+        axis_angle(&m->axis[3 * i], q[i - 1], Rj);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) E[a][b] = Rj[b][a];
+        plucker(E, &m->jpos[3 * i], K->X[i]);
+        m3_mul(K->R[l], Rj, K->R[i]);
+        double t[3];
+        m3_vec(K->R[l], &m->jpos[3 * i], t);
+        for (int a = 0; a < 3; ++a) K->p[i][a] = K->p[l][a] + t[a];
+        m6_vec(K->X[i], K->v[l], K->v[i]);
+        for (int a = 0; a < 3; ++a) K->v[i][a] += m->axis[3 * i + a] * qd[i - 1];
+    }
+    for (int i = 0; i < nb; ++i) memset(K->fext[i], 0, 6 * sizeof(double));
+    /* soft ground contact on the plane z = 0 */
+    for (int c = 0; c < m->nc; ++c) {
+        int b = m->contact_body[c];
+        const double* rc = &m->contact_pos[3 * c];
+        double pw[3], vloc[3], vw[3], t[3];
+        m3_vec(K->R[b], rc, t);
+        for (int a = 0; a < 3; ++a) pw[a] = K->p[b][a] + t[a];
+        cross3(K->v[b], rc, vloc); /* w x r */
+        for (int a = 0; a < 3; ++a) vloc[a] += K->v[b][3 + a];
+        m3_vec(K->R[b], vloc, vw);
+        double depth = -pw[2];
+        if (depth <= 0) continue;
+        double fn = m->contact_k * depth - m->contact_c * vw[2];
+        if (fn < 0) fn = 0;
+        double vt2 = vw[0] * vw[0] + vw[1] * vw[1];
+        double scale = -m->mu * fn / sqrt(vt2 + m->eps_f * m->eps_f);
+        double F[3] = {scale * vw[0], scale * vw[1], fn};
+        double fb[3], nb3[3];
+        m3_tvec(K->R[b], F, fb);
+        cross3(rc, fb, nb3);
+        for (int a = 0; a < 3; ++a) {
+            K->fext[b][a] += nb3[a];
+            K->fext[b][3 + a] += fb[a];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Articulated-body algorithm (floating or fixed base, gravity as a base offset).       */
+/* acc[nv] = (base spatial acceleration (w_dot, v_dot) in body coordinates, qdd).       */
+/* For a fixed base the base part is zero.                                               */
+/* ------------------------------------------------------------------------------------ */
+static int aba(const orc_model* m, const double* x, const double* tau, orc_kin* K, double* acc) {
+    const int nb = m->nb, nj = nb - 1, nq = 7 + nj;
+    const double* qd = x + nq + 6;
+    static __thread m6 IA[ORC_MAXB];
+    double pA[ORC_MAXB][6], c[ORC_MAXB][6], U[ORC_MAXB][6], D[ORC_MAXB], u[ORC_MAXB];
+    double a[ORC_MAXB][6];
+    kinematics(m, x, K);
+    for (int i = 0; i < nb; ++i) {
+        m6 I;
+        double Iv[6];
+        body_inertia(m, i, I);
+        memcpy(IA[i], I, sizeof(m6));
+        m6_vec(I, K->v[i], Iv);
+        crf(K->v[i], Iv, pA[i]);
+        for (int k = 0; k < 6; ++k) pA[i][k] -= K->fext[i][k];
+        memset(c[i], 0, sizeof c[i]);
+        if (i > 0) {
+            double Sq[6] = {0};
+            for (int k = 0; k < 3; ++k) Sq[k] = m->axis[3 * i + k] * qd[i - 1];
+            crm(K->v[i], Sq, c[i]);
+        }
+    }
+    for (int i = nb - 1; i >= 1; --i) {
+        const double* S = &m->axis[3 * i]; /* S = (axis, 0) */
+        for (int k = 0; k < 6; ++k) U[i][k] = IA[i][k][0] * S[0] + IA[i][k][1] * S[1] + IA[i][k][2] * S[2];
+        D[i] = S[0] * U[i][0] + S[1] * U[i][1] + S[2] * U[i][2] + m->armature[i];
+        u[i] = tau[i - 1] - (S[0] * pA[i][0] + S[1] * pA[i][1] + S[2] * pA[i][2]);
+        m6 Ia, tmp, XtIaX;
+        double pa[6], Iac[6], Xtpa[6];
+        for (int r = 0; r < 6; ++r)
+            for (int s = 0; s < 6; ++s) Ia[r][s] = IA[i][r][s] - U[i][r] * U[i][s] / D[i];
+        m6_vec(Ia, c[i], Iac);
+        for (int k = 0; k < 6; ++k) pa[k] = pA[i][k] + Iac[k] + U[i][k] * u[i] / D[i];
+        m6_mul(Ia, K->X[i], tmp);
+        m6_tmul(K->X[i], tmp, XtIaX);
+        m6_tvec(K->X[i], pa, Xtpa);
+        int l = m->parent[i];
+        for (int r = 0; r < 6; ++r) {
+            for (int s = 0; s < 6; ++s) IA[l][r][s] += XtIaX[r][s];
+            pA[l][r] += Xtpa[r];
+        }
+    }
+    /* gravity offset: a' = a - a_g, a_g = (0, R0^T g) */
+    double g_w[3] = {0, 0, -m->gravity}, g_b[3];
+    m3_tvec(K->R[0], g_w, g_b);
+    if (m->fixed_base) {
+        a[0][0] = a[0][1] = a[0][2] = 0;
+        a[0][3] = -g_b[0]; a[0][4] = -g_b[1]; a[0][5] = -g_b[2];
+    } else {
+        double rhs[6];
+        for (int k = 0; k < 6; ++k) rhs[k] = -pA[0][k];
+        if (spd_solve(6, &IA[0][0][0], rhs, a[0]) != 0) return -1;
+    }
+    for (int i = 1; i < nb; ++i) {
+        const double* S = &m->axis[3 * i];
+        int l = m->parent[i];
+        double ap[6];
+        m6_vec(K->X[i], a[l], ap);
+        for (int k = 0; k < 6; ++k) ap[k] += c[i][k];
+        double qdd = (u[i] - (U[i][0] * ap[0] + U[i][1] * ap[1] + U[i][2] * ap[2] + U[i][3] * ap[3] +
+                              U[i][4] * ap[4] + U[i][5] * ap[5])) / D[i];
+        for (int k = 0; k < 6; ++k) a[i][k] = ap[k];
+        for (int k = 0; k < 3; ++k) a[i][k] += S[k] * qdd;
+        acc[6 + i - 1] = qdd;
+    }
+    if (m->fixed_base) {
+        for (int k = 0; k < 6; ++k) acc[k] = 0;
+    } else {
+        for (int k = 0; k < 3; ++k) acc[k] = a[0][k];
+        for (int k = 0; k < 3; ++k) acc[3 + k] = a[0][3 + k] + g_b[k];
+    }
+    return 0;
+}
+
+/* Joint-space mass matrix by the composite-rigid-body algorithm (check only).
+ * Generalised velocity = (base (w, v) body coordinates [floating only], qdot). */
+int orc_crba(const orc_model* mdl, const double* x, double* M) {
+    const int nb = mdl->nb, nj = nb - 1;
+    const int off = mdl->fixed_base ? 0 : 6;
+    const int n = off + nj;
+    static __thread orc_kin K;
+    m6 Ic[ORC_MAXB];
+    kinematics(mdl, x, &K);
+    for (int i = 0; i < nb; ++i) body_inertia(mdl, i, Ic[i]);
+    for (int i = nb - 1; i >= 1; --i) {
+        m6 t, XtIX;
+        m6_mul(Ic[i], K.X[i], t);
+        m6_tmul(K.X[i], t, XtIX);
+        int l = mdl->parent[i];
+        for (int r = 0; r < 6; ++r)
+            for (int s = 0; s < 6; ++s) Ic[l][r][s] += XtIX[r][s];
+    }
+    memset(M, 0, sizeof(double) * n * n);
+    if (!mdl->fixed_base)
+        for (int r = 0; r < 6; ++r)
+            for (int s = 0; s < 6; ++s) M[r * n + s] = Ic[0][r][s];
+    for (int i = 1; i < nb; ++i) {
+        const double* S = &mdl->axis[3 * i];
+        double F[6];
+        for (int k = 0; k < 6; ++k) F[k] = Ic[i][k][0] * S[0] + Ic[i][k][1] * S[1] + Ic[i][k][2] * S[2];
+        int di = off + i - 1;
+        M[di * n + di] = S[0] * F[0] + S[1] * F[1] + S[2] * F[2] + mdl->armature[i];
+        int j = i;
+        while (mdl->parent[j] > 0) {
+            double t[6];
+            m6_tvec(K.X[j], F, t);
+            memcpy(F, t, sizeof t);
+            j = mdl->parent[j];
+            const double* Sj = &mdl->axis[3 * j];
+            int dj = off + j - 1;
+            double val = Sj[0] * F[0] + Sj[1] * F[1] + Sj[2] * F[2];
+            M[di * n + dj] = val;
+            M[dj * n + di] = val;
+        }
+        if (!mdl->fixed_base) {
+            double t[6];
+            m6_tvec(K.X[j], F, t); /* j's parent is the base */
+            for (int k = 0; k < 6; ++k) {
+                M[di * n + k] = t[k];
+                M[k * n + di] = t[k];
+            }
+        }
+    }
+    return n;
+}
+
+/* Bias forces h(q, v) (Coriolis, gravity, minus contact forces) by the recursive
+ * Newton-Euler algorithm with zero generalised acceleration (check only). */
+int orc_rnea_bias(const orc_model* mdl, const double* x, double* h) {
+    const int nb = mdl->nb;
+    const int off = mdl->fixed_base ? 0 : 6;
+    static __thread orc_kin K;
+    double a[ORC_MAXB][6], f[ORC_MAXB][6];
+    const int nj = nb - 1, nq = 7 + nj;
+    const double* qd = x + nq + 6;
+    kinematics(mdl, x, &K);
+    double g_w[3] = {0, 0, -mdl->gravity}, g_b[3];
+    m3_tvec(K.R[0], g_w, g_b);
+    a[0][0] = a[0][1] = a[0][2] = 0;
+    a[0][3] = -g_b[0]; a[0][4] = -g_b[1]; a[0][5] = -g_b[2];
+    for (int i = 0; i < nb; ++i) {
+        if (i > 0) {
+            int l = mdl->parent[i];
+            double Sq[6] = {0}, cc[6];
+            for (int k = 0; k < 3; ++k) Sq[k] = mdl->axis[3 * i + k] * qd[i - 1];
+            crm(K.v[i], Sq, cc);
+            m6_vec(K.X[i], a[l], a[i]);
+            for (int k = 0; k < 6; ++k) a[i][k] += cc[k];
+        }
+        m6 I;
+        double Ia[6], Iv[6], vxIv[6];
+        body_inertia(mdl, i, I);
+        m6_vec(I, a[i], Ia);
+        m6_vec(I, K.v[i], Iv);
+        crf(K.v[i], Iv, vxIv);
+        for (int k = 0; k < 6; ++k) f[i][k] = Ia[k] + vxIv[k] - K.fext[i][k];
+    }
+    for (int i = nb - 1; i >= 1; --i) {
+        const double* S = &mdl->axis[3 * i];
+        h[off + i - 1] = S[0] * f[i][0] + S[1] * f[i][1] + S[2] * f[i][2];
+        double t[6];
+        m6_tvec(K.X[i], f[i], t);
+        int l = mdl->parent[i];
+        for (int k = 0; k < 6; ++k) f[l][k] += t[k];
+    }
+    if (!mdl->fixed_base)
+        for (int k = 0; k < 6; ++k) h[k] = f[0][k];
+    return off + nj;
+}
+
+/* Generalised accelerations from ABA. acc[nv]: base (w_dot, v_dot) then qdd. */
+int orc_forward_dynamics(const orc_model* m, const double* x, const double* tau, double* acc) {
+    static __thread orc_kin K;
+    return aba(m, x, tau, &K, acc);
+}
+
+/* Contact forces in the world frame for every contact point: out [nc][3]. */
+void orc_contact_forces(const orc_model* m, const double* x, double* out) {
+    static __thread orc_kin K;
+    kinematics(m, x, &K);
+    for (int c = 0; c < m->nc; ++c) {
+        int b = m->contact_body[c];
+        const double* rc = &m->contact_pos[3 * c];
+        double pw[3], vloc[3], vw[3], t[3];
+        m3_vec(K.R[b], rc, t);
+        for (int a = 0; a < 3; ++a) pw[a] = K.p[b][a] + t[a];
+        cross3(K.v[b], rc, vloc);
+        for (int a = 0; a < 3; ++a) vloc[a] += K.v[b][3 + a];
+        m3_vec(K.R[b], vloc, vw);
+        double depth = -pw[2];
+        out[3 * c] = out[3 * c + 1] = out[3 * c + 2] = 0;
+        if (depth <= 0) continue;
+        double fn = m->contact_k * depth - m->contact_c * vw[2];
+        if (fn < 0) fn = 0;
+        double vt2 = vw[0] * vw[0] + vw[1] * vw[1];
+        double scale = -m->mu * fn / sqrt(vt2 + m->eps_f * m->eps_f);
+        out[3 * c] = scale * vw[0];
+        out[3 * c + 1] = scale * vw[1];
+        out[3 * c + 2] = fn;
+    }
+}
+
+/* World position of every body origin and contact point: bodies [nb][3], contacts [nc][3]. */
+void orc_positions(const orc_model* m, const double* x, double* bodies, double* contacts) {
+    static __thread orc_kin K;
+    kinematics(m, x, &K);
+    for (int b = 0; b < m->nb; ++b)
+        for (int a = 0; a < 3; ++a) bodies[3 * b + a] = K.p[b][a];
+    for (int c = 0; c < m->nc; ++c) {
+        int b = m->contact_body[c];
+        double t[3];
+        m3_vec(K.R[b], &m->contact_pos[3 * c], t);
+        for (int a = 0; a < 3; ++a) contacts[3 * c + a] = K.p[b][a] + t[a];
+    }
+}
+
+/* Kinetic + gravitational potential energy (check only). */
+double orc_energy(const orc_model* m, const double* x) {
+    static __thread orc_kin K;
+    kinematics(m, x, &K);
+    double e = 0;
+    for (int i = 0; i < m->nb; ++i) {
+        m6 I;
+        double Iv[6];
+        body_inertia(m, i, I);
+        m6_vec(I, K.v[i], Iv);
+        for (int k = 0; k < 6; ++k) e += 0.5 * K.v[i][k] * Iv[k];
+        double cw[3];
+        m3_vec(K.R[i], &m->com[3 * i], cw);
+        e += m->mass[i] * m->gravity * (K.p[i][2] + cw[2]);
+    }
+    for (int i = 1; i < m->nb; ++i) {
+        double qd = x[7 + m->nb - 1 + 6 + i - 1];
+        e += 0.5 * m->armature[i] * qd * qd;
+    }
+    return e;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* PD tracking, running cost, semi-implicit Euler                                       */
+/* ------------------------------------------------------------------------------------ */
+/* Sec. III-C Eq. (pd-controller), clipped to +-tau_max. */
+static void pd_torque(const orc_model* m, const double* x, const double* qref, const double* vref,
+                      double* tau) {
+    const int nj = m->nb - 1, nq = 7 + nj;
+    for (int j = 0; j < nj; ++j) {
+        double t = m->kp[j] * (qref[j] - x[7 + j]) + m->kd[j] * (vref[j] - x[nq + 6 + j]);
+        if (t > m->tau_max[j]) t = m->tau_max[j];
+        if (t < -m->tau_max[j]) t = -m->tau_max[j];
+        tau[j] = t;
+    }
+}
+
+/* Running cost c(x_h, u_h): w_z (z - z_des)^2 + w_vx (vx - vx_des)^2 + w_tilt tilt^2 +
+ * w_tau |tau|^2, z and tilt of the cost body, vx = world x-velocity of the base origin,
+ * tilt = angle between the cost body's z axis and the world z axis. */
+static double running_cost(const orc_model* m, const double* x, const orc_kin* K, const double* tau) {
+    const int nj = m->nb - 1, nq = 7 + nj;
+    int b = m->cost_body;
+    double z = K->p[b][2];
+    double tilt = atan2(sqrt(K->R[b][0][2] * K->R[b][0][2] + K->R[b][1][2] * K->R[b][1][2]), K->R[b][2][2]);
+    double vw[3];
+    m3_vec(K->R[0], x + nq, vw);
+    double vx = m->fixed_base ? 0.0 : vw[0];
+    double tt = 0;
+    for (int j = 0; j < nj; ++j) tt += tau[j] * tau[j];
+    return m->w_z * (z - m->z_des) * (z - m->z_des) + m->w_vx * (vx - m->vx_des) * (vx - m->vx_des) +
+           m->w_tilt * tilt * tilt + m->w_tau * tt;
+}
+
+/* Semi-implicit Euler: velocities first, then positions with the new velocities; base
+ * orientation by the quaternion exponential of the new body angular velocity. */
+static void integrate(const orc_model* m, double* x, const double* acc, double dt) {
+    const int nj = m->nb - 1, nq = 7 + nj;
+    double* vb = x + nq;
+    double* qd = x + nq + 6;
+    for (int j = 0; j < nj; ++j) {
+        qd[j] += dt * acc[6 + j];
+        x[7 + j] += dt * qd[j];
+    }
+    if (m->fixed_base) return;
+    /* acc = (w_dot, v_dot); state velocity = (v_lin, omega) */
+    for (int k = 0; k < 3; ++k) {
+        vb[k] += dt * acc[3 + k];
+        vb[3 + k] += dt * acc[k];
+    }
+    m3 R;
+    quat_to_R(x + 3, R);
+    double dp[3];
+    m3_vec(R, vb, dp);
+    for (int k = 0; k < 3; ++k) x[k] += dt * dp[k];
+    const double* w = vb + 3;
+    double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double th = wn * dt;
+    double dq[4];
+    if (th < 1e-12) {
+        dq[0] = 1; dq[1] = 0.5 * dt * w[0]; dq[2] = 0.5 * dt * w[1]; dq[3] = 0.5 * dt * w[2];
+    } else {
+        double s = sin(0.5 * th) / wn;
+        dq[0] = cos(0.5 * th); dq[1] = s * w[0]; dq[2] = s * w[1]; dq[3] = s * w[2];
+    }
+    double* q = x + 3;
+    double r[4] = {q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3],
+                   q[0] * dq[1] + q[1] * dq[0] + q[2] * dq[3] - q[3] * dq[2],
+                   q[0] * dq[2] - q[1] * dq[3] + q[2] * dq[0] + q[3] * dq[1],
+                   q[0] * dq[3] + q[1] * dq[2] - q[2] * dq[1] + q[3] * dq[0]};
+    double nrm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    for (int k = 0; k < 4; ++k) q[k] = r[k] / nrm;
+}
+
+/* One step under a given torque: x <- step(x, tau). Returns 0 or -1 (singular). */
+int orc_step(const orc_model* m, double* x, const double* tau, double dt) {
+    double acc[ORC_MAXNV];
+    static __thread orc_kin K;
+    if (aba(m, x, tau, &K, acc) != 0) return -1;
+    integrate(m, x, acc, dt);
+    return 0;
+}
+
+/* Rollout of one sample (Alg. 1 "simulate"): H steps from x0 tracking the Hermite
+ * setpoints of knots [nk][2][nu]; returns S = sum_h c(x_h, u_h). x_final [nx] and
+ * traj [(H+1)][nx] are optional. */
+double orc_rollout(const orc_model* m, const double* x0, const double* knots, int nk, int H,
+                   double dt, double* x_final, double* traj) {
+    const int nj = m->nb - 1, nq = 7 + nj, nx = nq + 6 + nj;
+    double x[7 + ORC_MAXB + 6 + ORC_MAXB];
+    double qref[ORC_MAXB], vref[ORC_MAXB], tau[ORC_MAXB], acc[ORC_MAXNV];
+    orc_kin* K = (orc_kin*)malloc(sizeof(orc_kin));
+    memcpy(x, x0, sizeof(double) * nx);
+    const double dtk = knot_dt(nk, H, dt);
+    double S = 0;
+    if (traj) memcpy(traj, x, sizeof(double) * nx);
+    for (int h = 0; h < H; ++h) {
+        int k;
+        double s;
+        orc_segment(h, H, nk, &k, &s);
+        for (int j = 0; j < nj; ++j)
+            orc_hermite(s, dtk, knots[(k * 2 + 0) * nj + j], knots[(k * 2 + 1) * nj + j],
+                        knots[((k + 1) * 2 + 0) * nj + j], knots[((k + 1) * 2 + 1) * nj + j],
+                        &qref[j], &vref[j]);
+        pd_torque(m, x, qref, vref, tau);
+        if (aba(m, x, tau, K, acc) != 0) {
+            S = NAN;
+            break;
+        }
+        S += running_cost(m, x, K, tau);
+        integrate(m, x, acc, dt);
+        if (traj) memcpy(traj + (size_t)(h + 1) * nx, x, sizeof(double) * nx);
+    }
+    if (x_final) memcpy(x_final, x, sizeof(double) * nx);
+    free(K);
+    return S;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Weights and average (Sec. III-C)                                                      */
+/* ------------------------------------------------------------------------------------ */
+/* info[0..5] = S_min, S_max, argmin (ties -> lowest index), ESS = 1/sum w^2, n_finite,
+ * log-sum-exp. normalize 0: min-max Eq. (softmax_minmax); 1: raw Eq. (omega-weights).
+ * Non-finite costs get weight 0. Returns 0, or -3 when no cost is finite (w = 0). */
+int orc_weights(int N, const double* S, double lambda, int normalize, double* w, double* info) {
+    double smin = INFINITY, smax = -INFINITY;
+    int best = -1, nf = 0;
+    for (int n = 0; n < N; ++n) {
+        if (!isfinite(S[n])) continue;
+        ++nf;
+        if (S[n] < smin) { smin = S[n]; best = n; }
+        if (S[n] > smax) smax = S[n];
+    }
+    for (int n = 0; n < N; ++n) w[n] = 0;
+    if (nf == 0) {
+        info[0] = NAN; info[1] = NAN; info[2] = -1; info[3] = 0; info[4] = 0; info[5] = NAN;
+        return -3;
+    }
+    double range = smax - smin;
+    double z = 0;
+    for (int n = 0; n < N; ++n) {
+        if (!isfinite(S[n])) continue;
+        double sh;
+        if (normalize == 0) sh = range > 0 ? (S[n] - smin) / range : 0.0;
+        else sh = S[n] - smin;
+        z += exp(-sh / lambda);
+    }
+    double lse = log(z);
+    double ess_den = 0;
+    for (int n = 0; n < N; ++n) {
+        if (!isfinite(S[n])) continue;
+        double sh;
+        if (normalize == 0) sh = range > 0 ? (S[n] - smin) / range : 0.0;
+        else sh = S[n] - smin;
+        w[n] = exp(-sh / lambda - lse);
+        ess_den += w[n] * w[n];
+    }
+    info[0] = smin; info[1] = smax; info[2] = best; info[3] = 1.0 / ess_den; info[4] = nf; info[5] = lse;
+    return 0;
+}
+
+/* Eq. (update-nominal) on the knots: out[e] = sum_n w_n theta_{n,e}. */
+void orc_average(int N, int E, const double* knots, const double* w, double* out) {
+    for (int e = 0; e < E; ++e) {
+        double s = 0;
+        for (int n = 0; n < N; ++n) s += w[n] * knots[(size_t)n * E + e];
+        out[e] = s;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Parallel rollouts over samples (std pthreads; each sample is independent)            */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    const orc_model* m;
+    const double* x0;
+    const double* knots;
+    int N, nk, H, E, nx, tid, nthreads;
+    double dt;
+    double* costs;
+    double* finals;
+} rollout_job;
+
+static void* rollout_worker(void* arg) {
+    rollout_job* j = (rollout_job*)arg;
+    for (int n = j->tid; n < j->N; n += j->nthreads)
+        j->costs[n] = orc_rollout(j->m, j->x0, j->knots + (size_t)n * j->E, j->nk, j->H, j->dt,
+                                  j->finals ? j->finals + (size_t)n * j->nx : NULL, NULL);
+    return NULL;
+}
+
+/* costs[N] (and finals[N][nx] if non-null) for knots [N][nk][2][nu]. */
+void orc_rollout_batch(const orc_model* m, int N, const double* x0, const double* knots, int nk,
+                       int H, double dt, double* costs, double* finals, int nthreads) {
+    const int nj = m->nb - 1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    rollout_job jobs[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = (rollout_job){m, x0, knots, N, nk, H, nk * 2 * nj, 7 + nj + 6 + nj, t, nthreads,
+                                dt, costs, finals};
+        if (nthreads > 1) pthread_create(&th[t], NULL, rollout_worker, &jobs[t]);
+    }
+    if (nthreads == 1) rollout_worker(&jobs[0]);
+    else
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Alg. 1: one MPPI solve of `iters` iterations from state x0 and nominal knots.         */
+/* ------------------------------------------------------------------------------------ */
+/* sigma [iters][nk]; mean_out, best_out [E]; knots_out (optional) [iters][N][E]
+ * costs_out (optional) [iters][N].
+ * info[0..7] = S_min, S_max (last iteration), best cost over the solve, best sample
+ * index, iteration of the best, ESS (last iteration), n_finite (last), status.
+ * Iteration i draws noise with counter iter_base + i. Returns status (0 or -3). */
+int orc_solve(const orc_model* m, int N, int nk, int H, int iters, double dt, double lambda,
+              int normalize, const double* sigma, double scale_q, double scale_v, uint64_t seed,
+              uint32_t iter_base, uint32_t inst, const double* x0, const double* nominal_in,
+              double* mean_out, double* best_out, double* info, int nthreads, double* knots_out,
+              double* costs_out) {
+    const int nj = m->nb - 1, E = nk * 2 * nj;
+    double* knots = (double*)malloc(sizeof(double) * (size_t)N * E);
+    double* costs = (double*)malloc(sizeof(double) * N);
+    double* w = (double*)malloc(sizeof(double) * N);
+    double* nominal = (double*)malloc(sizeof(double) * (size_t)E);
+    memcpy(nominal, nominal_in, sizeof(double) * E);
+    int has_limits = 0;
+    for (int j = 0; j < nj; ++j)
+        if (isfinite(m->q_min[j]) || isfinite(m->q_max[j])) has_limits = 1;
+    double best_cost = INFINITY;
+    int best_idx = -1, best_it = -1, status = 0;
+    double winfo[6] = {0};
+    memcpy(best_out, nominal, sizeof(double) * E);
+    for (int it = 0; it < iters; ++it) {
+        orc_sample_knots(nj, nk, N, H, dt, nominal, sigma + (size_t)it * nk, scale_q, scale_v, seed,
+                         iter_base + (uint32_t)it, inst, has_limits ? m->q_min : NULL,
+                         has_limits ? m->q_max : NULL, knots);
+        orc_rollout_batch(m, N, x0, knots, nk, H, dt, costs, NULL, nthreads);
+        if (knots_out) memcpy(knots_out + (size_t)it * N * E, knots, sizeof(double) * (size_t)N * E);
+        if (costs_out) memcpy(costs_out + (size_t)it * N, costs, sizeof(double) * N);
+        int st = orc_weights(N, costs, lambda, normalize, w, winfo);
+        if (st != 0) {
+            status = st;
+            continue;
+        }
+        orc_average(N, E, knots, w, nominal);
+        int b = (int)winfo[2];
+        if (costs[b] < best_cost) {
+            best_cost = costs[b];
+            best_idx = b;
+            best_it = it;
+            memcpy(best_out, knots + (size_t)b * E, sizeof(double) * E);
+        }
+    }
+    memcpy(mean_out, nominal, sizeof(double) * E);
+    info[0] = winfo[0]; info[1] = winfo[1]; info[2] = best_cost; info[3] = best_idx;
+    info[4] = best_it; info[5] = winfo[3]; info[6] = winfo[4]; info[7] = status;
+    free(knots);
+    free(costs);
+    free(w);
+    free(nominal);
+    return status;
+}
