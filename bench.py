@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Hermite-spline MPPI path.
+
+Metric: MPPI rollout steps/s (step-samples per second) and solves/s of one full MPPI
+update (Alg. 1: knot noise, rollouts, weights, knot average; 3 iterations) on the
+single-instance scale workload: the 18-DoF quadruped, K = 8192 samples, 6 Hermite knots
+over 1.0 s, dt = 0.005 (200 semi-implicit Euler steps), lambda = 0.1, random initial base
+velocity. Synthetic, seeded inputs; inputs resident in HBM when the timed region starts;
+L2 flushed (256 MiB write) between timed solves.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun): every rank solves its own instance (replicas, no data-path collective);
+value = all ranks' step-samples / max-over-ranks time ("scaling": "weak").
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPPI rollout steps/s & solves/s on 1 GB300; p50/p99 solve latency vs plain launch"
+UNIT = "rollout steps/s"
+WORKLOAD = ("single-instance scale: quadruped (floating base + 12 revolute joints), K=8192 samples, "
+            "6 Hermite knots over 1.0 s, H=200 steps (dt 0.005), 3 MPPI iterations per solve")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--samples", type=int, default=8192)
+    ap.add_argument("--mapping", type=int, default=-1, help="-1 autotuned, 0 warp, 1 half-warp, 2 thread")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-samples", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", action="store_true", help="also run the batched and serving workloads")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------
+# multi-rank control plane (gloo; timing only, no data-path collective)
+# ------------------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_max_sum(dist, t_local: float, units_local: float):
+    """(max over ranks of the timed seconds, sum over ranks of the units)."""
+    if dist is None:
+        return t_local, units_local
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64)
+    u = torch.tensor([units_local], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on the host cores
+# ------------------------------------------------------------------------------------
+def cpu_baseline(n_samples: int):
+    import oracle
+    from paper_2511_19204_gb300 import synth
+    oracle.build()
+    p = synth.scale_quadruped(n=n_samples)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.solve_problem(p, nthreads=cores)
+    dt = time.perf_counter() - t0
+    units = p.n * p.horizon * p.iters
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{p.n} of 8192 samples, all {p.iters} iterations x {p.horizon} steps, one solve "
+                      f"({dt:.2f} s wall, FP64 C oracle, {cores} threads)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2511_19204_gb300 import synth
+    oracle.build()
+    n = max(64, args.cpu_samples // 2)
+    p = synth.scale_quadruped(n=n)
+    cores = os.cpu_count() or 1
+    for _ in range(max(args.warmup, 0)):
+        oracle.solve_problem(p, nthreads=cores)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.solve_problem(p, nthreads=cores, iter_base=3 * k)
+        times.append(time.perf_counter() - t0)
+    units = p.n * p.horizon * p.iters
+    value = units * len(times) / sum(times)
+    ms = 1e3 * sum(times) / len(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{n} of 8192 samples per step (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} of 8192 samples, 3 iterations x 200 steps per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2511_19204_gb300 import build as B
+    from paper_2511_19204_gb300 import flops, mppi, synth
+
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    B.build()
+    mppi.load()
+    p = synth.scale_quadruped(n=args.samples, seed_state=20 + rank)
+    p.instance = rank
+    stream = torch.cuda.Stream()
+    model = mppi.Model(p.model)
+    ctrl = mppi.Controller.from_problem(model, p, mapping=args.mapping, block=args.block,
+                                        stream=stream.cuda_stream)
+    tuned = None
+    if args.mapping == -1:
+        try:
+            m, b, ms = ctrl.autotune()
+            tuned = {"mapping": mppi.MAPPING_NAMES.get(m, m), "block": b,
+                     "ms_per_rollout": {mppi.MAPPING_NAMES[k]: [round(float(v), 4) if v > 0 else None for v in ms[k]]
+                                        for k in range(4)}}
+        except mppi.MppiError:
+            tuned = None
+    info = ctrl.info()
+    ctrl.profile(True)
+    nx, E = p.model.nx, ctrl.E
+    x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
+    mean = torch.zeros(E, dtype=torch.float32, device="cuda")
+    best = torch.zeros(E, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        ctrl.solve_device(x.data_ptr(), mean.data_ptr(), best.data_ptr())
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    per_solve_ms, rollout_ms = [], []
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)                                   # L2 flush (not timed)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            ctrl.solve_device(x.data_ptr(), mean.data_ptr(), best.data_ptr())
+            ev1.record(stream)
+        ev1.synchronize()
+        per_solve_ms.append(ev0.elapsed_time(ev1))
+        rollout_ms.extend(float(v) for v in ctrl.rollout_ms())
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    t_local = sum(per_solve_ms) / 1e3
+    units = p.n * p.horizon * p.iters
+    t_max, units_all = reduce_max_sum(dist, t_local, units * args.steps)
+    value = units_all / t_max
+    # end to end through the C ABI with host buffers (H2D state, graph, D2H results, sync)
+    xs = p.state.copy()
+    e2e_t = []
+    for k in range(args.e2e_steps + 2):
+        t0 = time.perf_counter()
+        ctrl.solve(xs)
+        if k >= 2:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_local = sum(e2e_t)
+    e2e_max, e2e_units = reduce_max_sum(dist, e2e_local, units * len(e2e_t))
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel (the rollout): FP32 ALU bound
+    fl_step = flops.flops_per_step(p.model)
+    roll_ms = statistics.mean(rollout_ms)
+    achieved = fl_step * p.n * p.horizon / (roll_ms * 1e-3) / 1e12
+    peak = flops.fp32_peak_tflops()
+    lat = sorted(per_solve_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "samples": p.n, "knots": p.nk, "horizon": p.horizon,
+                   "iters": p.iters, "dt": p.dt, "lambda": p.lam,
+                   "mapping": mppi.MAPPING_NAMES.get(info["mapping"], info["mapping"]), "block": info["block"],
+                   "autotune": tuned, "l2": "flushed between timed solves (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "solves_per_s": args.steps * world / t_max,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "mean": statistics.mean(lat)},
+        "e2e": {"value": e2e_units / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * nx, "d2h_bytes_per_step": 4 * 2 * E + 48,
+                "ms_per_step": 1e3 * e2e_local / max(len(e2e_t), 1)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "rollout",
+                     "flops_per_step_sample": fl_step, "launch_ms": roll_ms,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts and max clock)"},
+        "gpu_launches": args.steps * ctrl.kernels_per_solve,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_samples)
+    print(json.dumps(line), flush=True)
+    del np
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

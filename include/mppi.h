@@ -1,0 +1,328 @@
+/*
+ * mppi.h - C ABI of the GB300 (sm_103a) Hermite-spline MPPI hot path.
+ *
+ * The library implements one receding-horizon update of "Reference-Free Sampling-Based
+ * Model Predictive Control" (arXiv 2511.19204): Alg. 1 (Sec. III-C) with the cubic
+ * Hermite knot parameterisation of Sec. III-A, the per-knot noise schedule of Sec. III-B,
+ * the min-max softmin weights and knot average of Sec. III-C, and best-trajectory
+ * tracking (Sec. III-D). Rollouts use floating-base rigid-body dynamics with soft
+ * ground contact in place of the paper's simulator.
+ *
+ * Conventions used by every entry point:
+ *   - Robot state x [nx], FP64 at the boundary, rounded to FP32 on the device:
+ *       [p_base(3, world), quat(4: w,x,y,z, Hamilton, body->world), q(nj),
+ *        v_base_lin(3, body frame), omega_base(3, body frame), qdot(nj)],
+ *     nq = 7 + nj, nv = 6 + nj, nx = nq + nv.
+ *   - Knots [nk][2][nj] row-major FP32: [knot][position | velocity][joint]. Knot j sits
+ *     at t_j = j * H * dt / (nk - 1) (uniform, both horizon ends included).
+ *   - Pointers named h_* are host memory, d_* device memory of the current CUDA device.
+ *     Unless stated otherwise the caller owns every buffer it passes; the library
+ *     copies inputs before returning and never keeps caller pointers.
+ *   - Every call returns an mppi_status: 0 = MPPI_OK, > 0 = MPPI_PENDING, < 0 = error.
+ *     No exception crosses the ABI and nothing aborts the process. After
+ *     MPPI_ERR_CUDA, mppi_last_error() describes the failing CUDA call.
+ *   - A context (mppi_ctx) is not thread-safe; a server (mppi_server) is.
+ */
+#ifndef MPPI_H_
+#define MPPI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mppi_status;
+#define MPPI_OK 0
+#define MPPI_PENDING 1
+#define MPPI_ERR_INVALID_ARG (-1)
+#define MPPI_ERR_NONFINITE_STATE (-2)
+#define MPPI_ERR_ALL_COSTS_NONFINITE (-3)
+#define MPPI_ERR_OUT_OF_MEMORY (-4)
+#define MPPI_ERR_ADMISSION (-5)
+#define MPPI_ERR_TIMEOUT (-6)
+#define MPPI_ERR_CUDA (-7)
+#define MPPI_ERR_UNSUPPORTED (-8)
+#define MPPI_ERR_NOT_FOUND (-9)
+
+/* Rollout mappings (chosen per context, MPPI_MAP_AUTO asks the autotuner). */
+#define MPPI_MAP_AUTO (-1)
+#define MPPI_MAP_WARP 0       /* one sample per warp, one lane per body             */
+#define MPPI_MAP_HALFWARP 1   /* one sample per 16 lanes, one lane per body (nb<=16) */
+#define MPPI_MAP_CHAIN 2      /* one sample per 4 lanes, one lane per leg chain (a
+                                 floating base with 4 equal 3-body chains)           */
+#define MPPI_MAP_THREAD 3     /* one sample per thread (specialised robot trees)    */
+
+/* Weight normalisation. */
+#define MPPI_NORM_MINMAX 0    /* Eq. (softmax_minmax): costs min-max normalised first */
+#define MPPI_NORM_RAW 1       /* Eq. (omega-weights): exp(-S/lambda)                   */
+
+/* What stays resident as the next solve's warm start. */
+#define MPPI_WARM_BEST 0      /* Alg. 1: tau_0 <- tau_best at every control step      */
+#define MPPI_WARM_MEAN 1      /* the last weighted mean                               */
+
+#define MPPI_MAX_BODIES 32
+#define MPPI_MAX_CONTACTS 32
+#define MPPI_MAX_CHILDREN 8
+#define MPPI_MAX_KNOTS 16
+
+/*
+ * Robot description. Body 0 is the base (6-DoF floating unless fixed_base != 0); body
+ * i >= 1 hangs from parent[i] < i on a revolute joint whose frame sits at jpos[i] in
+ * the parent frame, parallel to it at q = 0, rotating by q_i about the unit axis[i]
+ * (child coordinates). Joint j (state index) belongs to body j + 1.
+ * Inertia of body b: mass[b], centre of mass com[b] (body frame), rotational inertia
+ * about it inertia[b] = (Ixx, Iyy, Izz, Ixy, Ixz, Iyz). armature[b] is the joint's
+ * reflected rotor inertia. PD gains, torque limits and joint limits are per joint
+ * (Eq. pd-controller; Eq. vel-clamp uses q_min/q_max, +-INFINITY disables it).
+ * Contacts are points contact_pos[c] on body contact_body[c] against the ground plane
+ * z = 0: f_n = max(0, k*depth - c*v_z), f_t = -mu f_n v_t / sqrt(|v_t|^2 + eps_f^2).
+ * Running cost c(x_h, u_h) = w_z (z - z_des)^2 + w_vx (vx - vx_des)^2 + w_tilt tilt^2
+ * + w_tau |u|^2 with z and tilt of body cost_body and vx the world-x velocity of the
+ * base origin (Sec. IV-A cost sum, quadratic terms of the synthetic workloads).
+ * q_init (nullable, [nj]) seeds the initial nominal theta^q = q_init, theta^v = 0
+ * (Alg. 1 initialisation); NULL means zeros. All arrays are read during the call only.
+ */
+typedef struct mppi_model_desc {
+    int32_t nb;                   /* bodies, 1..MPPI_MAX_BODIES */
+    int32_t nc;                   /* contacts, 0..MPPI_MAX_CONTACTS */
+    int32_t fixed_base;
+    int32_t cost_body;
+    const int32_t* parent;        /* [nb], parent[0] = -1 */
+    const double* axis;           /* [nb][3] */
+    const double* jpos;           /* [nb][3] */
+    const double* mass;           /* [nb] */
+    const double* com;            /* [nb][3] */
+    const double* inertia;        /* [nb][6] */
+    const double* armature;       /* [nb] */
+    const double* q_min;          /* [nb-1] */
+    const double* q_max;          /* [nb-1] */
+    const double* kp;             /* [nb-1] */
+    const double* kd;             /* [nb-1] */
+    const double* tau_max;        /* [nb-1] */
+    const int32_t* contact_body;  /* [nc] */
+    const double* contact_pos;    /* [nc][3] */
+    const double* q_init;         /* [nb-1] or NULL */
+    double contact_k, contact_c, mu, eps_f, gravity;
+    double z_des, vx_des, w_z, w_vx, w_tilt, w_tau;
+} mppi_model_desc;
+
+typedef struct mppi_params {
+    double dt;            /* simulation step (s) */
+    double scale_q;       /* position-knot noise scale (Alg. 1 scale_q), default 1 */
+    double scale_v;       /* velocity-knot noise scale; <= 0 selects 1 / knot spacing */
+    int32_t normalize;    /* MPPI_NORM_MINMAX (default) or MPPI_NORM_RAW */
+    int32_t warm_from;    /* MPPI_WARM_BEST (default) or MPPI_WARM_MEAN */
+    uint64_t seed;        /* Philox key */
+    uint32_t instance_id; /* Philox counter word 3: results depend on it, not on scheduling */
+    int32_t mapping;      /* MPPI_MAP_* */
+    int32_t block_size;   /* threads per block of the rollout kernel, 0 = default */
+    int32_t reserved;
+    void* stream;         /* cudaStream_t for all work of this context, NULL = own stream */
+} mppi_params;
+
+/* Per-solve information. Costs are the last iteration's unless stated. */
+typedef struct mppi_result {
+    double cost_min;      /* S_min over finite costs */
+    double cost_max;      /* S_max over finite costs */
+    double best_cost;     /* lowest cost seen in any iteration of this solve (Sec. III-D) */
+    double ess;           /* 1 / sum w^2 */
+    double lse;           /* log sum_j exp(-S_hat_j / lambda) */
+    int32_t best_index;   /* sample of best_cost (ties -> lowest index) */
+    int32_t best_iter;    /* iteration of best_cost */
+    int32_t n_finite;     /* finite costs in the last iteration */
+    int32_t status;       /* MPPI_OK or MPPI_ERR_ALL_COSTS_NONFINITE */
+} mppi_result;
+
+typedef struct mppi_model mppi_model;
+typedef struct mppi_ctx mppi_ctx;
+typedef struct mppi_server mppi_server;
+
+/* ---------------------------------------------------------------------------------- */
+/* Models and contexts                                                                 */
+/* ---------------------------------------------------------------------------------- */
+
+/* Validate desc and upload the model's constants to the current device.
+ * Errors: INVALID_ARG (sizes, parents, non-unit axes, negative masses, cost_body),
+ * OUT_OF_MEMORY, CUDA. *out is owned by the caller (mppi_model_destroy). */
+mppi_status mppi_model_create(const mppi_model_desc* desc, mppi_model** out);
+void mppi_model_destroy(mppi_model* model);
+
+/* One MPC instance (Alg. 1 parameters): K samples (sample 0 is the unperturbed nominal,
+ * Alg. 1 samples n = 1..K-1), H simulation steps, `knots` Hermite knots
+ * (2..MPPI_MAX_KNOTS), temperature lambda > 0, `iters` MPPI iterations per solve and
+ * the noise schedule sigma_schedule[iters][knots] (standard deviations, rad; the
+ * cached table of Eq. overall-noise-kernel). All device buffers are allocated here and
+ * owned by the context; the model must outlive it.
+ * Errors: INVALID_ARG (K < 1, H < 1, knots out of range, lambda <= 0, sigma < 0 or not
+ * finite, dt <= 0, unsupported mapping), OUT_OF_MEMORY, CUDA. */
+mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t knots,
+                        double lambda, const float* h_sigma_schedule, int32_t iters,
+                        const mppi_params* params, mppi_ctx** out);
+void mppi_destroy(mppi_ctx* ctx);
+
+/* One MPPI update (Alg. 1 inner loop over `iters` iterations) from state h_state.
+ * h_warm_start [knots][2][nj] replaces the resident nominal if non-NULL; NULL keeps the
+ * resident one (initially theta^q = q_init, theta^v = 0; after each solve the best
+ * knots, or the mean under MPPI_WARM_MEAN). Writes the weighted-mean knots of the last
+ * iteration to h_out_mean and, if non-NULL, the best knots (tau_best) to h_out_best and
+ * the information to h_info. Blocks until the results are on the host.
+ * Errors: INVALID_ARG, NONFINITE_STATE (state not finite, nothing launched),
+ * ALL_COSTS_NONFINITE (some iteration had no finite cost; that iteration left the
+ * nominal unchanged, outputs are still written), CUDA. */
+mppi_status mppi_solve(mppi_ctx* ctx, const double* h_state, const float* h_warm_start,
+                       float* h_out_mean, float* h_out_best, mppi_result* h_info);
+
+/* Same update on device-resident data, enqueued on the context's stream without a host
+ * synchronisation: d_state [nx] FP64, d_warm_start nullable, d_out_mean [knots*2*nj],
+ * d_out_best nullable, d_info nullable (device mppi_result). The CUDA-graph-captured
+ * iteration sequence runs as one graph launch. Finiteness of the state is not checked.
+ * Errors: INVALID_ARG, CUDA. */
+mppi_status mppi_solve_device(mppi_ctx* ctx, const double* d_state, const float* d_warm_start,
+                              float* d_out_mean, float* d_out_best, mppi_result* d_info);
+
+/* Wait for all work of the context. */
+mppi_status mppi_sync(mppi_ctx* ctx);
+
+/* Rollout step only (Alg. 1 "simulate") on caller-given knots, bypassing the noise:
+ * h_knots [K][knots][2][nj] -> h_costs [K] (FP32 sums with Kahan compensation, widened to
+ * FP64) and, if non-NULL, h_final_states [K][nx]. Uses the context's rollout mapping. */
+mppi_status mppi_rollout_explicit(mppi_ctx* ctx, const double* h_state, const float* h_knots,
+                                  double* h_costs, double* h_final_states);
+
+/* Noise step only (Alg. 1 sampling, clamp of Eq. vel-clamp): the knots of iteration
+ * `iter` (selects the sigma row) drawn around h_nominal with Philox counter word 2 =
+ * iter_counter. h_out [K][knots][2][nj]. */
+mppi_status mppi_sample_knots(mppi_ctx* ctx, int32_t iter, uint32_t iter_counter,
+                              const float* h_nominal, float* h_out);
+
+/* Counter of the next solve's first iteration (Philox counter word 2); it advances by
+ * `iters` per solve. Set it to replay a solve. */
+mppi_status mppi_get_iter_counter(const mppi_ctx* ctx, uint32_t* out);
+mppi_status mppi_set_iter_counter(mppi_ctx* ctx, uint32_t value);
+
+/* Deterministic resume: the resident warm start and the noise counter, as bytes.
+ * Call with buf = NULL to query *len. */
+mppi_status mppi_export_state(const mppi_ctx* ctx, void* buf, size_t* len);
+mppi_status mppi_import_state(mppi_ctx* ctx, const void* buf, size_t len);
+
+/* ---------------------------------------------------------------------------------- */
+/* Kernel-level entry points (each runs one kernel of the path on host buffers)         */
+/* ---------------------------------------------------------------------------------- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) words for n counters: h_ctr [n][4], key [2],
+ * h_out [n][4]. */
+mppi_status mppi_philox_words(int32_t n, const uint32_t* h_ctr, const uint32_t* h_key,
+                              uint32_t* h_out);
+
+/* Weights of Eq. (softmax_minmax) (normalize = MPPI_NORM_MINMAX) or Eq. (omega-weights)
+ * (MPPI_NORM_RAW) for K costs, FP64 log-sum-exp. Non-finite costs get weight 0.
+ * h_w [K] FP64. Returns ALL_COSTS_NONFINITE when no cost is finite (w = 0). */
+mppi_status mppi_weights(int32_t K, const float* h_costs, double lambda, int32_t normalize,
+                         double* h_w, mppi_result* h_info);
+
+/* Eq. (update-nominal) on the knots: h_out[e] = sum_n h_w[n] h_knots[n][e] with FP64
+ * accumulation in a fixed order (chunks of 64 samples). h_knots [K][E], h_out [E]. */
+mppi_status mppi_average(int32_t K, int32_t E, const float* h_knots, const double* h_w,
+                         double* h_out);
+
+/* Single-step state derivative: generalised accelerations h_acc [n][nv] (base spatial
+ * acceleration (w_dot, v_dot) in body coordinates, then qdd) of n states under
+ * torques h_tau [n][nj], contact forces included, by the warp-per-sample articulated-
+ * body recursion. */
+mppi_status mppi_forward_dynamics(const mppi_model* model, int32_t n, const double* h_states,
+                                  const double* h_tau, double* h_acc);
+/* Same with fp64 != 0 selecting the FP64 check build of the kernel. */
+mppi_status mppi_forward_dynamics_ex(const mppi_model* model, int32_t n, const double* h_states,
+                                     const double* h_tau, double* h_acc, int32_t fp64);
+
+/* ---------------------------------------------------------------------------------- */
+/* Batched solves: many contexts in one persistent launch                               */
+/* ---------------------------------------------------------------------------------- */
+
+/* Solve `count` independent contexts (uneven models, K, H, knots, lambda) in one
+ * persistent kernel that walks a device work queue of (instance, sample tile) items;
+ * the last tile of an instance computes its weights and average and enqueues its next
+ * iteration. h_states[i] [nx_i], h_warm[i] nullable, h_out_mean[i] [E_i],
+ * h_out_best[i] nullable, h_info [count] nullable. Every instance's result equals its
+ * mppi_solve result for the same inputs (noise depends only on seed, instance_id and
+ * the iteration counter). Blocks until done. Device waits inside the kernel are bounded
+ * (MPPI_ERR_TIMEOUT). Errors: INVALID_ARG, UNSUPPORTED (contexts on other devices or
+ * with foreign streams), OUT_OF_MEMORY, TIMEOUT, CUDA. */
+mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, const double* const* h_states,
+                             const float* const* h_warm, float* const* h_out_mean,
+                             float* const* h_out_best, mppi_result* h_info);
+
+/* ---------------------------------------------------------------------------------- */
+/* Serving: continuous batching of controller requests on one GPU                       */
+/* ---------------------------------------------------------------------------------- */
+
+/* A request loop on `device` that admits solves while their device memory fits in
+ * mem_budget_bytes and at most max_inflight launch groups are on the GPU; requests that
+ * arrive while others run are admitted as slots and memory free up, and their work
+ * overlaps on the device (separate streams). *out owned by the caller. */
+mppi_status mppi_server_create(int32_t device, size_t mem_budget_bytes, int32_t max_inflight,
+                               mppi_server** out);
+void mppi_server_destroy(mppi_server* server);
+
+/* Queue one solve of ctx from h_state (copied now) with the resident warm start (or
+ * h_warm_start, copied now). The context must not be used elsewhere until its ticket
+ * is polled complete. Errors: INVALID_ARG, NONFINITE_STATE, ADMISSION (the request
+ * alone exceeds the memory budget). */
+mppi_status mppi_submit(mppi_server* server, mppi_ctx* ctx, const double* h_state,
+                        const float* h_warm_start, uint64_t* ticket);
+
+/* Result of a ticket: MPPI_PENDING while running (after waiting up to timeout_us,
+ * < 0 = wait forever), else the solve's status with h_out_mean [E], h_out_best
+ * (nullable) and h_info (nullable) written. A completed ticket is released; polling it
+ * again returns NOT_FOUND. */
+mppi_status mppi_poll(mppi_server* server, uint64_t ticket, float* h_out_mean,
+                      float* h_out_best, mppi_result* h_info, int64_t timeout_us);
+
+/* Server counters: [0] submitted, [1] completed, [2] launches, [3] peak bytes admitted,
+ * [4] requests that waited for admission. */
+mppi_status mppi_server_stats(mppi_server* server, int64_t* h_out5);
+
+/* ---------------------------------------------------------------------------------- */
+/* Autotuning and introspection                                                         */
+/* ---------------------------------------------------------------------------------- */
+
+/* Time every supported rollout mapping and block size for this context's model and
+ * sizes (a few timed launches each) and switch the context to the fastest. h_ms (nullable,
+ * [4*4]) receives the timings in ms per rollout launch (mapping-major, block sizes 32, 64,
+ * 128, 256; negative = not supported). Writes the choice to *mapping / *block_size. */
+mppi_status mppi_autotune(mppi_ctx* ctx, int32_t* mapping, int32_t* block_size, float* h_ms);
+
+/* Switch a context's rollout mapping and block size (MPPI_MAP_WARP/HALFWARP/CHAIN/THREAD). */
+mppi_status mppi_ctx_set_mapping(mppi_ctx* ctx, int32_t mapping, int32_t block_size);
+
+/* FP64 check build: when on, mppi_rollout_explicit runs the same rollout source in double
+ * precision (the warp mappings) so that comparisons with an FP64 reference separate
+ * algorithmic differences from FP32 rounding. The product path is unaffected. */
+mppi_status mppi_ctx_set_fp64_check(mppi_ctx* ctx, int32_t on);
+
+/* Profiling: with on != 0 the captured solve graph records CUDA events around each
+ * iteration's rollout launch; mppi_ctx_rollout_ms then returns the rollout kernel
+ * durations of the last completed solve (h_ms [iters], milliseconds; synchronises). */
+mppi_status mppi_ctx_profile(mppi_ctx* ctx, int32_t on);
+mppi_status mppi_ctx_rollout_ms(mppi_ctx* ctx, float* h_ms);
+
+/* Dimensions of a context: [0] K, [1] H, [2] knots, [3] iters, [4] nj, [5] nx,
+ * [6] mapping, [7] block_size. */
+mppi_status mppi_ctx_info(const mppi_ctx* ctx, int32_t* h_out8);
+
+/* Device bytes one solve of a context occupies (its buffers). */
+size_t mppi_ctx_device_bytes(const mppi_ctx* ctx);
+
+/* Number of kernels one solve launches (for launch accounting). */
+int32_t mppi_ctx_kernels_per_solve(const mppi_ctx* ctx);
+
+const char* mppi_status_str(mppi_status status);
+/* Text of the last CUDA error seen by this context (or by the library when ctx is NULL). */
+const char* mppi_last_error(const mppi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPPI_H_ */

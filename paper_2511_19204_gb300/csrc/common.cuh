@@ -1,0 +1,380 @@
+// Device-side building blocks of the GB300 MPPI path: model constants, Philox4x32-10,
+// Box-Muller, small spatial-algebra helpers. Everything is templated on the scalar
+// type T (float for the product, double for the FP64 check build).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mppi.h"
+
+namespace mppi {
+
+constexpr int MAXB = MPPI_MAX_BODIES;
+constexpr int MAXC = MPPI_MAX_CONTACTS;
+constexpr int MAXCH = MPPI_MAX_CHILDREN;
+constexpr int MAXK = MPPI_MAX_KNOTS;
+
+// ------------------------------------------------------------------------------------
+// Scalar helpers (overloads keep the templated code free of f/non-f spellings)
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void sc_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sc_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sc_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sc_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ float sc_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sc_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float sc_log(float x) { return logf(x); }
+__device__ __forceinline__ double sc_log(double x) { return log(x); }
+__device__ __forceinline__ float sc_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double sc_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float sc_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double sc_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float sc_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double sc_min(double a, double b) { return fmin(a, b); }
+template <typename T>
+__device__ __forceinline__ T sc_clamp(T x, T lo, T hi) { return sc_min(sc_max(x, lo), hi); }
+
+// ------------------------------------------------------------------------------------
+// Model constants. Per-body arrays are structure-of-arrays over MAXB so that lane b of
+// a warp reads entry b without bank conflicts. Joint j lives on body j + 1; per-joint
+// arrays are indexed by body. The struct is copied into shared memory by one bulk
+// (TMA) copy per block, so its size is a multiple of 16 bytes.
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct alignas(16) DevModel {
+    T axis[3][MAXB];
+    T jpos[3][MAXB];
+    T mass[MAXB];
+    T mc[3][MAXB];        // mass * centre of mass (body frame)
+    T Ao[6][MAXB];        // rotational inertia about the body origin: xx yy zz xy xz yz
+    T armature[MAXB];
+    T kp[MAXB];
+    T kd[MAXB];
+    T tau_max[MAXB];
+    T q_min[MAXB];
+    T q_max[MAXB];
+    T q_init[MAXB];
+    T cpos[3][MAXC];      // contact points, sorted by body (stable)
+    int32_t parent[MAXB];
+    int32_t level[MAXB];
+    int32_t nchild[MAXB];
+    int32_t child[MAXCH][MAXB];
+    int32_t cfirst[MAXB];
+    int32_t ccount[MAXB];
+    int32_t nb, nc, nlevels, fixed_base;
+    int32_t cost_body, has_limits, topology, pad0;
+    T contact_k, contact_c, mu, eps_f;
+    T gravity, z_des, vx_des, w_z;
+    T w_vx, w_tilt, w_tau, pad1;
+};
+
+// Robot trees with a specialised thread-per-sample kernel.
+constexpr int TOPO_GENERIC = 0;
+constexpr int TOPO_QUADRUPED = 1;   // 4 x (hip, thigh, calf) chains off the base, foot on calf
+constexpr int TOPO_HUMANOID = 2;
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64-bit
+// multiplies, Weyl key schedule.
+// ------------------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        U4 n;
+        n.x = hi1 ^ c.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k1;
+        n.w = lo0;
+        c = n;
+    }
+    return c;
+}
+
+// Box-Muller (Box & Muller 1958) on two words: u1 = ((wa >> 8) + 1) 2^-24 in (0, 1],
+// u2 = (wb >> 8) 2^-24 in [0, 1); eps_a = r cos(2 pi u2), eps_b = r sin(2 pi u2).
+// u1 and 2*u2 are exact in FP32; sincospi avoids rounding 2*pi.
+template <typename T>
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* ea, T* eb) {
+    const T two_m24 = T(1.0 / 16777216.0);
+    const T u1 = (T)((wa >> 8) + 1u) * two_m24;
+    const T u2x2 = (T)(wb >> 8) * (T(2) * two_m24);
+    const T r = sc_sqrt(T(-2) * sc_log(u1));
+    T s, c;
+    sc_sincospi(u2x2, &s, &c);
+    *ea = r * c;
+    *eb = r * s;
+}
+
+// ------------------------------------------------------------------------------------
+// 3-vector / 3x3 helpers
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ V3<T> v3(T x, T y, T z) { return V3<T>{x, y, z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T>
+__device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Row-major 3x3.
+template <typename T>
+struct M3 {
+    T m[9];
+};
+template <typename T>
+__device__ __forceinline__ V3<T> mul(const M3<T>& R, V3<T> v) {
+    return {R.m[0] * v.x + R.m[1] * v.y + R.m[2] * v.z, R.m[3] * v.x + R.m[4] * v.y + R.m[5] * v.z,
+            R.m[6] * v.x + R.m[7] * v.y + R.m[8] * v.z};
+}
+template <typename T>
+__device__ __forceinline__ V3<T> mulT(const M3<T>& R, V3<T> v) {
+    return {R.m[0] * v.x + R.m[3] * v.y + R.m[6] * v.z, R.m[1] * v.x + R.m[4] * v.y + R.m[7] * v.z,
+            R.m[2] * v.x + R.m[5] * v.y + R.m[8] * v.z};
+}
+template <typename T>
+__device__ __forceinline__ M3<T> mul(const M3<T>& A, const M3<T>& B) {
+    M3<T> C;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            C.m[3 * i + j] = A.m[3 * i] * B.m[j] + A.m[3 * i + 1] * B.m[3 + j] + A.m[3 * i + 2] * B.m[6 + j];
+    return C;
+}
+// Rotation about unit axis a by angle (child -> parent): c I + s [a]x + (1 - c) a a^T.
+template <typename T>
+__device__ __forceinline__ M3<T> axis_rotation(V3<T> a, T s, T c) {
+    const T t = T(1) - c;
+    M3<T> R;
+    R.m[0] = c + t * a.x * a.x;
+    R.m[1] = t * a.x * a.y - s * a.z;
+    R.m[2] = t * a.x * a.z + s * a.y;
+    R.m[3] = t * a.y * a.x + s * a.z;
+    R.m[4] = c + t * a.y * a.y;
+    R.m[5] = t * a.y * a.z - s * a.x;
+    R.m[6] = t * a.z * a.x - s * a.y;
+    R.m[7] = t * a.z * a.y + s * a.x;
+    R.m[8] = c + t * a.z * a.z;
+    return R;
+}
+template <typename T>
+__device__ __forceinline__ M3<T> quat_to_R(T w, T x, T y, T z) {
+    M3<T> R;
+    R.m[0] = T(1) - T(2) * (y * y + z * z);
+    R.m[1] = T(2) * (x * y - w * z);
+    R.m[2] = T(2) * (x * z + w * y);
+    R.m[3] = T(2) * (x * y + w * z);
+    R.m[4] = T(1) - T(2) * (x * x + z * z);
+    R.m[5] = T(2) * (y * z - w * x);
+    R.m[6] = T(2) * (x * z - w * y);
+    R.m[7] = T(2) * (y * z + w * x);
+    R.m[8] = T(1) - T(2) * (x * x + y * y);
+    return R;
+}
+
+// ------------------------------------------------------------------------------------
+// Symmetric 6x6 articulated inertia [[A, B], [B^T, C]], A and C symmetric (xx yy zz xy
+// xz yz), B full row-major. Acts on motion (w, v) and yields force (n, f).
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct Art {
+    T A[6];
+    T B[9];
+    T C[6];
+};
+
+template <typename T>
+__device__ __forceinline__ V3<T> sym_mul(const T* S, V3<T> v) {
+    return {S[0] * v.x + S[3] * v.y + S[4] * v.z, S[3] * v.x + S[1] * v.y + S[5] * v.z,
+            S[4] * v.x + S[5] * v.y + S[2] * v.z};
+}
+
+// R S R^T for symmetric S.
+template <typename T>
+__device__ __forceinline__ void sym_rotate(const M3<T>& R, const T* S, T* out) {
+    // N = S R^T  (N[i][j] = sum_k S[i][k] R[j][k])
+    const T s[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
+    T N[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) N[i][j] = s[i][0] * R.m[3 * j] + s[i][1] * R.m[3 * j + 1] + s[i][2] * R.m[3 * j + 2];
+    auto e = [&](int i, int j) { return R.m[3 * i] * N[0][j] + R.m[3 * i + 1] * N[1][j] + R.m[3 * i + 2] * N[2][j]; };
+    out[0] = e(0, 0);
+    out[1] = e(1, 1);
+    out[2] = e(2, 2);
+    out[3] = e(0, 1);
+    out[4] = e(0, 2);
+    out[5] = e(1, 2);
+}
+// R B R^T for full B.
+template <typename T>
+__device__ __forceinline__ void full_rotate(const M3<T>& R, const T* B, T* out) {
+    T N[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            N[i][j] = B[3 * i] * R.m[3 * j] + B[3 * i + 1] * R.m[3 * j + 1] + B[3 * i + 2] * R.m[3 * j + 2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            out[3 * i + j] = R.m[3 * i] * N[0][j] + R.m[3 * i + 1] * N[1][j] + R.m[3 * i + 2] * N[2][j];
+}
+
+// Congruence X^T Ia X for the parent->child Plucker transform X = [E 0; -E r^ E] with
+// E = Rj^T (Rj = joint rotation child->parent) and r = joint position in the parent:
+// rotate (Rj M Rj^T), then shift the reference point by r:
+//   C' unchanged, B' += r^ C', A' += r^ B'^T - B'' r^  (B'' the shifted B).
+template <typename T>
+__device__ __forceinline__ void art_to_parent(const Art<T>& Ia, const M3<T>& Rj, V3<T> r, Art<T>& out) {
+    T A[6], B[9], C[6];
+    sym_rotate(Rj, Ia.A, A);
+    full_rotate(Rj, Ia.B, B);
+    sym_rotate(Rj, Ia.C, C);
+    // B2 = B + r^ C : column j of r^ C = r x C[:, j]
+    const V3<T> c0 = v3(C[0], C[3], C[4]), c1 = v3(C[3], C[1], C[5]), c2 = v3(C[4], C[5], C[2]);
+    const V3<T> x0 = cross(r, c0), x1 = cross(r, c1), x2 = cross(r, c2);
+    T B2[9] = {B[0] + x0.x, B[1] + x1.x, B[2] + x2.x, B[3] + x0.y, B[4] + x1.y,
+               B[5] + x2.y, B[6] + x0.z, B[7] + x1.z, B[8] + x2.z};
+    // D = r^ B^T : column j = r x (row j of B)
+    const V3<T> d0 = cross(r, v3(B[0], B[1], B[2]));
+    const V3<T> d1 = cross(r, v3(B[3], B[4], B[5]));
+    const V3<T> d2 = cross(r, v3(B[6], B[7], B[8]));
+    // F = B2 r^ : row i = (row i of B2) x r
+    const V3<T> f0 = cross(v3(B2[0], B2[1], B2[2]), r);
+    const V3<T> f1 = cross(v3(B2[3], B2[4], B2[5]), r);
+    const V3<T> f2 = cross(v3(B2[6], B2[7], B2[8]), r);
+    // A + D - F (symmetric in exact arithmetic; D[i][j] = d_j.i)
+    out.A[0] = A[0] + d0.x - f0.x;
+    out.A[1] = A[1] + d1.y - f1.y;
+    out.A[2] = A[2] + d2.z - f2.z;
+    out.A[3] = A[3] + d1.x - f0.y;
+    out.A[4] = A[4] + d2.x - f0.z;
+    out.A[5] = A[5] + d2.y - f1.z;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out.B[k] = B2[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out.C[k] = C[k];
+}
+
+// Solve the 6x6 SPD system [[A, B], [B^T, C]] x = b by Cholesky (in registers).
+template <typename T>
+__device__ __forceinline__ void art_solve(const Art<T>& I, const T* b, T* x) {
+    T M[6][6];
+    M[0][0] = I.A[0]; M[1][1] = I.A[1]; M[2][2] = I.A[2];
+    M[0][1] = M[1][0] = I.A[3]; M[0][2] = M[2][0] = I.A[4]; M[1][2] = M[2][1] = I.A[5];
+    M[3][3] = I.C[0]; M[4][4] = I.C[1]; M[5][5] = I.C[2];
+    M[3][4] = M[4][3] = I.C[3]; M[3][5] = M[5][3] = I.C[4]; M[4][5] = M[5][4] = I.C[5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][3 + j] = M[3 + j][i] = I.B[3 * i + j];
+    T L[6][6];
+    T inv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            T s = M[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                const T d = sc_sqrt(s);
+                L[i][i] = d;
+                inv[i] = T(1) / d;
+            } else {
+                L[i][j] = s * inv[j];
+            }
+        }
+    }
+    T y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T s = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+        y[i] = s * inv[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        T s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
+        x[i] = s * inv[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Bounded TMA bulk copy of a global block into shared memory (cp.async.bulk +
+// mbarrier). Thread 0 issues; every thread waits with an iteration limit. Returns false
+// when the wait gave up (the caller reports MPPI_ERR_TIMEOUT and skips its work).
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ bool bulk_load_to_smem(void* smem_dst, const void* gmem_src, uint32_t bytes,
+                                                  uint64_t* mbar) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+            "l"(gmem_src), "r"(bytes), "r"(bar)
+            : "memory");
+    }
+    __syncthreads();
+    auto wait = [&](int limit) {
+        bool done = false;
+        for (int it = 0; it < limit && !done; ++it) {
+            uint32_t ok;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok)
+                : "r"(bar)
+                : "memory");
+            done = ok != 0;
+        }
+        return done;
+    };
+    // every thread of the block takes the same decision
+    if (__syncthreads_and(wait(1 << 22) ? 1 : 0)) return true;
+    // gave up: wait once more (bounded) for the copy in flight before the caller exits
+    wait(1 << 22);
+    __syncthreads();
+    return false;
+}
+
+// Status word written by kernels whose bounded waits gave up.
+constexpr uint32_t DEV_ERR_TMA_TIMEOUT = 1u;
+constexpr uint32_t DEV_ERR_QUEUE_TIMEOUT = 2u;
+constexpr uint32_t DEV_ERR_BAD_ITEM = 4u;
+
+}  // namespace mppi

@@ -1,0 +1,104 @@
+// Host-side internal interface shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mppi.h"
+#include "common.cuh"
+
+namespace mppi {
+
+constexpr int REDUCE_THREADS = 256;   // fixed: the weight reduction order depends on it
+constexpr int AVG_CHUNK = 64;         // samples per FP64 partial sum of the knot average
+constexpr int AVG_THREADS = 128;
+
+// Per-iteration weight information (device), written by the weights step.
+struct DevIterInfo {
+    double smin, smax, lse, ess;
+    int32_t best, nfinite, status, pad;
+};
+
+// Per-solve state of a context (device), reset at the start of each solve.
+struct DevSolve {
+    double best_cost;
+    int32_t best_index, best_iter, status, pad;
+    uint32_t iter_counter;   // Philox counter word 2 of the solve's first iteration
+    uint32_t pad2;
+    uint32_t dev_error;      // DEV_ERR_* bits from bounded device waits
+    uint32_t pad3;
+};
+
+struct SampleArgs {
+    const float* nominal;    // [E]
+    const float* sigma_row;  // [nk]
+    const DevModel<float>* model;
+    float* knots;            // [N][E]
+    const DevSolve* solve;   // iter_counter source (nullable -> iter_counter_override)
+    uint32_t iter_offset;    // added to the counter
+    uint32_t iter_counter_override;
+    uint32_t inst;
+    uint32_t seed_lo, seed_hi;
+    int N, nk, nj, has_limits;
+    float scale_q, scale_v, dtk;
+};
+
+template <typename T>
+struct RolloutArgs {
+    const DevModel<T>* model;
+    const double* x0;
+    const float* knots;   // [N][E]
+    T* costs;             // [N]
+    double* finals;       // [N][nx] nullable
+    uint32_t* status;     // DEV_ERR bits (nullable)
+    int N, H, nk;
+    T dt, dtk;
+};
+
+// launches (kernels.cu / rollout_*.cu)
+cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s);
+cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s);
+cudaError_t launch_rollout_warp_f64(const RolloutArgs<double>& a, int G, int block, cudaStream_t s);
+cudaError_t launch_rollout_thread_f32(const RolloutArgs<float>& a, int topology, int block, cudaStream_t s);
+bool thread_mapping_supported(int topology);
+cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, int block, cudaStream_t s);
+bool chain_mapping_supported(int topology);
+cudaError_t prepare_warp_f32();
+cudaError_t prepare_warp_f64();
+cudaError_t prepare_thread_f32();
+// weights of each chunk of AVG_CHUNK samples and their partial knot sums (reduce.cuh)
+cudaError_t launch_weights_average(const float* costs, const float* knots, int N, int E, double lambda, int normalize,
+                                   double* e_out, double* zq, double* partial, DevIterInfo* info, cudaStream_t s);
+// w = e / z and the iteration's lse / ESS (standalone weights entry point)
+cudaError_t launch_normalize_weights(const double* e, const double* zq, int N, double* w, DevIterInfo* info,
+                                     cudaStream_t s);
+// weighted average with given weights: chunk partials, then chunk totals
+cudaError_t launch_average_partial(const float* knots, const double* w, int N, int E, double* partial,
+                                   cudaStream_t s);
+cudaError_t launch_average_reduce(const double* partial, int nchunks, int E, double* out, cudaStream_t s);
+struct FinalizeArgs {
+    const double* partial;
+    const double* zq;
+    int nchunks, E, iter, iters, warm_from;
+    const float* knots;
+    const float* costs;
+    DevIterInfo* info;
+    DevSolve* solve;
+    float* nominal;     // next iteration's nominal (and the resident warm start at the end)
+    float* mean_out;    // [E]
+    float* best_out;    // [E]
+    mppi_result* result;
+};
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* best_out, int E, cudaStream_t s);
+cudaError_t launch_philox_words(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s);
+cudaError_t launch_dynamics_f32(const DevModel<float>* m, int n, const double* x, const double* tau, double* acc,
+                                cudaStream_t s);
+cudaError_t launch_dynamics_f64(const DevModel<double>* m, int n, const double* x, const double* tau, double* acc,
+                                cudaStream_t s);
+
+__host__ __device__ inline int num_chunks(int N) { return (N + AVG_CHUNK - 1) / AVG_CHUNK; }
+
+}  // namespace mppi

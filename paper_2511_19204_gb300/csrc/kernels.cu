@@ -1,0 +1,194 @@
+// Per-iteration kernels around the rollout: knot noise (Alg. 1 sampling + Eq. vel-clamp),
+// chunked weights with FP64 partial knot sums (Eqs. omega-weights / softmax_minmax,
+// Eq. update-nominal) and the iteration's finalize (log-sum-exp, mean, best tracking of
+// Sec. III-D).
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace mppi {
+
+// ------------------------------------------------------------------------------------
+// K1: knot noise. A block owns SPB samples: phase 1 draws one Philox block (4 words ->
+// 2 Box-Muller pairs) per thread into shared memory; phase 2 forms
+// theta = nominal + sigma_k * scale * eps per (knot, joint), clamps, and stores
+// position and velocity knots with consecutive joints on consecutive threads.
+// Counter = (e / 4, n, iteration counter, instance), key = (seed lo, seed hi).
+// ------------------------------------------------------------------------------------
+constexpr int SAMPLE_SPB = 8;
+constexpr int SAMPLE_THREADS = 256;
+
+__global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs a) {
+    extern __shared__ float eps[];  // [SPB][E]
+    const int E = a.nk * 2 * a.nj;
+    const int B4 = (E + 3) / 4;
+    const int n0 = blockIdx.x * SAMPLE_SPB;
+    const uint32_t it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
+    for (int idx = threadIdx.x; idx < SAMPLE_SPB * B4; idx += blockDim.x) {
+        const int nl = idx / B4, b = idx - nl * B4;
+        const int n = n0 + nl;
+        if (n >= a.N) continue;
+        float e4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (n > 0) {
+            const U4 w = philox4x32_10(U4{(uint32_t)b, (uint32_t)n, it, a.inst}, a.seed_lo, a.seed_hi);
+            box_muller<float>(w.x, w.y, &e4[0], &e4[1]);
+            box_muller<float>(w.z, w.w, &e4[2], &e4[3]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * b + i < E) eps[nl * E + 4 * b + i] = e4[i];
+    }
+    __syncthreads();
+    const int KJ = a.nk * a.nj;
+    for (int idx = threadIdx.x; idx < SAMPLE_SPB * KJ; idx += blockDim.x) {
+        const int nl = idx / KJ, rem = idx - nl * KJ;
+        const int n = n0 + nl;
+        if (n >= a.N) continue;
+        const int k = rem / a.nj, j = rem - k * a.nj;
+        const int eq = (2 * k) * a.nj + j, ev = eq + a.nj;
+        const float sg = a.sigma_row[k];
+        float q = a.nominal[eq] + sg * a.scale_q * eps[nl * E + eq];
+        float v = a.nominal[ev] + sg * a.scale_v * eps[nl * E + ev];
+        if (a.has_limits) {
+            const float lo = a.model->q_min[j + 1], hi = a.model->q_max[j + 1];
+            if (isfinite(lo) || isfinite(hi)) {
+                q = fminf(fmaxf(q, lo), hi);
+                const float room = fminf(hi - q, q - lo);
+                const float vmax = room / (a.dtk * 0.5f);
+                v = fminf(fmaxf(v, -vmax), vmax);
+            }
+        }
+        a.knots[(size_t)n * E + eq] = q;
+        a.knots[(size_t)n * E + ev] = v;
+    }
+}
+
+cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s) {
+    const int E = a.nk * 2 * a.nj;
+    const int grid = (a.N + SAMPLE_SPB - 1) / SAMPLE_SPB;
+    if (grid == 0) return cudaSuccess;
+    const size_t sm = (size_t)SAMPLE_SPB * E * sizeof(float);
+    sample_knots_kernel<<<grid, SAMPLE_THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// K3: weights and partial knot sums per chunk (grid = chunks x element tiles).
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(AVG_THREADS) weights_average_kernel(const float* __restrict__ costs,
+                                                                      const float* __restrict__ knots, int N, int E,
+                                                                      double lambda, int normalize, double* e_out,
+                                                                      double* zq, double* partial, DevIterInfo* info) {
+    chunk_weights_average(costs, knots, N, E, lambda, normalize, blockIdx.x, blockIdx.y, e_out, zq, partial, info);
+}
+
+cudaError_t launch_weights_average(const float* costs, const float* knots, int N, int E, double lambda, int normalize,
+                                   double* e_out, double* zq, double* partial, DevIterInfo* info, cudaStream_t s) {
+    const dim3 grid(num_chunks(N), (E + AVG_THREADS - 1) / AVG_THREADS);
+    if (grid.x == 0) return cudaSuccess;
+    weights_average_kernel<<<grid, AVG_THREADS, 0, s>>>(costs, knots, N, E, lambda, normalize, e_out, zq, partial, info);
+    return cudaGetLastError();
+}
+
+__global__ void normalize_weights_kernel(const double* __restrict__ e, const double* __restrict__ zq, int N,
+                                         double* __restrict__ w, DevIterInfo* info) {
+    __shared__ double s_z;
+    if (threadIdx.x == 0) {
+        double z = 0.0, q = 0.0;
+        total_zq(zq, num_chunks(N), &z, &q);
+        s_z = z;
+        const bool ok = info->status == MPPI_OK;
+        info->lse = ok ? log(z) : NAN;
+        info->ess = ok ? z * z / q : 0.0;
+    }
+    __syncthreads();
+    const double z = s_z;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+        w[n] = z > 0.0 ? e[n] / z : 0.0;
+}
+
+cudaError_t launch_normalize_weights(const double* e, const double* zq, int N, double* w, DevIterInfo* info,
+                                     cudaStream_t s) {
+    normalize_weights_kernel<<<1, 256, 0, s>>>(e, zq, N, w, info);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// K4 (standalone): FP64 average with given weights, in two deterministic stages:
+// per-chunk partial sums over 64 samples, then chunk totals in increasing order.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(AVG_THREADS) average_partial_kernel(const float* __restrict__ knots,
+                                                                      const double* __restrict__ w, int N, int E,
+                                                                      double* __restrict__ partial) {
+    const int c = blockIdx.x;
+    const int e = blockIdx.y * AVG_THREADS + threadIdx.x;
+    if (e >= E) return;
+    const int n0 = c * AVG_CHUNK, n1 = min(N, n0 + AVG_CHUNK);
+    double acc = 0.0;
+    for (int n = n0; n < n1; ++n) acc = fma(w[n], (double)knots[(size_t)n * E + e], acc);
+    partial[(size_t)c * E + e] = acc;
+}
+
+cudaError_t launch_average_partial(const float* knots, const double* w, int N, int E, double* partial,
+                                   cudaStream_t s) {
+    const dim3 grid(num_chunks(N), (E + AVG_THREADS - 1) / AVG_THREADS);
+    if (grid.x == 0) return cudaSuccess;
+    average_partial_kernel<<<grid, AVG_THREADS, 0, s>>>(knots, w, N, E, partial);
+    return cudaGetLastError();
+}
+
+__global__ void average_reduce_kernel(const double* __restrict__ partial, int nchunks, int E, double* out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+        out[e] = chunk_total(partial, nchunks, E, e);
+}
+
+cudaError_t launch_average_reduce(const double* partial, int nchunks, int E, double* out, cudaStream_t s) {
+    average_reduce_kernel<<<(E + 255) / 256, 256, 0, s>>>(partial, nchunks, E, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Iteration bookkeeping.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs a) { finalize_iteration(a); }
+
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+    finalize_kernel<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void solve_begin_kernel(DevSolve* solve, const float* nominal, float* best_out, int E) {
+    if (threadIdx.x == 0) {
+        solve->best_cost = INFINITY;
+        solve->best_index = -1;
+        solve->best_iter = -1;
+        solve->status = MPPI_OK;
+    }
+    for (int e = threadIdx.x; e < E; e += blockDim.x) best_out[e] = nominal[e];
+}
+
+cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* best_out, int E, cudaStream_t s) {
+    solve_begin_kernel<<<1, 256, 0, s>>>(solve, nominal, best_out, E);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Philox words for a list of counters (bit-exactness checks).
+// ------------------------------------------------------------------------------------
+__global__ void philox_words_kernel(int n, const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                                    uint32_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const U4 w = philox4x32_10(U4{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]}, k0, k1);
+    out[4 * i] = w.x;
+    out[4 * i + 1] = w.y;
+    out[4 * i + 2] = w.z;
+    out[4 * i + 3] = w.w;
+}
+
+cudaError_t launch_philox_words(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    philox_words_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, ctr, k0, k1, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mppi

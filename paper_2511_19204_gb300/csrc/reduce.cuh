@@ -1,0 +1,212 @@
+// Cost -> weight reduction (Sec. III-C Eqs. omega-weights / softmax_minmax) and the
+// FP64 knot average (Eq. update-nominal), shared by the per-iteration kernels and the
+// persistent batched kernel so both produce identical bits.
+//
+// Layout of the work: samples are cut into chunks of AVG_CHUNK. For chunk c a block
+//   1. scans all N FP32 costs for S_min, S_max, the argmin (ties -> lowest index) and the
+//      number of finite costs (cheap; every block does it redundantly),
+//   2. forms the unnormalised weights e_n = exp(-S_hat_n / lambda) of its own samples in
+//      FP64 (every e_n <= 1 and the argmin's e is exactly 1, so nothing overflows),
+//   3. writes P_c[e] = sum_{n in c} e_n theta_{n,e} (FP64, increasing n) and, from the
+//      first element tile, z_c = sum e_n and q_c = sum e_n^2.
+// The iteration's finalize then forms z = sum_c z_c, lse = log z, ESS = z^2 / sum q_c and
+// the mean sum_c P_c[e] / z. Each sum runs in a fixed order, so results depend only on
+// AVG_CHUNK, never on the grid or on scheduling.
+#pragma once
+#include "internal.h"
+
+namespace mppi {
+
+struct MinMax {
+    float smin, smax;
+    int best, nfinite;
+};
+
+// Block-wide scan of N costs; every thread receives the result. Any block size that is a
+// multiple of 32 and at most 1024.
+__device__ __forceinline__ MinMax block_minmax(const float* __restrict__ costs, int N) {
+    __shared__ float s_min[32], s_max[32];
+    __shared__ int s_arg[32], s_cnt[32];
+    __shared__ MinMax s_res;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    float mn = INFINITY, mx = -INFINITY;
+    int arg = 0x7fffffff, cnt = 0;
+    for (int n = t; n < N; n += blockDim.x) {
+        const float c = costs[n];
+        if (isfinite(c)) {
+            ++cnt;
+            if (c < mn) {
+                mn = c;
+                arg = n;
+            }
+            mx = fmaxf(mx, c);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float omn = __shfl_xor_sync(0xffffffffu, mn, off);
+        const int oarg = __shfl_xor_sync(0xffffffffu, arg, off);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (omn < mn || (omn == mn && oarg < arg)) {
+            mn = omn;
+            arg = oarg;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        s_min[wid] = mn;
+        s_max[wid] = mx;
+        s_arg[wid] = arg;
+        s_cnt[wid] = cnt;
+    }
+    __syncthreads();
+    if (t == 0) {
+        MinMax r{INFINITY, -INFINITY, 0x7fffffff, 0};
+        for (int i = 0; i < nw; ++i) {
+            if (s_min[i] < r.smin || (s_min[i] == r.smin && s_arg[i] < r.best)) {
+                r.smin = s_min[i];
+                r.best = s_arg[i];
+            }
+            r.smax = fmaxf(r.smax, s_max[i]);
+            r.nfinite += s_cnt[i];
+        }
+        if (r.nfinite == 0) r.best = -1;
+        s_res = r;
+    }
+    __syncthreads();
+    return s_res;
+}
+
+// Unnormalised weight of one cost given the scan (0 for non-finite costs).
+__device__ __forceinline__ double unnorm_weight(float c, const MinMax& mm, double lambda, int normalize) {
+    if (!isfinite(c)) return 0.0;
+    const double range = (double)mm.smax - (double)mm.smin;
+    const double scale = normalize == MPPI_NORM_MINMAX ? (range > 0.0 ? 1.0 / range : 0.0) : 1.0;
+    return exp(-(((double)c - (double)mm.smin) * scale) / lambda);
+}
+
+// One (chunk, element tile) block: weights of the chunk and its partial knot sums.
+// e_out (nullable) [N], zq [nchunks][2], partial [nchunks][E]. Element tile ey covers
+// elements [ey * blockDim.x, (ey + 1) * blockDim.x).
+__device__ __forceinline__ void chunk_weights_average(const float* __restrict__ costs, const float* __restrict__ knots,
+                                                      int N, int E, double lambda, int normalize, int c, int ey,
+                                                      double* __restrict__ e_out, double* __restrict__ zq,
+                                                      double* __restrict__ partial, DevIterInfo* __restrict__ info) {
+    __shared__ double s_e[AVG_CHUNK];
+    const MinMax mm = block_minmax(costs, N);
+    const int n0 = c * AVG_CHUNK;
+    const int cn = min(AVG_CHUNK, N - n0);
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+        const double e = mm.nfinite > 0 ? unnorm_weight(costs[n0 + i], mm, lambda, normalize) : 0.0;
+        s_e[i] = e;
+        if (e_out && ey == 0) e_out[n0 + i] = e;
+    }
+    __syncthreads();
+    const int el = ey * blockDim.x + threadIdx.x;
+    if (el < E) {
+        double acc = 0.0;
+        for (int i = 0; i < cn; ++i) acc = fma(s_e[i], (double)knots[(size_t)(n0 + i) * E + el], acc);
+        partial[(size_t)c * E + el] = acc;
+    }
+    if (ey == 0 && threadIdx.x == 0) {
+        double z = 0.0, q = 0.0;
+        for (int i = 0; i < cn; ++i) {
+            z += s_e[i];
+            q += s_e[i] * s_e[i];
+        }
+        zq[2 * c] = z;
+        zq[2 * c + 1] = q;
+        if (c == 0) {
+            info->smin = mm.nfinite ? (double)mm.smin : NAN;
+            info->smax = mm.nfinite ? (double)mm.smax : NAN;
+            info->best = mm.best;
+            info->nfinite = mm.nfinite;
+            info->status = mm.nfinite ? MPPI_OK : MPPI_ERR_ALL_COSTS_NONFINITE;
+        }
+    }
+    __syncthreads();
+}
+
+// z = sum of the chunks' z_c (increasing c), and sum of q_c.
+__device__ __forceinline__ void total_zq(const double* __restrict__ zq, int nchunks, double* z, double* q) {
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+        a += zq[2 * c];
+        b += zq[2 * c + 1];
+    }
+    *z = a;
+    *q = b;
+}
+
+// Sum of the partials of element e over chunks in increasing order.
+__device__ __forceinline__ double chunk_total(const double* __restrict__ partial, int nchunks, int E, int e) {
+    double acc = 0.0;
+    for (int c = 0; c < nchunks; ++c) acc += partial[(size_t)c * E + e];
+    return acc;
+}
+
+// End of one iteration (one block, any size): lse and ESS, mean = sum_c P_c / z,
+// best-trajectory tracking over the solve (Sec. III-D), next nominal, and at the last
+// iteration the outputs, the resident warm start and the noise counter.
+__device__ __forceinline__ void finalize_iteration(const FinalizeArgs& a) {
+    __shared__ int s_update;
+    __shared__ double s_z;
+    const int t = threadIdx.x;
+    DevIterInfo inf = *a.info;
+    const bool ok = inf.status == MPPI_OK;
+    if (t == 0) {
+        double z = 0.0, q = 0.0;
+        total_zq(a.zq, a.nchunks, &z, &q);
+        s_z = z;
+        inf.lse = ok ? log(z) : NAN;
+        inf.ess = ok ? z * z / q : 0.0;
+        a.info->lse = inf.lse;
+        a.info->ess = inf.ess;
+        int upd = 0;
+        if (ok) {
+            const double cb = (double)a.costs[inf.best];
+            if (cb < a.solve->best_cost) {
+                upd = 1;
+                a.solve->best_cost = cb;
+                a.solve->best_index = inf.best;
+                a.solve->best_iter = a.iter;
+            }
+        } else {
+            a.solve->status = inf.status;
+        }
+        s_update = upd;
+    }
+    __syncthreads();
+    const double z = s_z;
+    const bool last = a.iter == a.iters - 1;
+    for (int e = t; e < a.E; e += blockDim.x) {
+        float m = a.nominal[e];
+        if (ok) m = (float)(chunk_total(a.partial, a.nchunks, a.E, e) / z);
+        if (s_update) a.best_out[e] = a.knots[(size_t)inf.best * a.E + e];
+        if (last) a.mean_out[e] = m;
+        a.nominal[e] = m;
+    }
+    __syncthreads();
+    if (last) {
+        if (a.warm_from == MPPI_WARM_BEST && a.solve->best_index >= 0)
+            for (int e = t; e < a.E; e += blockDim.x) a.nominal[e] = a.best_out[e];
+        if (t == 0) {
+            mppi_result r;
+            r.cost_min = inf.smin;
+            r.cost_max = inf.smax;
+            r.best_cost = a.solve->best_cost;
+            r.ess = inf.ess;
+            r.lse = inf.lse;
+            r.best_index = a.solve->best_index;
+            r.best_iter = a.solve->best_iter;
+            r.n_finite = inf.nfinite;
+            r.status = a.solve->status;
+            *a.result = r;
+            a.solve->iter_counter += (uint32_t)a.iters;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace mppi

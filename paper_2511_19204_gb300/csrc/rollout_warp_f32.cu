@@ -1,0 +1,16 @@
+// FP32 product instantiations of the warp-per-sample rollout and dynamics kernels.
+#include "internal.h"
+#include "rollout_warp.cuh"
+
+namespace mppi {
+cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s) {
+    if (G == 32) return launch_rollout_warp_t<float, 32>(a, block, s);
+    if (G == 16) return launch_rollout_warp_t<float, 16>(a, block, s);
+    return cudaErrorInvalidValue;
+}
+cudaError_t launch_dynamics_f32(const DevModel<float>* m, int n, const double* x, const double* tau, double* acc,
+                                cudaStream_t s) {
+    return launch_dynamics_t<float>(m, n, x, tau, acc, s);
+}
+cudaError_t prepare_warp_f32() { return prepare_warp_kernels<float>(); }
+}  // namespace mppi

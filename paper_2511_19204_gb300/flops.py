@@ -1,0 +1,43 @@
+"""Algorithmic floating-point work of one rollout step of one sample (one unit).
+
+Counted from the formulation the kernels evaluate (articulated-body algorithm with
+spatial quantities split into 3-vector / 3x3 blocks, symmetric 6x6 inertias stored as
+21 numbers), per primitive, with a fused multiply-add counted as 2 flops and an add,
+multiply, divide, square root, sine/cosine pair or arctangent as 1. The same numbers
+are derived in the design notes; they do not depend on the lane mapping.
+
+Per joint body (revolute):
+  Hermite setpoint + derivative (Eq. hermite_segment) + PD (Eq. pd-controller)   55
+  joint rotation (sincos + Rodrigues)                                            31
+  pass 1: world rotation 45, origin 18, angular 21 and linear 27 velocity       111
+  velocity product c                                                             21
+  bias force v x* (I v)                                                          78
+  pass 2: U, D, u (28), articulated inertia update (63), Ia c (66),
+          bias update (24), congruence X^T Ia X (342), force transform (42)     565
+  child -> parent accumulation                                                   27
+  pass 3: acceleration transform (48), joint acceleration (13), update (6)       67
+  semi-implicit Euler                                                             4
+  effort term tau^2                                                               2
+Per contact point in penetration: position 18, velocity 27, normal force 4,
+  regularised friction 12, body-frame force 15, moment 12                       88
+Per floating base: rotation from quaternion 25, bias 78, 6x6 Cholesky solve 161,
+  gravity 6, integration 94 (velocities 12, position 21, quaternion exponential
+  and product 61), running cost 42                                              406
+"""
+from __future__ import annotations
+
+PER_JOINT = 55 + 31 + 111 + 21 + 78 + 565 + 27 + 67 + 4 + 2
+PER_CONTACT = 18 + 27 + 4 + 12 + 15 + 12
+PER_BASE = 25 + 78 + 161 + 6 + 94 + 42
+
+
+def flops_per_step(model, contacts_active=None) -> int:
+    """Flops of one step of one sample. ``contacts_active`` defaults to every contact
+    point (the standing / walking regime); pass a number for another regime."""
+    nc = model.nc if contacts_active is None else contacts_active
+    return PER_JOINT * model.nj + PER_CONTACT * nc + PER_BASE
+
+
+def fp32_peak_tflops(sms: int = 152, clock_mhz: float = 2070.0) -> float:
+    """FP32 ALU peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return sms * 128 * 2 * clock_mhz * 1e6 / 1e12

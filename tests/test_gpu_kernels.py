@@ -1,0 +1,253 @@
+"""Kernel-level parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 product unless stated):
+  Philox words                       bit-exact
+  knot noise                         |d| <= 4 ulp(FP32)|sigma s eps| + 2 ulp(theta) + 1e-6
+  single-step state derivative       1e-5 relative (to the largest component)
+  50-step contact-free rollouts      1e-4 relative (costs, final states)
+  FP64 check build                   1e-9 relative
+  weights / average (FP64 on both)   1e-12 relative
+"""
+import numpy as np
+import pytest
+
+from paper_2511_19204_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+F32_ULP = 2.0 ** -23
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2511_19204_gb300 import build, mppi
+    build.build()
+    mppi.load()
+    return mppi
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ------------------------------------------------------------------------------------
+# Philox / noise
+# ------------------------------------------------------------------------------------
+def test_philox_words_bit_exact(M, orc):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    ctr[2] = [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]
+    for key in ([0, 0], [0xFFFFFFFF, 0xFFFFFFFF], [0xA4093822, 0x299F31D0], [12345, 678]):
+        got = M.philox_words(ctr, key)
+        for i in range(0, 4096, 97):
+            assert list(got[i]) == list(orc.philox(ctr[i], key)), i
+        for i in range(3):
+            assert list(got[i]) == list(orc.philox(ctr[i], key))
+
+
+@pytest.mark.parametrize("name,nk,n", [("quadruped", 4, 37), ("quadruped", 6, 300), ("humanoid", 7, 50),
+                                       ("humanoid", 8, 129)])
+def test_sample_knots_match_oracle(M, orc, name, nk, n):
+    m = S.MODELS[name]()
+    H, dt = 200, 0.005
+    sig = S.linear_sigma(nk, 2)
+    sig[1] *= 0.5
+    nom = S.random_knots(m, 1, nk, seed=3, scale=0.2)[0]
+    mod = M.Model(m)
+    c = M.Controller(mod, n, H, nk, 0.1, sig, iters=2, dt=dt, seed=0xABCDEF0123, instance=7,
+                     mapping=M.MPPI_MAP_WARP)
+    nom32 = nom.astype(np.float32)
+    for it, ctrv in ((0, 5), (1, 77)):
+        got = c.sample_knots(it, ctrv, nom32)
+        ref = orc.sample_knots(m.nj, nk, n, H, dt, nom32.astype(np.float64), sig[it], seed=0xABCDEF0123,
+                               iter_ctr=ctrv, inst=7)
+        np.testing.assert_array_equal(got[0], nom32)            # sample 0 is the nominal
+        dtk = H * dt / (nk - 1)
+        scale = np.array([1.0, 1.0 / dtk])[None, None, :, None]
+        dev = np.abs(ref - nom32.astype(np.float64)) + 0 * scale
+        tol = 4 * F32_ULP * dev + 2 * F32_ULP * np.abs(ref) + 1e-6
+        assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
+
+
+def test_sample_knots_clamp(M, orc):
+    lo, hi = np.array([-0.3, 0.2, -2.0]), np.array([0.3, 1.5, -0.8])
+    m = S.quadruped(limits=(lo, hi))
+    nk, n, H, dt = 5, 200, 100, 0.01
+    sig = S.linear_sigma(nk, 1) * 4
+    nom = S.nominal_knots(m, nk)
+    c = M.Controller(M.Model(m), n, H, nk, 0.1, sig, iters=1, dt=dt, seed=9, mapping=M.MPPI_MAP_WARP)
+    got = c.sample_knots(0, 3, nom.astype(np.float32)).astype(np.float64)
+    ref = orc.sample_knots(m.nj, nk, n, H, dt, nom, sig[0], seed=9, iter_ctr=3, q_min=m.q_min, q_max=m.q_max)
+    assert np.max(np.abs(got - ref)) < 2e-5
+    q, v = got[:, :, 0, :], got[:, :, 1, :]
+    assert np.all(q >= m.q_min - 1e-6) and np.all(q <= m.q_max + 1e-6)
+    dtk = H * dt / (nk - 1)
+    room = np.minimum(m.q_max - q, q - m.q_min)
+    assert np.all(np.abs(v) <= 2 * room / dtk + 1e-5)
+
+
+# ------------------------------------------------------------------------------------
+# Dynamics
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["quadruped", "humanoid", "chain2", "branch3", "free_body", "pendulum",
+                                  "point_mass"])
+def test_forward_dynamics(M, orc, name):
+    m = S.MODELS[name]()
+    rng = np.random.default_rng(11)
+    xs = np.stack([S.random_state(m, 50 + i, height=0.3 if i % 2 else 0.05) for i in range(24)])
+    tau = rng.normal(scale=5.0, size=(24, m.nj))
+    mod = M.Model(m)
+    ref = np.stack([orc.forward_dynamics(m, xs[i], tau[i]) for i in range(24)])
+    got32 = mod.forward_dynamics(xs, tau)
+    got64 = mod.forward_dynamics(xs, tau, fp64=True)
+    for i in range(24):
+        assert _rel(got64[i], ref[i]) < 1e-9, (i, _rel(got64[i], ref[i]))
+        assert _rel(got32[i], ref[i]) < 1e-5, (i, _rel(got32[i], ref[i]))
+
+
+def _lifted(m, seed):
+    x = S.standing_state(m, jitter=0.05, seed=seed)
+    x[2] = 3.0 + 0.1 * (seed % 3)
+    rng = np.random.default_rng(seed)
+    x[m.nq:m.nq + 6] = rng.normal(scale=0.3, size=6)
+    return x
+
+
+@pytest.mark.parametrize("name,mapping", [("quadruped", 0), ("quadruped", 1), ("quadruped", 2), ("humanoid", 0)])
+def test_rollout_contact_free(M, orc, name, mapping):
+    # 50 steps in the air: no contact ever acts, so FP32 stays within 1e-4 of FP64
+    m = S.MODELS[name]()
+    nk, H, dt, n = 4, 50, 0.01, 40
+    kn = S.random_knots(m, n, nk, seed=4, scale=0.2).astype(np.float32)
+    x0 = _lifted(m, 1)
+    c = M.Controller(M.Model(m), n, H, nk, 0.1, S.linear_sigma(nk), dt=dt, mapping=mapping)
+    costs, fins = c.rollout_explicit(x0, kn, finals=True)
+    ref_c, ref_f = orc.rollout_batch(m, x0, kn.astype(np.float64), H, dt, finals=True)
+    _, cpos = orc.positions(m, ref_f[0])
+    assert cpos[:, 2].min() > 0.0
+    assert _rel(costs, ref_c) < 1e-4
+    for i in range(n):
+        assert _rel(fins[i], ref_f[i]) < 1e-4, i
+    if mapping == 2:
+        return
+    c.set_fp64_check(True)
+    costs64, fins64 = c.rollout_explicit(x0, kn, finals=True)
+    assert _rel(costs64, ref_c) < 1e-9
+    for i in range(n):
+        assert _rel(fins64[i], ref_f[i]) < 1e-9, i
+
+
+@pytest.mark.parametrize("cfg", ["scale", "humanoid", "plain"])
+def test_rollout_with_contact_fp64_check(M, orc, cfg):
+    # contact rollouts of the configurations: the FP64 check build within 1e-9 where the
+    # dynamics are well conditioned (dt = 0.005), and within the oracle's own FP64
+    # sensitivity envelope at dt = 0.01; the FP32 product's cost error is reported and
+    # bounded by 1e-3 (median) or the FP32 envelope
+    from _parity import rollout_envelope
+    if cfg == "scale":
+        p = S.scale_quadruped(n=64)
+    elif cfg == "humanoid":
+        p = S.humanoid_problem(n=32)
+        p.horizon = 100
+    else:
+        p = S.plain_quadruped()
+    m = p.model
+    kn = orc.sample_knots(m.nj, p.nk, p.n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed)
+    kn32 = kn.astype(np.float32)
+    kn64 = kn32.astype(np.float64)
+    (ref_c, ref_f), env_c64, env_f64 = rollout_envelope(m, p.state, kn64, p.horizon, p.dt, 1e-15)
+    c = M.Controller.from_problem(M.Model(m), p, mapping=M.MPPI_MAP_WARP)
+    c.set_fp64_check(True)
+    c64, f64 = c.rollout_explicit(p.state, kn32, finals=True)
+    scale_f = np.max(np.abs(ref_f), axis=1)
+    err_f = np.max(np.abs(f64 - ref_f), axis=1) / scale_f
+    err_c = np.abs(c64 - ref_c) / np.abs(ref_c)
+    print(f"{cfg}: FP64 check build rel. error costs max {err_c.max():.2e}, final states max {err_f.max():.2e}; "
+          f"oracle FP64 envelope max {np.max(env_f64 / scale_f):.2e}")
+    if cfg == "plain":
+        assert np.all(np.abs(f64 - ref_f).max(axis=1) <= np.maximum(1e-9 * scale_f, 10 * env_f64))
+        assert np.median(err_f) < 1e-9
+    else:
+        assert err_c.max() < 1e-9 and err_f.max() < 1e-9
+    c.set_fp64_check(False)
+    if m.name == "quadruped":
+        c.set_mapping(M.MPPI_MAP_CHAIN)
+    c32 = c.rollout_explicit(p.state, kn32)
+    err = np.abs(c32 - ref_c) / np.abs(ref_c)
+    print(f"{cfg}: FP32 contact-rollout cost rel. error median {np.median(err):.2e} max {err.max():.2e}")
+    assert np.median(err) < 1e-3
+    if cfg != "plain":
+        assert err.max() < 1e-3
+    else:
+        # chaotic: FP32 rounding of every step is amplified ~1e5-fold, so most samples
+        # agree closely and a tail does not; bound the bulk and the tail separately
+        _, env_c32, _ = rollout_envelope(m, p.state, kn64, p.horizon, p.dt, 1e-6, draws=8)
+        env = env_c32 / np.abs(ref_c)
+        print(f"plain: oracle FP32-level envelope median {np.median(env):.2e} max {env.max():.2e}")
+        assert np.median(err) <= 10 * np.median(env) + 1e-6
+        assert err.max() <= 10 * env.max() + 1e-6
+
+
+@pytest.mark.parametrize("n,block", [(1, 0), (37, 32), (300, 64), (1000, 128), (2049, 256)])
+def test_mappings_agree(M, orc, n, block):
+    # every rollout mapping runs the same algorithm: on the well-conditioned dt = 0.005
+    # workload they agree with each other and with the oracle to FP32 accuracy
+    p = S.scale_quadruped(n=n)
+    p.horizon = 120
+    kn = orc.sample_knots(p.model.nj, p.nk, n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed).astype(np.float32)
+    c = M.Controller.from_problem(M.Model(p.model), p, mapping=0)
+    out = {}
+    for mapping in (0, 1, 2):
+        c.set_mapping(mapping, block if (block or mapping != 1) else 0)
+        out[mapping], fin = c.rollout_explicit(p.state, kn, finals=True)
+        assert np.all(np.isfinite(fin))
+    idx = np.arange(n) if n <= 64 else np.r_[0:16, n - 16:n]
+    ref = orc.rollout_batch(p.model, p.state, kn.astype(np.float64)[idx], p.horizon, p.dt)
+    for mapping in (0, 1, 2):
+        err = np.abs(out[mapping][idx] - ref) / np.abs(ref)
+        assert err.max() < 1e-4, (mapping, err.max())
+        assert np.max(np.abs(out[mapping] - out[0]) / np.abs(out[0])) < 1e-4
+
+
+# ------------------------------------------------------------------------------------
+# Weights and average
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,norm", [(1, 0), (7, 0), (256, 0), (1000, 1), (8192, 0), (8193, 0)])
+def test_weights_match_oracle(M, orc, n, norm):
+    rng = np.random.default_rng(n)
+    c = rng.uniform(100, 900, size=n).astype(np.float32)
+    if n > 10:
+        c[3] = np.nan
+        c[5] = np.inf
+        c[n // 2] = c.min()        # a tie: lowest index wins
+    st, w, info = M.weights(c, 0.1 if norm == 0 else 50.0, norm)
+    st_o, w_o, info_o = orc.weights(c.astype(np.float64), 0.1 if norm == 0 else 50.0, norm)
+    assert st == st_o == 0
+    np.testing.assert_allclose(w, w_o, rtol=1e-12, atol=1e-300)
+    assert info["best_index"] == info_o["best"]
+    assert info["n_finite"] == info_o["n_finite"]
+    assert info["ess"] == pytest.approx(info_o["ess"], rel=1e-12)
+    assert info["lse"] == pytest.approx(info_o["lse"], rel=1e-12, abs=1e-14)
+
+
+def test_weights_all_non_finite(M):
+    st, w, info = M.weights(np.array([np.nan, np.inf, -np.inf], np.float32), 0.1)
+    assert st == -3 and np.all(w == 0) and info["best_index"] == -1
+
+
+@pytest.mark.parametrize("n,E", [(1, 48), (64, 48), (65, 144), (1000, 336), (8192, 144)])
+def test_average_matches_oracle(M, orc, n, E):
+    rng = np.random.default_rng(E + n)
+    kn = rng.normal(size=(n, E)).astype(np.float32)
+    w = rng.random(n)
+    w /= w.sum()
+    got = M.average(kn, w)
+    ref = orc.average(kn.astype(np.float64), w)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14)
+    # exact on a rational case
+    kn2 = np.array([[1.0, -2.0, 4.0], [3.0, 0.5, 8.0]], np.float32)
+    np.testing.assert_array_equal(M.average(kn2, np.array([0.25, 0.75])), 0.25 * kn2[0] + 0.75 * kn2[1])
