@@ -1,0 +1,671 @@
+// Batched solves: many independent MPC instances (uneven model, K, H, knots, lambda,
+// iterations) in one persistent kernel that walks a device work queue.
+//
+// Items are ROLLOUT(instance, tile) and REDUCE(instance, chunk). A ROLLOUT block draws
+// its tile's knots (Alg. 1 sampling) and rolls them out with the instance's mapping; the
+// last tile of an instance publishes its REDUCE items (weights and FP64 partial knot sums
+// per chunk of AVG_CHUNK samples); the last REDUCE item runs the iteration's finalize and
+// publishes the next iteration's ROLLOUT tiles. Every step calls the same device
+// functions as the per-instance kernels, so each instance's result is bit-identical to
+// its mppi_solve result.
+//
+// Progress needs no co-residency: a block waits only for an item whose producer is a
+// block that has already taken and finished its own item and publishes without waiting.
+// Every wait is bounded by the global timer and sets an error word when it gives up.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <list>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "capi_internal.h"
+#include "noise.cuh"
+#include "reduce.cuh"
+#include "rollout_chain.cuh"
+
+namespace mppi {
+
+constexpr int BATCH_THREADS = 256;
+constexpr int ITEM_ROLLOUT = 1;
+constexpr int ITEM_REDUCE = 2;
+
+struct BatchInst {
+    const DevModel<float>* model;
+    const double* x0;
+    float* knots;
+    float* costs;
+    double* zq;
+    double* partial;
+    float* nominal;
+    float* mean;
+    float* best;
+    const float* sigma;
+    DevIterInfo* info;
+    DevSolve* solve;
+    mppi_result* result;
+    double lambda;
+    int N, H, nk, nj, E, iters, mapping, tile, ntiles, nchunks, normalize, warm_from, has_limits;
+    float dt, dtk, scale_q, scale_v;
+    uint32_t inst, seed_lo, seed_hi;
+    // packed host <-> device exchange
+    int in_off;    // offset (bytes) of this instance's input record in the packed input
+    int out_off;   // offset (bytes) of this instance's output record in the packed output
+};
+
+struct InstCounters {
+    int it, done_roll, done_red, pad;
+};
+
+struct QueueItem {
+    int type, inst, idx;
+    volatile int ready;
+};
+
+struct BatchQueue {
+    int head, append, total, nprefill;
+    uint32_t error, pad0, pad1, pad2;
+};
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bulk copy into shared memory with a persistent mbarrier (phase parity flips each use).
+__device__ __forceinline__ bool bulk_load_phase(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* mbar,
+                                                uint32_t phase) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    __syncthreads();  // everyone is done with the previous contents
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+            "l"(gsrc), "r"(bytes), "r"(bar)
+            : "memory");
+    }
+    auto wait = [&](int limit) {
+        bool done = false;
+        for (int i = 0; i < limit && !done; ++i) {
+            uint32_t ok;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok)
+                : "r"(bar), "r"(phase)
+                : "memory");
+            done = ok != 0;
+        }
+        return done;
+    };
+    if (__syncthreads_and(wait(1 << 22) ? 1 : 0)) return true;
+    wait(1 << 22);
+    __syncthreads();
+    return false;
+}
+
+// Publish `count` items of one type for instance `inst` (whole block).
+__device__ __forceinline__ void publish(QueueItem* items, BatchQueue* q, int type, int inst, int count) {
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = atomicAdd(&q->append, count);
+    __syncthreads();
+    const int base = s_base;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        if (base + k >= q->total) continue;  // cannot happen with a consistent plan
+        items[base + k].type = type;
+        items[base + k].inst = inst;
+        items[base + k].idx = k;
+    }
+    __threadfence();
+    __syncthreads();
+    for (int k = threadIdx.x; k < count; k += blockDim.x)
+        if (base + k < q->total) items[base + k].ready = 1;
+    __threadfence();
+    __syncthreads();
+}
+
+__device__ __forceinline__ FinalizeArgs finalize_args(const BatchInst& I, int it) {
+    FinalizeArgs f;
+    f.partial = I.partial;
+    f.zq = I.zq;
+    f.nchunks = I.nchunks;
+    f.E = I.E;
+    f.iter = it;
+    f.iters = I.iters;
+    f.warm_from = I.warm_from;
+    f.knots = I.knots;
+    f.costs = I.costs;
+    f.info = I.info;
+    f.solve = I.solve;
+    f.nominal = I.nominal;
+    f.mean_out = I.mean;
+    f.best_out = I.best;
+    f.result = I.result;
+    return f;
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+    persistent_kernel(const BatchInst* __restrict__ insts, InstCounters* ctr, QueueItem* items, BatchQueue* q,
+                      uint64_t budget_ns) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ int s_idx;
+    __shared__ int s_type, s_inst, s_item, s_last;
+    __shared__ const void* s_loaded;
+    DevModel<float>* M = reinterpret_cast<DevModel<float>*>(smem);
+    float* work = reinterpret_cast<float*>(smem + sizeof(DevModel<float>));
+    const uint64_t t0 = globaltimer_ns();
+    uint32_t phase = 0;
+    if (threadIdx.x == 0) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_loaded = nullptr;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int idx = atomicAdd(&q->head, 1);
+            int type = 0;
+            if (idx < q->total) {
+                // wait (bounded) until the item is published
+                while (items[idx].ready == 0) {
+                    if (globaltimer_ns() - t0 > budget_ns) {
+                        atomicOr(&q->error, DEV_ERR_QUEUE_TIMEOUT);
+                        type = -1;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                __threadfence();
+                if (type == 0) {
+                    const volatile QueueItem* vi = items + idx;
+                    type = vi->type;
+                    s_inst = vi->inst;
+                    s_item = vi->idx;
+                }
+            }
+            s_idx = idx;
+            s_type = type;
+        }
+        __syncthreads();
+        const int type = s_type;
+        if (type != ITEM_ROLLOUT && type != ITEM_REDUCE) {
+            if (type > 0 && threadIdx.x == 0) atomicOr(&q->error, DEV_ERR_BAD_ITEM);
+            break;
+        }
+        const int ii = s_inst;
+        const BatchInst& I = insts[ii];
+        const int it = *reinterpret_cast<volatile int*>(&ctr[ii].it);
+        if (type == ITEM_ROLLOUT) {
+            if (s_loaded != (const void*)I.model) {
+                const bool ok = bulk_load_phase(M, I.model, (uint32_t)sizeof(DevModel<float>), &mbar, phase);
+                phase ^= 1u;
+                if (!ok) {
+                    if (threadIdx.x == 0) atomicOr(&q->error, DEV_ERR_TMA_TIMEOUT);
+                    break;
+                }
+                if (threadIdx.x == 0) s_loaded = I.model;
+                __syncthreads();
+            }
+            const int n0 = s_item * I.tile;
+            const int cnt = min(I.tile, I.N - n0);
+            // knots of this tile (Alg. 1 sampling), NOISE_SPB samples at a time
+            NoiseParams np;
+            np.nominal = I.nominal;
+            np.sigma_row = I.sigma + (size_t)it * I.nk;
+            np.model = M;
+            np.knots = I.knots;
+            np.it = *reinterpret_cast<volatile uint32_t*>(&I.solve->iter_counter) + (uint32_t)it;
+            np.inst = I.inst;
+            np.seed_lo = I.seed_lo;
+            np.seed_hi = I.seed_hi;
+            np.N = I.N;
+            np.nk = I.nk;
+            np.nj = I.nj;
+            np.has_limits = I.has_limits;
+            np.scale_q = I.scale_q;
+            np.scale_v = I.scale_v;
+            np.dtk = I.dtk;
+            for (int s0 = 0; s0 < cnt; s0 += NOISE_SPB) block_sample_knots(np, n0 + s0, min(NOISE_SPB, cnt - s0), work);
+            // rollouts of the tile with the instance's mapping
+            const int last_n = n0 + cnt - 1;
+            if (I.mapping == MPPI_MAP_CHAIN) {
+                const int g = threadIdx.x & 3;
+                const int n = n0 + (threadIdx.x >> 2);
+                const int ne = min(n, last_n);
+                const float c = chain_rollout<4, 3>(*M, g, I.x0, I.knots + (size_t)ne * I.E, I.H, I.nk, I.dt, I.dtk,
+                                                    nullptr);
+                if (n <= last_n && g == 0) I.costs[n] = c;
+            } else if (I.mapping == MPPI_MAP_HALFWARP) {
+                const int gl = threadIdx.x & 15;
+                const int n = n0 + (threadIdx.x >> 4);
+                const int ne = min(n, last_n);
+                LaneConst<float> L;
+                load_lane_const(*M, gl, L);
+                const float c = warp_rollout<float, 16, double>(*M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H,
+                                                                I.nk, I.dt, I.dtk, work, nullptr);
+                if (n <= last_n && gl == 0) I.costs[n] = c;
+            } else {
+                const int gl = threadIdx.x & 31;
+                const int n = n0 + (threadIdx.x >> 5);
+                const int ne = min(n, last_n);
+                LaneConst<float> L;
+                load_lane_const(*M, gl, L);
+                const float c = warp_rollout<float, 32, double>(*M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H,
+                                                                I.nk, I.dt, I.dtk, work, nullptr);
+                if (n <= last_n && gl == 0) I.costs[n] = c;
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&ctr[ii].done_roll, 1) == I.ntiles - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                if (threadIdx.x == 0) ctr[ii].done_roll = 0;
+                publish(items, q, ITEM_REDUCE, ii, I.nchunks);
+            }
+        } else {
+            const int c = s_item;
+            for (int ey = 0; ey * BATCH_THREADS < I.E; ++ey)
+                chunk_weights_average(I.costs, I.knots, I.N, I.E, I.lambda, I.normalize, c, ey, nullptr, I.zq,
+                                      I.partial, I.info);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&ctr[ii].done_red, 1) == I.nchunks - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                finalize_iteration(finalize_args(I, it));
+                __threadfence();
+                __syncthreads();
+                if (it + 1 < I.iters) {
+                    if (threadIdx.x == 0) {
+                        ctr[ii].done_red = 0;
+                        ctr[ii].it = it + 1;
+                    }
+                    __threadfence();
+                    __syncthreads();
+                    publish(items, q, ITEM_ROLLOUT, ii, I.ntiles);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Reset of a batch before the persistent launch: queue counters, prefilled iteration-0
+// ROLLOUT items, per-instance counters and solve state (as solve_begin), and the inputs
+// scattered from the packed host record: state [nx] doubles, then (if flagged) the warm
+// start [E] floats into the nominal.
+__global__ void batch_reset_kernel(const BatchInst* __restrict__ insts, int count, InstCounters* ctr,
+                                   QueueItem* items, BatchQueue* q, const int* __restrict__ prefill,
+                                   const unsigned char* __restrict__ packed_in) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    for (int k = tid; k < q->total; k += nth) {
+        if (k < q->nprefill) {
+            items[k].type = ITEM_ROLLOUT;
+            items[k].inst = prefill[2 * k];
+            items[k].idx = prefill[2 * k + 1];
+            items[k].ready = 1;
+        } else {
+            items[k].type = 0;
+            items[k].ready = 0;
+        }
+    }
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const BatchInst& I = insts[i];
+        const unsigned char* rec = packed_in + I.in_off;
+        const int nx = 13 + 2 * I.nj;
+        const double* st = reinterpret_cast<const double*>(rec);
+        const int has_warm = *reinterpret_cast<const int*>(rec + 8 * nx);
+        const float* warm = reinterpret_cast<const float*>(rec + 8 * nx + 16);
+        for (int k = threadIdx.x; k < nx; k += blockDim.x) const_cast<double*>(I.x0)[k] = st[k];
+        for (int e = threadIdx.x; e < I.E; e += blockDim.x) {
+            const float v = has_warm ? warm[e] : I.nominal[e];
+            I.nominal[e] = v;
+            I.best[e] = v;
+        }
+        if (threadIdx.x == 0) {
+            ctr[i].it = 0;
+            ctr[i].done_roll = 0;
+            ctr[i].done_red = 0;
+            I.solve->best_cost = INFINITY;
+            I.solve->best_index = -1;
+            I.solve->best_iter = -1;
+            I.solve->status = MPPI_OK;
+        }
+    }
+    if (tid == 0) {
+        q->head = 0;
+        q->append = q->nprefill;
+        q->error = 0;
+    }
+}
+
+// Outputs of every instance into one packed record per instance: result, mean [E],
+// best [E]; and the queue's error word at offset 0.
+__global__ void batch_gather_kernel(const BatchInst* __restrict__ insts, int count, const BatchQueue* q,
+                                    unsigned char* __restrict__ packed_out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<uint32_t*>(packed_out) = q->error;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const BatchInst& I = insts[i];
+        unsigned char* rec = packed_out + I.out_off;
+        if (threadIdx.x == 0) *reinterpret_cast<mppi_result*>(rec) = *I.result;
+        float* mean = reinterpret_cast<float*>(rec + sizeof(mppi_result));
+        float* best = mean + I.E;
+        for (int e = threadIdx.x; e < I.E; e += blockDim.x) {
+            mean[e] = I.mean[e];
+            best[e] = I.best[e];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Host side: a plan per batch composition (contexts by unique id), cached (LRU of 4).
+// ------------------------------------------------------------------------------------
+struct BatchPlan {
+    std::vector<uint64_t> uids;
+    int device = 0, count = 0, grid = 0;
+    size_t in_bytes = 0, out_bytes = 0;
+    std::vector<int> nx, E;
+    std::vector<size_t> in_off, out_off;
+    void* dev = nullptr;        // insts, ctr, items, q, prefill, packed in/out
+    BatchInst* d_insts = nullptr;
+    InstCounters* d_ctr = nullptr;
+    QueueItem* d_items = nullptr;
+    BatchQueue* d_q = nullptr;
+    int* d_prefill = nullptr;
+    unsigned char* d_in = nullptr;
+    unsigned char* d_out = nullptr;
+    unsigned char* h_in = nullptr;   // pinned
+    unsigned char* h_out = nullptr;  // pinned
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int kernels_per_launch = 3;
+    ~BatchPlan() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (stream) cudaStreamDestroy(stream);
+        if (dev) cudaFree(dev);
+        if (h_in) cudaFreeHost(h_in);
+        if (h_out) cudaFreeHost(h_out);
+    }
+};
+
+static std::mutex g_plan_mu;
+static std::list<BatchPlan*> g_plans;
+
+size_t batch_smem_bytes(int max_E) {
+    const size_t contrib = (size_t)27 * BATCH_THREADS * sizeof(float);
+    const size_t eps = (size_t)NOISE_SPB * max_E * sizeof(float);
+    return sizeof(DevModel<float>) + std::max(contrib, eps);
+}
+
+static mppi_status build_plan(mppi_ctx* const* ctxs, int count, BatchPlan* P) {
+    int dev;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    P->device = dev;
+    P->count = count;
+    std::vector<BatchInst> hi(count);
+    std::vector<int> order(count);
+    int max_E = 0;
+    long total = 0, nprefill = 0;
+    size_t in_off = 0, out_off = 16;
+    for (int i = 0; i < count; ++i) {
+        mppi_ctx* c = ctxs[i];
+        BatchInst& I = hi[i];
+        I.model = (const DevModel<float>*)c->model->d_f;
+        I.x0 = c->d_x0;
+        I.knots = c->d_knots;
+        I.costs = c->d_costs;
+        I.zq = c->d_zq;
+        I.partial = c->d_partial;
+        I.nominal = c->d_nominal;
+        I.mean = c->d_mean;
+        I.best = c->d_best;
+        I.sigma = c->d_sigma;
+        I.info = c->d_info;
+        I.solve = c->d_solve;
+        I.result = c->d_result;
+        I.lambda = c->lambda;
+        I.N = c->N;
+        I.H = c->H;
+        I.nk = c->nk;
+        I.nj = c->nj;
+        I.E = c->E;
+        I.iters = c->iters;
+        I.mapping = c->mapping;
+        I.tile = c->mapping == MPPI_MAP_CHAIN ? BATCH_THREADS / 4
+                 : c->mapping == MPPI_MAP_HALFWARP ? BATCH_THREADS / 16 : BATCH_THREADS / 32;
+        I.ntiles = (c->N + I.tile - 1) / I.tile;
+        I.nchunks = num_chunks(c->N);
+        I.normalize = c->normalize;
+        I.warm_from = c->warm_from;
+        I.has_limits = c->model->host_f.has_limits;
+        I.dt = (float)c->dt;
+        I.dtk = (float)c->dtk;
+        I.scale_q = (float)c->scale_q;
+        I.scale_v = (float)c->scale_v;
+        I.inst = c->instance_id;
+        I.seed_lo = (uint32_t)(c->seed & 0xffffffffu);
+        I.seed_hi = (uint32_t)(c->seed >> 32);
+        I.in_off = (int)in_off;
+        I.out_off = (int)out_off;
+        P->nx.push_back(c->nx);
+        P->E.push_back(c->E);
+        P->in_off.push_back(in_off);
+        P->out_off.push_back(out_off);
+        in_off += ((size_t)8 * c->nx + 16 + 4 * (size_t)c->E + 15) & ~(size_t)15;
+        out_off += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
+        max_E = std::max(max_E, c->E);
+        total += (long)c->iters * (I.ntiles + I.nchunks);
+        nprefill += I.ntiles;
+        order[i] = i;
+    }
+    // largest instances first: the long rollouts start early and the tail is short
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long)hi[a].N * hi[a].H > (long)hi[b].N * hi[b].H;
+    });
+    std::vector<int> prefill;
+    prefill.reserve(2 * nprefill);
+    for (int i : order)
+        for (int t = 0; t < hi[i].ntiles; ++t) {
+            prefill.push_back(i);
+            prefill.push_back(t);
+        }
+    P->in_bytes = in_off;
+    P->out_bytes = out_off;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_insts = take(sizeof(BatchInst) * count);
+    const size_t o_ctr = take(sizeof(InstCounters) * count);
+    const size_t o_items = take(sizeof(QueueItem) * total);
+    const size_t o_q = take(sizeof(BatchQueue));
+    const size_t o_pre = take(sizeof(int) * prefill.size());
+    const size_t o_in = take(P->in_bytes);
+    const size_t o_out = take(P->out_bytes);
+    e = cudaMalloc(&P->dev, off);
+    if (e == cudaSuccess) e = cudaMallocHost(&P->h_in, P->in_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, P->out_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch plan allocation");
+    char* base = (char*)P->dev;
+    P->d_insts = (BatchInst*)(base + o_insts);
+    P->d_ctr = (InstCounters*)(base + o_ctr);
+    P->d_items = (QueueItem*)(base + o_items);
+    P->d_q = (BatchQueue*)(base + o_q);
+    P->d_prefill = (int*)(base + o_pre);
+    P->d_in = (unsigned char*)(base + o_in);
+    P->d_out = (unsigned char*)(base + o_out);
+    BatchQueue hq;
+    memset(&hq, 0, sizeof hq);
+    hq.total = (int)total;
+    hq.nprefill = (int)nprefill;
+    memset(P->h_in, 0, P->in_bytes);
+    e = cudaMemcpy(P->d_insts, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_q, &hq, sizeof hq, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_prefill, prefill.data(), sizeof(int) * prefill.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch plan upload");
+    // persistent grid: the resident capacity of the device
+    const size_t sm = batch_smem_bytes(max_E);
+    e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, BATCH_THREADS, sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch occupancy");
+    P->grid = std::max(1, per_sm) * sms;
+    if (P->grid > total) P->grid = (int)total;
+    // the launch sequence, captured once: inputs H2D, reset/scatter, persistent walk,
+    // gather, outputs D2H
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch capture");
+    cudaError_t ce = cudaMemcpyAsync(P->d_in, P->h_in, P->in_bytes, cudaMemcpyHostToDevice, P->stream);
+    if (ce == cudaSuccess) {
+        batch_reset_kernel<<<std::min(count, 1024), 256, 0, P->stream>>>(P->d_insts, count, P->d_ctr, P->d_items, P->d_q,
+                                                                       P->d_prefill, P->d_in);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+        const uint64_t budget_ns = 20ull * 1000 * 1000 * 1000;  // 20 s
+        persistent_kernel<<<P->grid, BATCH_THREADS, sm, P->stream>>>(P->d_insts, P->d_ctr, P->d_items, P->d_q,
+                                                                     budget_ns);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+        batch_gather_kernel<<<std::min(count, 1024), 128, 0, P->stream>>>(P->d_insts, count, P->d_q, P->d_out);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(P->h_out, P->d_out, P->out_bytes, cudaMemcpyDeviceToHost, P->stream);
+    e = cudaStreamEndCapture(P->stream, &g);
+    if (ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(nullptr, ce, "batch launch capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch end capture");
+    e = cudaGraphInstantiate(&P->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph instantiate");
+    return MPPI_OK;
+}
+
+BatchPlan* get_plan(mppi_ctx* const* ctxs, int count, mppi_status* st) {
+    std::vector<uint64_t> uids(count);
+    for (int i = 0; i < count; ++i) uids[i] = ctxs[i]->uid;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end(); ++it)
+        if ((*it)->uids == uids) {
+            BatchPlan* p = *it;
+            g_plans.erase(it);
+            g_plans.push_front(p);
+            *st = MPPI_OK;
+            return p;
+        }
+    BatchPlan* p = new (std::nothrow) BatchPlan();
+    if (!p) {
+        *st = MPPI_ERR_OUT_OF_MEMORY;
+        return nullptr;
+    }
+    p->uids = uids;
+    *st = build_plan(ctxs, count, p);
+    if (*st != MPPI_OK) {
+        delete p;
+        return nullptr;
+    }
+    g_plans.push_front(p);
+    while (g_plans.size() > 4) {
+        BatchPlan* old = g_plans.back();
+        g_plans.pop_back();
+        cudaStreamSynchronize(old->stream);
+        delete old;
+    }
+    return p;
+}
+
+// Writes inputs into the plan's pinned record, launches the graph and (if wait) copies
+// the outputs out. Returns the status.
+mppi_status run_plan(BatchPlan* P, mppi_ctx* const* ctxs, const double* const* states, const float* const* warm,
+                     float* const* out_mean, float* const* out_best, mppi_result* info) {
+    for (int i = 0; i < P->count; ++i) {
+        unsigned char* rec = P->h_in + P->in_off[i];
+        memcpy(rec, states[i], sizeof(double) * P->nx[i]);
+        const int has = (warm && warm[i]) ? 1 : 0;
+        memcpy(rec + 8 * P->nx[i], &has, sizeof has);
+        if (has) memcpy(rec + 8 * P->nx[i] + 16, warm[i], sizeof(float) * P->E[i]);
+    }
+    cudaError_t e = cudaGraphLaunch(P->graph, P->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
+    uint32_t err;
+    memcpy(&err, P->h_out, sizeof err);
+    mppi_status st = MPPI_OK;
+    for (int i = 0; i < P->count; ++i) {
+        const unsigned char* rec = P->h_out + P->out_off[i];
+        mppi_result r;
+        memcpy(&r, rec, sizeof r);
+        const float* mean = reinterpret_cast<const float*>(rec + sizeof(mppi_result));
+        if (out_mean && out_mean[i]) memcpy(out_mean[i], mean, sizeof(float) * P->E[i]);
+        if (out_best && out_best[i]) memcpy(out_best[i], mean + P->E[i], sizeof(float) * P->E[i]);
+        if (info) info[i] = r;
+        if (r.status != MPPI_OK && st == MPPI_OK) st = r.status;
+        ctxs[i]->has_state = true;
+    }
+    if (err) {
+        set_error(nullptr, "a bounded device wait of the batched kernel gave up");
+        return MPPI_ERR_TIMEOUT;
+    }
+    return st;
+}
+
+}  // namespace mppi
+
+using namespace mppi;
+
+extern "C" mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, const double* const* h_states,
+                                        const float* const* h_warm, float* const* h_out_mean,
+                                        float* const* h_out_best, mppi_result* h_info) {
+    if (!ctxs || count < 1 || !h_states || !h_out_mean) return MPPI_ERR_INVALID_ARG;
+    int dev;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    for (int i = 0; i < count; ++i) {
+        mppi_ctx* c = ctxs[i];
+        if (!c || !h_states[i] || !h_out_mean[i]) return MPPI_ERR_INVALID_ARG;
+        if (c->device != dev) {
+            set_error(nullptr, "batched contexts must live on the current device");
+            return MPPI_ERR_UNSUPPORTED;
+        }
+        if (c->mapping != MPPI_MAP_WARP && c->mapping != MPPI_MAP_HALFWARP && c->mapping != MPPI_MAP_CHAIN) {
+            set_error(nullptr, "batched contexts need the warp, half-warp or chain mapping");
+            return MPPI_ERR_UNSUPPORTED;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) {
+                set_error(nullptr, "a context appears twice in one batch");
+                return MPPI_ERR_INVALID_ARG;
+            }
+        for (int k = 0; k < c->nx; ++k)
+            if (!isfinite(h_states[i][k])) {
+                set_error(nullptr, "state is not finite");
+                return MPPI_ERR_NONFINITE_STATE;
+            }
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "context stream");
+    }
+    mppi_status st;
+    BatchPlan* P = get_plan(ctxs, count, &st);
+    if (!P) return st;
+    return run_plan(P, ctxs, h_states, h_warm, h_out_mean, h_out_best, h_info);
+}

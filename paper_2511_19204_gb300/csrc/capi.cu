@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -426,7 +427,9 @@ mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t k
     if (dev != model->device) return bad("model lives on another device");
     mppi_ctx* c = new (std::nothrow) mppi_ctx();
     if (!c) return MPPI_ERR_OUT_OF_MEMORY;
+    static std::atomic<uint64_t> next_uid{1};
     c->model = model;
+    c->uid = next_uid++;
     c->device = dev;
     c->N = K;
     c->H = H;

@@ -22,6 +22,7 @@ struct mppi_model {
 
 struct mppi_ctx {
     const mppi_model* model = nullptr;
+    uint64_t uid = 0;                            // unique per context for the life of the process
     int device = 0;
     int N = 0, H = 0, nk = 0, iters = 0, nj = 0, E = 0, nx = 0;
     double lambda = 0, dt = 0, dtk = 0, scale_q = 1, scale_v = 0;

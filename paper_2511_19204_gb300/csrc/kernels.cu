@@ -3,70 +3,45 @@
 // Eq. update-nominal) and the iteration's finalize (log-sum-exp, mean, best tracking of
 // Sec. III-D).
 #include "internal.h"
+#include "noise.cuh"
 #include "reduce.cuh"
 
 namespace mppi {
 
 // ------------------------------------------------------------------------------------
-// K1: knot noise. A block owns SPB samples: phase 1 draws one Philox block (4 words ->
-// 2 Box-Muller pairs) per thread into shared memory; phase 2 forms
-// theta = nominal + sigma_k * scale * eps per (knot, joint), clamps, and stores
-// position and velocity knots with consecutive joints on consecutive threads.
-// Counter = (e / 4, n, iteration counter, instance), key = (seed lo, seed hi).
+// K1: knot noise, NOISE_SPB samples per block (block_sample_knots: one Philox block of 4
+// words -> 2 Box-Muller pairs per thread into shared memory, then theta = nominal +
+// sigma_k * scale * eps per (knot, joint), clamped, consecutive joints on consecutive
+// threads).
 // ------------------------------------------------------------------------------------
-constexpr int SAMPLE_SPB = 8;
 constexpr int SAMPLE_THREADS = 256;
 
 __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs a) {
-    extern __shared__ float eps[];  // [SPB][E]
-    const int E = a.nk * 2 * a.nj;
-    const int B4 = (E + 3) / 4;
-    const int n0 = blockIdx.x * SAMPLE_SPB;
-    const uint32_t it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
-    for (int idx = threadIdx.x; idx < SAMPLE_SPB * B4; idx += blockDim.x) {
-        const int nl = idx / B4, b = idx - nl * B4;
-        const int n = n0 + nl;
-        if (n >= a.N) continue;
-        float e4[4] = {0.f, 0.f, 0.f, 0.f};
-        if (n > 0) {
-            const U4 w = philox4x32_10(U4{(uint32_t)b, (uint32_t)n, it, a.inst}, a.seed_lo, a.seed_hi);
-            box_muller<float>(w.x, w.y, &e4[0], &e4[1]);
-            box_muller<float>(w.z, w.w, &e4[2], &e4[3]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (4 * b + i < E) eps[nl * E + 4 * b + i] = e4[i];
-    }
-    __syncthreads();
-    const int KJ = a.nk * a.nj;
-    for (int idx = threadIdx.x; idx < SAMPLE_SPB * KJ; idx += blockDim.x) {
-        const int nl = idx / KJ, rem = idx - nl * KJ;
-        const int n = n0 + nl;
-        if (n >= a.N) continue;
-        const int k = rem / a.nj, j = rem - k * a.nj;
-        const int eq = (2 * k) * a.nj + j, ev = eq + a.nj;
-        const float sg = a.sigma_row[k];
-        float q = a.nominal[eq] + sg * a.scale_q * eps[nl * E + eq];
-        float v = a.nominal[ev] + sg * a.scale_v * eps[nl * E + ev];
-        if (a.has_limits) {
-            const float lo = a.model->q_min[j + 1], hi = a.model->q_max[j + 1];
-            if (isfinite(lo) || isfinite(hi)) {
-                q = fminf(fmaxf(q, lo), hi);
-                const float room = fminf(hi - q, q - lo);
-                const float vmax = room / (a.dtk * 0.5f);
-                v = fminf(fmaxf(v, -vmax), vmax);
-            }
-        }
-        a.knots[(size_t)n * E + eq] = q;
-        a.knots[(size_t)n * E + ev] = v;
-    }
+    extern __shared__ float eps[];  // [NOISE_SPB][E]
+    NoiseParams p;
+    p.nominal = a.nominal;
+    p.sigma_row = a.sigma_row;
+    p.model = a.model;
+    p.knots = a.knots;
+    p.it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
+    p.inst = a.inst;
+    p.seed_lo = a.seed_lo;
+    p.seed_hi = a.seed_hi;
+    p.N = a.N;
+    p.nk = a.nk;
+    p.nj = a.nj;
+    p.has_limits = a.has_limits;
+    p.scale_q = a.scale_q;
+    p.scale_v = a.scale_v;
+    p.dtk = a.dtk;
+    block_sample_knots(p, blockIdx.x * NOISE_SPB, NOISE_SPB, eps);
 }
 
 cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s) {
     const int E = a.nk * 2 * a.nj;
-    const int grid = (a.N + SAMPLE_SPB - 1) / SAMPLE_SPB;
+    const int grid = (a.N + NOISE_SPB - 1) / NOISE_SPB;
     if (grid == 0) return cudaSuccess;
-    const size_t sm = (size_t)SAMPLE_SPB * E * sizeof(float);
+    const size_t sm = (size_t)NOISE_SPB * E * sizeof(float);
     sample_knots_kernel<<<grid, SAMPLE_THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }

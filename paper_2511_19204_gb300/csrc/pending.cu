@@ -3,8 +3,6 @@
 #include "capi_internal.h"
 
 extern "C" {
-mppi_status mppi_solve_batch(mppi_ctx* const*, int32_t, const double* const*, const float* const*, float* const*,
-                             float* const*, mppi_result*) { return MPPI_ERR_UNSUPPORTED; }
 mppi_status mppi_server_create(int32_t, size_t, int32_t, mppi_server** out) { if (out) *out = nullptr; return MPPI_ERR_UNSUPPORTED; }
 void mppi_server_destroy(mppi_server*) {}
 mppi_status mppi_submit(mppi_server*, mppi_ctx*, const double*, const float*, uint64_t*) { return MPPI_ERR_UNSUPPORTED; }

@@ -1,0 +1,102 @@
+"""Batched solves (one persistent launch over uneven instances) against per-instance
+solves and the oracle, through the C ABI."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2511_19204_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2511_19204_gb300 import build, mppi
+    build.build()
+    mppi.load()
+    return mppi
+
+
+def _mix(M):
+    """Uneven instances: both robots, every batched mapping, ragged K, 1 and 3 iterations."""
+    quad, hum = S.quadruped(), S.humanoid()
+    mq, mh = M.Model(quad), M.Model(hum)
+    specs = [  # (model, robot, mapping, K, H, nk, iters, lam, seed)
+        (mq, quad, 2, 97, 60, 4, 1, 0.1, 1), (mq, quad, 2, 256, 120, 6, 3, 0.2, 2),
+        (mq, quad, 1, 33, 50, 5, 1, 0.3, 3), (mq, quad, 0, 40, 40, 4, 2, 0.1, 4),
+        (mh, hum, 0, 70, 50, 8, 1, 0.05, 5), (mh, hum, 0, 129, 30, 7, 2, 0.5, 6),
+        (mq, quad, 2, 1, 20, 4, 1, 0.1, 7), (mq, quad, 2, 65, 100, 8, 1, 0.25, 8),
+    ]
+    out = []
+    for i, (mod, rob, mp, K, H, nk, it, lam, seed) in enumerate(specs):
+        sig = S.linear_sigma(nk, it)
+        x0 = S.standing_state(rob, jitter=0.02, base_vel=0.2, seed=100 + i)
+        warm = S.nominal_knots(rob, nk).astype(np.float32)
+        kw = dict(iters=it, dt=0.005, seed=seed, instance=i, mapping=mp)
+        out.append(dict(mod=mod, rob=rob, K=K, H=H, nk=nk, it=it, lam=lam, sig=sig, x0=x0, warm=warm, kw=kw))
+    return out
+
+
+def _batch(M, ctrls, states, warms):
+    L = M.load()
+    n = len(ctrls)
+    hs = (C.c_void_p * n)(*[c.h for c in ctrls])
+    st = [np.ascontiguousarray(s, dtype=np.float64) for s in states]
+    wa = [np.ascontiguousarray(w, dtype=np.float32).reshape(-1) if w is not None else None for w in warms]
+    means = [np.zeros(c.E, np.float32) for c in ctrls]
+    bests = [np.zeros(c.E, np.float32) for c in ctrls]
+    dp = C.POINTER(C.c_double)
+    fp = C.POINTER(C.c_float)
+    ps = (dp * n)(*[s.ctypes.data_as(dp) for s in st])
+    pw = (fp * n)(*[w.ctypes.data_as(fp) if w is not None else None for w in wa])
+    pm = (fp * n)(*[m.ctypes.data_as(fp) for m in means])
+    pb = (fp * n)(*[b.ctypes.data_as(fp) for b in bests])
+    info = (M.mppi_result * n)()
+    rc = L.mppi_solve_batch(hs, n, ps, pw, pm, pb, info)
+    return rc, means, bests, [info[i].as_dict() for i in range(n)]
+
+
+def test_batch_equals_alone_bitwise(M):
+    mix = _mix(M)
+    alone = [M.Controller(d["mod"], d["K"], d["H"], d["nk"], d["lam"], d["sig"], **d["kw"]) for d in mix]
+    batch = [M.Controller(d["mod"], d["K"], d["H"], d["nk"], d["lam"], d["sig"], **d["kw"]) for d in mix]
+    ref = [c.solve(d["x0"], warm=d["warm"]) for c, d in zip(alone, mix)]
+    rc, means, bests, infos = _batch(M, batch, [d["x0"] for d in mix], [d["warm"] for d in mix])
+    assert rc == 0
+    for i, (r, m, b, inf) in enumerate(zip(ref, means, bests, infos)):
+        np.testing.assert_array_equal(m, r[0].reshape(-1), err_msg=f"instance {i}")
+        np.testing.assert_array_equal(b, r[1].reshape(-1), err_msg=f"instance {i}")
+        assert inf["best_cost"] == r[2]["best_cost"] and inf["best_index"] == r[2]["best_index"]
+        assert inf["n_finite"] == r[2]["n_finite"] and inf["ess"] == r[2]["ess"]
+    # the next solve of each: resident warm start and counters advance the same way
+    ref2 = [c.solve(d["x0"]) for c, d in zip(alone, mix)]
+    rc, means2, _, _ = _batch(M, batch, [d["x0"] for d in mix], [None] * len(mix))
+    assert rc == 0
+    for i, (r, m) in enumerate(zip(ref2, means2)):
+        np.testing.assert_array_equal(m, r[0].reshape(-1), err_msg=f"second solve, instance {i}")
+        assert batch[i].iter_counter == alone[i].iter_counter
+
+
+def test_batch_matches_oracle(M, orc):
+    mix = _mix(M)
+    ctrls = [M.Controller(d["mod"], d["K"], d["H"], d["nk"], d["lam"], d["sig"], **d["kw"]) for d in mix]
+    rc, means, _, infos = _batch(M, ctrls, [d["x0"] for d in mix], [d["warm"] for d in mix])
+    assert rc == 0
+    for i, d in enumerate(mix):
+        ref = orc.solve(d["rob"], d["K"], d["nk"], d["H"], d["it"], 0.005, d["lam"], d["sig"], d["x0"],
+                        d["warm"].astype(np.float64), seed=d["kw"]["seed"], inst=i)
+        err = np.max(np.abs(means[i] - ref["mean"].reshape(-1)) / np.maximum(1.0, np.abs(ref["mean"].reshape(-1))))
+        assert err < 1e-3, (i, err)
+        assert infos[i]["best_cost"] == pytest.approx(ref["best_cost"], rel=1e-3)
+
+
+def test_batch_rejects_bad_input(M):
+    mix = _mix(M)[:2]
+    c = [M.Controller(d["mod"], d["K"], d["H"], d["nk"], d["lam"], d["sig"], **d["kw"]) for d in mix]
+    rc, *_ = _batch(M, [c[0], c[0]], [mix[0]["x0"], mix[0]["x0"]], [None, None])
+    assert rc == M.MPPI_ERR_INVALID_ARG
+    x = mix[1]["x0"].copy()
+    x[0] = np.inf
+    rc, *_ = _batch(M, c, [mix[0]["x0"], x], [None, None])
+    assert rc == M.MPPI_ERR_NONFINITE_STATE
