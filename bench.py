@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-samples", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", action="store_true", help="also run the batched and serving workloads")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-instance workload")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     return ap.parse_args()
 
 
@@ -188,6 +189,160 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
+def batched_extra(mppi, synth, torch, count=256, reps=5):
+    """Batched uneven instances: one persistent graph-captured launch per solve of all
+    instances vs the same instances as sequential plain launches (one CUDA graph each,
+    all on one stream). Each instance: one MPPI iteration, its own model/K/H/knots/lambda."""
+    probs = synth.batched_problems(count)
+    models = {}
+    stream = torch.cuda.Stream()
+    ctrls = []
+    for p in probs:
+        if p.model.name not in models:
+            models[p.model.name] = mppi.Model(p.model)
+        ctrls.append(mppi.Controller.from_problem(models[p.model.name], p, stream=stream.cuda_stream))
+    units = sum(p.n * p.horizon * p.iters for p in probs)
+    states = [p.state for p in probs]
+    warms = [p.nominal for p in probs]
+    # batched (host buffers in and out, packed into one H2D and one D2H inside the graph)
+    for _ in range(2):
+        mppi.solve_batch(ctrls, states, warms)
+    tb = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        mppi.solve_batch(ctrls, states, warms)
+        tb.append(time.perf_counter() - t0)
+    # sequential plain launches, device-resident inputs, completion time of each instance
+    xs = [torch.tensor(p.state, dtype=torch.float64, device="cuda") for p in probs]
+    ws = [torch.tensor(p.nominal.reshape(-1), dtype=torch.float32, device="cuda") for p in probs]
+    outs = [torch.zeros(c.E, dtype=torch.float32, device="cuda") for c in ctrls]
+    for _ in range(2):
+        for c, x, w, o in zip(ctrls, xs, ws, outs):
+            c.solve_device(x.data_ptr(), o.data_ptr(), d_warm=w.data_ptr())
+    torch.cuda.synchronize()
+    tp, done_ms = [], []
+    for _ in range(reps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(count + 1)]
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            for i, (c, x, w, o) in enumerate(zip(ctrls, xs, ws, outs)):
+                c.solve_device(x.data_ptr(), o.data_ptr(), d_warm=w.data_ptr())
+                evs[i + 1].record(stream)
+        evs[-1].synchronize()
+        tp.append(evs[0].elapsed_time(evs[-1]) / 1e3)
+        done_ms = [evs[0].elapsed_time(e) for e in evs[1:]]
+    tb_s, tp_s = statistics.median(tb), statistics.median(tp)
+    done_ms.sort()
+    q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))]
+    return {"workload": f"{count} uneven instances (70% quadruped / 30% humanoid, K log-uniform 64-2048, "
+                        f"H 50-200, 4-8 knots, lambda U(0.05,0.5), 1 iteration), seeds 1000+i",
+            "step_samples_per_batch": units,
+            "batched": {"launch": "one persistent kernel walking a device work queue, graph-captured "
+                                  "with packed H2D/D2H (host buffers, wall clock)",
+                        "ms": 1e3 * tb_s, "solves_per_s": count / tb_s, "rollout_steps_per_s": units / tb_s,
+                        "latency_ms_p50": 1e3 * tb_s, "latency_ms_p99": 1e3 * max(tb)},
+            "plain_sequential": {"launch": f"{count} mppi_solve_device graphs back to back on one stream "
+                                           "(device-resident inputs, CUDA events)",
+                                 "ms": 1e3 * tp_s, "solves_per_s": count / tp_s, "rollout_steps_per_s": units / tp_s,
+                                 "instance_done_ms_p50": q(done_ms, 0.5), "instance_done_ms_p99": q(done_ms, 0.99)},
+            "speedup": tp_s / tb_s}
+
+
+def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1.0, n_ctrl=512):
+    """Continuous-batching server under Poisson load: 512 closed-loop controllers (70 %
+    quadruped, K log-uniform 256-2048, H 100-200, 4-8 knots), each request = current
+    state + resident warm start; a controller's next request waits for its previous
+    result. Latency = server completion time - arrival time (CLOCK_MONOTONIC)."""
+    import heapq
+    import math
+
+    import numpy as np
+    rng = np.random.default_rng(7)
+    quad, hum = synth.quadruped(), synth.humanoid()
+    mods = {"quadruped": mppi.Model(quad), "humanoid": mppi.Model(hum)}
+    ctrls, states, work = [], [], []
+    for i in range(n_ctrl):
+        rob = quad if rng.random() < 0.7 else hum
+        n = int(math.floor(math.exp(rng.uniform(math.log(256), math.log(2048)))))
+        h = int(rng.integers(100, 201))
+        nk = int(rng.integers(4, 9))
+        c = mppi.Controller(mods[rob.name], n, h, nk, float(rng.uniform(0.05, 0.5)), synth.linear_sigma(nk),
+                            dt=0.005, seed=7000 + i, instance=i)
+        ctrls.append(c)
+        states.append(synth.standing_state(rob, jitter=0.02, seed=7000 + i))
+        work.append(n * h)
+    # plain single-instance launches back to back: capacity of the unbatched path
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(0, n_ctrl, 4):
+        ctrls[i].solve(states[i])
+        done += 1
+    plain_solves_per_s = done / (time.perf_counter() - t0)
+    srv = mppi.Server(mem_budget_bytes=8 << 30, max_inflight=4)
+    out = {"workload": f"{n_ctrl} controllers, Poisson arrivals, 70% quadruped / 30% humanoid, K 256-2048, "
+                       f"H 100-200, 4-8 knots, 1 iteration; {seconds:.0f} s per load after {warm_s:.0f} s warm-up",
+           "memory_budget_bytes": 8 << 30, "max_inflight_launches": 4,
+           "plain_single_instance_solves_per_s": plain_solves_per_s, "loads": []}
+    for load in loads:
+        rate = load / n_ctrl
+        now0 = time.monotonic_ns()
+        heap = [(now0 + int(rng.exponential(1e9 / rate)), i) for i in range(n_ctrl)]
+        heapq.heapify(heap)
+        busy = [None] * n_ctrl          # outstanding ticket
+        backlog = [[] for _ in range(n_ctrl)]  # arrival times waiting for the controller
+        owner, arrival = {}, {}
+        lat, units = [], 0
+        t_end = now0 + int((seconds + warm_s) * 1e9)
+        t_meas = now0 + int(warm_s * 1e9)
+        s0 = srv.stats()
+
+        def submit(i, t_arr):
+            x = states[i].copy()
+            x[7:7 + ctrls[i].nj] += rng.normal(scale=0.002, size=ctrls[i].nj)
+            t = srv.submit(ctrls[i], x)
+            busy[i] = t
+            owner[t] = i
+            arrival[t] = t_arr
+
+        while True:
+            now = time.monotonic_ns()
+            if now >= t_end and not owner:
+                break
+            while heap and heap[0][0] <= now and now < t_end:
+                t_arr, i = heapq.heappop(heap)
+                heapq.heappush(heap, (t_arr + int(rng.exponential(1e9 / rate)), i))
+                if busy[i] is None:
+                    submit(i, t_arr)
+                else:
+                    backlog[i].append(t_arr)
+            nc = srv.next_completed(timeout_us=200)
+            while nc is not None:
+                t, _, t_done = nc
+                i = owner.pop(t)
+                t_arr = arrival.pop(t)
+                srv.poll(t, ctrls[i], timeout_us=0)
+                busy[i] = None
+                if t_arr >= t_meas and t_arr < t_end:
+                    lat.append((t_done - t_arr) / 1e6)
+                    units += work[i]
+                if backlog[i] and time.monotonic_ns() < t_end:
+                    submit(i, backlog[i].pop(0))
+                else:
+                    backlog[i] = []
+                nc = srv.next_completed(timeout_us=0)
+        s1 = srv.stats()
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+        launches = s1["launches"] - s0["launches"]
+        completed = s1["completed"] - s0["completed"]
+        out["loads"].append({"offered_req_per_s": load, "completed_req_per_s": len(lat) / seconds,
+                             "rollout_steps_per_s": units / seconds, "latency_ms_p50": q(0.5),
+                             "latency_ms_p99": q(0.99), "latency_ms_p999": q(0.999),
+                             "mean_requests_per_launch": completed / max(launches, 1)})
+    srv.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -287,6 +442,16 @@ def run_ours(args, rank, world, local):
         "gpu_launches": args.steps * ctrl.kernels_per_solve,
         "clocks": clk,
     }
+    if not args.no_batched:
+        try:
+            line["batched_uneven"] = batched_extra(mppi, synth, torch)
+        except Exception as exc:  # reported, never silently dropped
+            line["batched_uneven"] = {"error": repr(exc)}
+    if not args.no_serving:
+        try:
+            line["serving"] = serving_extra(mppi, synth)
+        except Exception as exc:  # reported, never silently dropped
+            line["serving"] = {"error": repr(exc)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_samples)
     print(json.dumps(line), flush=True)

@@ -280,8 +280,14 @@ mppi_status mppi_submit(mppi_server* server, mppi_ctx* ctx, const double* h_stat
 mppi_status mppi_poll(mppi_server* server, uint64_t ticket, float* h_out_mean,
                       float* h_out_best, mppi_result* h_info, int64_t timeout_us);
 
+/* Next completed ticket, in completion order: MPPI_PENDING if none completes within
+ * timeout_us (< 0 = wait forever, 0 = do not wait). times_ns (nullable, [2]) receives the
+ * ticket's submit and completion times on CLOCK_MONOTONIC. The ticket still has to be
+ * polled to fetch its results and release it. */
+mppi_status mppi_next_completed(mppi_server* server, int64_t timeout_us, uint64_t* ticket, int64_t* times_ns);
+
 /* Server counters: [0] submitted, [1] completed, [2] launches, [3] peak bytes admitted,
- * [4] requests that waited for admission. */
+ * [4] admissions deferred by the memory budget. */
 mppi_status mppi_server_stats(mppi_server* server, int64_t* h_out5);
 
 /* ---------------------------------------------------------------------------------- */

@@ -12,6 +12,7 @@
 // Progress needs no co-residency: a block waits only for an item whose producer is a
 // block that has already taken and finished its own item and publishes without waiting.
 // Every wait is bounded by the global timer and sets an error word when it gives up.
+#pragma once
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -21,6 +22,7 @@
 #include <new>
 #include <vector>
 
+#include "batch.h"
 #include "capi_internal.h"
 #include "noise.cuh"
 #include "reduce.cuh"
@@ -28,7 +30,6 @@
 
 namespace mppi {
 
-constexpr int BATCH_THREADS = 256;
 constexpr int ITEM_ROLLOUT = 1;
 constexpr int ITEM_REDUCE = 2;
 
@@ -155,7 +156,6 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                       uint64_t budget_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t mbar;
-    __shared__ int s_idx;
     __shared__ int s_type, s_inst, s_item, s_last;
     __shared__ const void* s_loaded;
     DevModel<float>* M = reinterpret_cast<DevModel<float>*>(smem);
@@ -191,7 +191,6 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                     s_item = vi->idx;
                 }
             }
-            s_idx = idx;
             s_type = type;
         }
         __syncthreads();
@@ -369,57 +368,75 @@ __global__ void batch_gather_kernel(const BatchInst* __restrict__ insts, int cou
 }
 
 // ------------------------------------------------------------------------------------
-// Host side: a plan per batch composition (contexts by unique id), cached (LRU of 4).
+// Host side. A batch image is one contiguous block, identical in pinned host memory and
+// on the device: [queue header][descriptors][prefilled items][packed inputs], followed
+// on the device by the counters, the item array and the packed outputs. One H2D copy of
+// the image, the reset/scatter kernel, the persistent kernel, the gather kernel and one
+// D2H copy of the outputs make a launch.
 // ------------------------------------------------------------------------------------
-struct BatchPlan {
-    std::vector<uint64_t> uids;
-    int device = 0, count = 0, grid = 0;
-    size_t in_bytes = 0, out_bytes = 0;
-    std::vector<int> nx, E;
-    std::vector<size_t> in_off, out_off;
-    void* dev = nullptr;        // insts, ctr, items, q, prefill, packed in/out
-    BatchInst* d_insts = nullptr;
-    InstCounters* d_ctr = nullptr;
-    QueueItem* d_items = nullptr;
-    BatchQueue* d_q = nullptr;
-    int* d_prefill = nullptr;
-    unsigned char* d_in = nullptr;
-    unsigned char* d_out = nullptr;
-    unsigned char* h_in = nullptr;   // pinned
-    unsigned char* h_out = nullptr;  // pinned
-    cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int kernels_per_launch = 3;
-    ~BatchPlan() {
-        if (graph) cudaGraphExecDestroy(graph);
-        if (stream) cudaStreamDestroy(stream);
-        if (dev) cudaFree(dev);
-        if (h_in) cudaFreeHost(h_in);
-        if (h_out) cudaFreeHost(h_out);
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+BatchLayout layout_batch(mppi_ctx* const* ctxs, int count) {
+    BatchLayout L;
+    L.count = count;
+    long total = 0, nprefill = 0;
+    size_t in_bytes = 0, out_bytes = 16;
+    int max_E = 0;
+    for (int i = 0; i < count; ++i) {
+        mppi_ctx* c = ctxs[i];
+        const int tile = batch_tile(c->mapping);
+        const int ntiles = (c->N + tile - 1) / tile;
+        total += (long)c->iters * (ntiles + num_chunks(c->N));
+        nprefill += ntiles;
+        in_bytes += ((size_t)8 * c->nx + 16 + 4 * (size_t)c->E + 15) & ~(size_t)15;
+        out_bytes += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
+        max_E = std::max(max_E, c->E);
     }
-};
-
-static std::mutex g_plan_mu;
-static std::list<BatchPlan*> g_plans;
-
-size_t batch_smem_bytes(int max_E) {
-    const size_t contrib = (size_t)27 * BATCH_THREADS * sizeof(float);
-    const size_t eps = (size_t)NOISE_SPB * max_E * sizeof(float);
-    return sizeof(DevModel<float>) + std::max(contrib, eps);
+    L.total = total;
+    L.nprefill = nprefill;
+    L.max_E = max_E;
+    L.in_bytes = in_bytes;
+    L.out_bytes = out_bytes;
+    size_t off = 0;
+    L.o_q = off;
+    off += al256(sizeof(BatchQueue));
+    L.o_insts = off;
+    off += al256(sizeof(BatchInst) * count);
+    L.o_pre = off;
+    off += al256(sizeof(int) * 2 * nprefill);
+    L.o_in = off;
+    off += al256(in_bytes);
+    L.image_bytes = off;
+    L.o_ctr = off;
+    off += al256(sizeof(InstCounters) * count);
+    L.o_items = off;
+    off += al256(sizeof(QueueItem) * total);
+    L.o_out = off;
+    off += al256(out_bytes);
+    L.dev_bytes = off;
+    return L;
 }
 
-static mppi_status build_plan(mppi_ctx* const* ctxs, int count, BatchPlan* P) {
-    int dev;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
-    P->device = dev;
-    P->count = count;
-    std::vector<BatchInst> hi(count);
-    std::vector<int> order(count);
-    int max_E = 0;
-    long total = 0, nprefill = 0;
-    size_t in_off = 0, out_off = 16;
-    for (int i = 0; i < count; ++i) {
+int batch_tile(int mapping) {
+    return mapping == MPPI_MAP_CHAIN ? BATCH_THREADS / 4 : mapping == MPPI_MAP_HALFWARP ? BATCH_THREADS / 16
+                                                                                         : BATCH_THREADS / 32;
+}
+
+// Writes the image (queue header, descriptors pointing at each context's buffers, the
+// prefill list with the largest instances first, and the packed inputs) into `img`.
+void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double* const* states,
+                      const float* const* warm, unsigned char* img, std::vector<size_t>* in_off,
+                      std::vector<size_t>* out_off) {
+    BatchQueue* q = reinterpret_cast<BatchQueue*>(img + L.o_q);
+    memset(q, 0, sizeof *q);
+    q->total = (int)L.total;
+    q->nprefill = (int)L.nprefill;
+    BatchInst* hi = reinterpret_cast<BatchInst*>(img + L.o_insts);
+    size_t ioff = 0, ooff = 16;
+    if (in_off) in_off->clear();
+    if (out_off) out_off->clear();
+    std::vector<int> order(L.count);
+    for (int i = 0; i < L.count; ++i) {
         mppi_ctx* c = ctxs[i];
         BatchInst& I = hi[i];
         I.model = (const DevModel<float>*)c->model->d_f;
@@ -443,8 +460,7 @@ static mppi_status build_plan(mppi_ctx* const* ctxs, int count, BatchPlan* P) {
         I.E = c->E;
         I.iters = c->iters;
         I.mapping = c->mapping;
-        I.tile = c->mapping == MPPI_MAP_CHAIN ? BATCH_THREADS / 4
-                 : c->mapping == MPPI_MAP_HALFWARP ? BATCH_THREADS / 16 : BATCH_THREADS / 32;
+        I.tile = batch_tile(c->mapping);
         I.ntiles = (c->N + I.tile - 1) / I.tile;
         I.nchunks = num_chunks(c->N);
         I.normalize = c->normalize;
@@ -457,98 +473,161 @@ static mppi_status build_plan(mppi_ctx* const* ctxs, int count, BatchPlan* P) {
         I.inst = c->instance_id;
         I.seed_lo = (uint32_t)(c->seed & 0xffffffffu);
         I.seed_hi = (uint32_t)(c->seed >> 32);
-        I.in_off = (int)in_off;
-        I.out_off = (int)out_off;
-        P->nx.push_back(c->nx);
-        P->E.push_back(c->E);
-        P->in_off.push_back(in_off);
-        P->out_off.push_back(out_off);
-        in_off += ((size_t)8 * c->nx + 16 + 4 * (size_t)c->E + 15) & ~(size_t)15;
-        out_off += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
-        max_E = std::max(max_E, c->E);
-        total += (long)c->iters * (I.ntiles + I.nchunks);
-        nprefill += I.ntiles;
+        I.in_off = (int)ioff;
+        I.out_off = (int)ooff;
+        if (in_off) in_off->push_back(ioff);
+        if (out_off) out_off->push_back(ooff);
+        if (states) {
+            unsigned char* rec = img + L.o_in + ioff;
+            memcpy(rec, states[i], sizeof(double) * c->nx);
+            const int has = (warm && warm[i]) ? 1 : 0;
+            memcpy(rec + 8 * c->nx, &has, sizeof has);
+            if (has) memcpy(rec + 8 * c->nx + 16, warm[i], sizeof(float) * c->E);
+        }
+        ioff += ((size_t)8 * c->nx + 16 + 4 * (size_t)c->E + 15) & ~(size_t)15;
+        ooff += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
         order[i] = i;
     }
-    // largest instances first: the long rollouts start early and the tail is short
+    // largest instances first: the long rollouts start early and the tail stays short
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (long)hi[a].N * hi[a].H > (long)hi[b].N * hi[b].H;
     });
-    std::vector<int> prefill;
-    prefill.reserve(2 * nprefill);
+    int* pre = reinterpret_cast<int*>(img + L.o_pre);
+    long k = 0;
     for (int i : order)
         for (int t = 0; t < hi[i].ntiles; ++t) {
-            prefill.push_back(i);
-            prefill.push_back(t);
+            pre[2 * k] = i;
+            pre[2 * k + 1] = t;
+            ++k;
         }
-    P->in_bytes = in_off;
-    P->out_bytes = out_off;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        const size_t o = off;
-        off += (bytes + 255) & ~(size_t)255;
-        return o;
-    };
-    const size_t o_insts = take(sizeof(BatchInst) * count);
-    const size_t o_ctr = take(sizeof(InstCounters) * count);
-    const size_t o_items = take(sizeof(QueueItem) * total);
-    const size_t o_q = take(sizeof(BatchQueue));
-    const size_t o_pre = take(sizeof(int) * prefill.size());
-    const size_t o_in = take(P->in_bytes);
-    const size_t o_out = take(P->out_bytes);
-    e = cudaMalloc(&P->dev, off);
-    if (e == cudaSuccess) e = cudaMallocHost(&P->h_in, P->in_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, P->out_bytes);
+}
+
+// Packed inputs of instance i only (states / warm starts change between launches).
+void fill_batch_inputs(mppi_ctx* const* ctxs, const BatchLayout& L, const std::vector<size_t>& in_off,
+                       const double* const* states, const float* const* warm, unsigned char* img) {
+    for (int i = 0; i < L.count; ++i) {
+        mppi_ctx* c = ctxs[i];
+        unsigned char* rec = img + L.o_in + in_off[i];
+        memcpy(rec, states[i], sizeof(double) * c->nx);
+        const int has = (warm && warm[i]) ? 1 : 0;
+        memcpy(rec + 8 * c->nx, &has, sizeof has);
+        if (has) memcpy(rec + 8 * c->nx + 16, warm[i], sizeof(float) * c->E);
+    }
+}
+
+cudaError_t prepare_batch_kernel(int max_E, size_t* smem, int* per_sm) {
+    *smem = batch_smem_bytes(max_E);
+    cudaError_t e =
+        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(992));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel, BATCH_THREADS, *smem);
+    return e;
+}
+
+// H2D image, reset/scatter, persistent walk, gather, D2H outputs (host image and device
+// block share the layout `L`).
+cudaError_t enqueue_batch(const BatchLayout& L, const unsigned char* h_img, unsigned char* d_block,
+                          unsigned char* h_out, int grid, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(d_block, h_img, L.image_bytes, cudaMemcpyHostToDevice, s);
+    const BatchInst* insts = reinterpret_cast<const BatchInst*>(d_block + L.o_insts);
+    InstCounters* ctr = reinterpret_cast<InstCounters*>(d_block + L.o_ctr);
+    QueueItem* items = reinterpret_cast<QueueItem*>(d_block + L.o_items);
+    BatchQueue* q = reinterpret_cast<BatchQueue*>(d_block + L.o_q);
+    const int* pre = reinterpret_cast<const int*>(d_block + L.o_pre);
+    if (e == cudaSuccess) {
+        batch_reset_kernel<<<std::min(L.count, 1024), 256, 0, s>>>(insts, L.count, ctr, items, q, pre, d_block + L.o_in);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const uint64_t budget_ns = 20ull * 1000 * 1000 * 1000;  // 20 s
+        persistent_kernel<<<grid, BATCH_THREADS, smem, s>>>(insts, ctr, items, q, budget_ns);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        batch_gather_kernel<<<std::min(L.count, 1024), 128, 0, s>>>(insts, L.count, q, d_block + L.o_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_block + L.o_out, L.out_bytes, cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+// Unpack outputs; returns the first non-OK instance status or TIMEOUT.
+mppi_status unpack_batch(mppi_ctx* const* ctxs, const BatchLayout& L, const std::vector<size_t>& out_off,
+                         const unsigned char* h_out, float* const* out_mean, float* const* out_best,
+                         mppi_result* info) {
+    uint32_t err;
+    memcpy(&err, h_out, sizeof err);
+    mppi_status st = MPPI_OK;
+    for (int i = 0; i < L.count; ++i) {
+        const int E = ctxs[i]->E;
+        const unsigned char* rec = h_out + out_off[i];
+        mppi_result r;
+        memcpy(&r, rec, sizeof r);
+        const float* mean = reinterpret_cast<const float*>(rec + sizeof(mppi_result));
+        if (out_mean && out_mean[i]) memcpy(out_mean[i], mean, sizeof(float) * E);
+        if (out_best && out_best[i]) memcpy(out_best[i], mean + E, sizeof(float) * E);
+        if (info) info[i] = r;
+        if (r.status != MPPI_OK && st == MPPI_OK) st = r.status;
+        ctxs[i]->has_state = true;
+    }
+    if (err) {
+        set_error(nullptr, "a bounded device wait of the batched kernel gave up");
+        return MPPI_ERR_TIMEOUT;
+    }
+    return st;
+}
+
+// Cached plans for mppi_solve_batch: per batch composition (contexts by unique id) one
+// image, device block and captured graph; LRU of 4.
+struct BatchPlan {
+    std::vector<uint64_t> uids;
+    BatchLayout L;
+    std::vector<size_t> in_off, out_off;
+    unsigned char* h_img = nullptr;
+    unsigned char* h_out = nullptr;
+    unsigned char* d_block = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    ~BatchPlan() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (stream) cudaStreamDestroy(stream);
+        if (d_block) cudaFree(d_block);
+        if (h_img) cudaFreeHost(h_img);
+        if (h_out) cudaFreeHost(h_out);
+    }
+};
+
+static std::mutex g_plan_mu;
+static std::list<BatchPlan*> g_plans;
+
+size_t batch_smem_bytes(int max_E) {
+    const size_t contrib = (size_t)27 * BATCH_THREADS * sizeof(float);
+    const size_t eps = (size_t)NOISE_SPB * max_E * sizeof(float);
+    return sizeof(DevModel<float>) + std::max(contrib, eps);
+}
+
+static mppi_status build_plan(mppi_ctx* const* ctxs, int count, BatchPlan* P) {
+    int dev;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    P->L = layout_batch(ctxs, count);
+    e = cudaMalloc(&P->d_block, P->L.dev_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&P->h_img, P->L.image_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, P->L.out_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch plan allocation");
-    char* base = (char*)P->dev;
-    P->d_insts = (BatchInst*)(base + o_insts);
-    P->d_ctr = (InstCounters*)(base + o_ctr);
-    P->d_items = (QueueItem*)(base + o_items);
-    P->d_q = (BatchQueue*)(base + o_q);
-    P->d_prefill = (int*)(base + o_pre);
-    P->d_in = (unsigned char*)(base + o_in);
-    P->d_out = (unsigned char*)(base + o_out);
-    BatchQueue hq;
-    memset(&hq, 0, sizeof hq);
-    hq.total = (int)total;
-    hq.nprefill = (int)nprefill;
-    memset(P->h_in, 0, P->in_bytes);
-    e = cudaMemcpy(P->d_insts, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->d_q, &hq, sizeof hq, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->d_prefill, prefill.data(), sizeof(int) * prefill.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch plan upload");
-    // persistent grid: the resident capacity of the device
-    const size_t sm = batch_smem_bytes(max_E);
-    e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    memset(P->h_img, 0, P->L.image_bytes);
+    fill_batch_image(ctxs, P->L, nullptr, nullptr, P->h_img, &P->in_off, &P->out_off);
+    size_t smem = 0;
     int per_sm = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, BATCH_THREADS, sm);
+    e = prepare_batch_kernel(P->L.max_E, &smem, &per_sm);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch occupancy");
-    P->grid = std::max(1, per_sm) * sms;
-    if (P->grid > total) P->grid = (int)total;
-    // the launch sequence, captured once: inputs H2D, reset/scatter, persistent walk,
-    // gather, outputs D2H
+    const int grid = (int)std::min<long>((long)std::max(1, per_sm) * sms, P->L.total);
+    // the launch sequence, captured once
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch capture");
-    cudaError_t ce = cudaMemcpyAsync(P->d_in, P->h_in, P->in_bytes, cudaMemcpyHostToDevice, P->stream);
-    if (ce == cudaSuccess) {
-        batch_reset_kernel<<<std::min(count, 1024), 256, 0, P->stream>>>(P->d_insts, count, P->d_ctr, P->d_items, P->d_q,
-                                                                       P->d_prefill, P->d_in);
-        ce = cudaGetLastError();
-    }
-    if (ce == cudaSuccess) {
-        const uint64_t budget_ns = 20ull * 1000 * 1000 * 1000;  // 20 s
-        persistent_kernel<<<P->grid, BATCH_THREADS, sm, P->stream>>>(P->d_insts, P->d_ctr, P->d_items, P->d_q,
-                                                                     budget_ns);
-        ce = cudaGetLastError();
-    }
-    if (ce == cudaSuccess) {
-        batch_gather_kernel<<<std::min(count, 1024), 128, 0, P->stream>>>(P->d_insts, count, P->d_q, P->d_out);
-        ce = cudaGetLastError();
-    }
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(P->h_out, P->d_out, P->out_bytes, cudaMemcpyDeviceToHost, P->stream);
+    cudaError_t ce = enqueue_batch(P->L, P->h_img, P->d_block, P->h_out, grid, smem, P->stream);
     e = cudaStreamEndCapture(P->stream, &g);
     if (ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -594,44 +673,32 @@ BatchPlan* get_plan(mppi_ctx* const* ctxs, int count, mppi_status* st) {
     return p;
 }
 
-// Writes inputs into the plan's pinned record, launches the graph and (if wait) copies
-// the outputs out. Returns the status.
 mppi_status run_plan(BatchPlan* P, mppi_ctx* const* ctxs, const double* const* states, const float* const* warm,
                      float* const* out_mean, float* const* out_best, mppi_result* info) {
-    for (int i = 0; i < P->count; ++i) {
-        unsigned char* rec = P->h_in + P->in_off[i];
-        memcpy(rec, states[i], sizeof(double) * P->nx[i]);
-        const int has = (warm && warm[i]) ? 1 : 0;
-        memcpy(rec + 8 * P->nx[i], &has, sizeof has);
-        if (has) memcpy(rec + 8 * P->nx[i] + 16, warm[i], sizeof(float) * P->E[i]);
-    }
+    fill_batch_inputs(ctxs, P->L, P->in_off, states, warm, P->h_img);
     cudaError_t e = cudaGraphLaunch(P->graph, P->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
-    uint32_t err;
-    memcpy(&err, P->h_out, sizeof err);
-    mppi_status st = MPPI_OK;
-    for (int i = 0; i < P->count; ++i) {
-        const unsigned char* rec = P->h_out + P->out_off[i];
-        mppi_result r;
-        memcpy(&r, rec, sizeof r);
-        const float* mean = reinterpret_cast<const float*>(rec + sizeof(mppi_result));
-        if (out_mean && out_mean[i]) memcpy(out_mean[i], mean, sizeof(float) * P->E[i]);
-        if (out_best && out_best[i]) memcpy(out_best[i], mean + P->E[i], sizeof(float) * P->E[i]);
-        if (info) info[i] = r;
-        if (r.status != MPPI_OK && st == MPPI_OK) st = r.status;
-        ctxs[i]->has_state = true;
-    }
-    if (err) {
-        set_error(nullptr, "a bounded device wait of the batched kernel gave up");
-        return MPPI_ERR_TIMEOUT;
-    }
-    return st;
+    return unpack_batch(ctxs, P->L, P->out_off, P->h_out, out_mean, out_best, info);
 }
 
 }  // namespace mppi
 
 using namespace mppi;
+
+namespace mppi {
+mppi_status check_batchable(const mppi_ctx* c, int dev) {
+    if (c->device != dev) {
+        set_error(nullptr, "batched contexts must live on the current device");
+        return MPPI_ERR_UNSUPPORTED;
+    }
+    if (c->mapping != MPPI_MAP_WARP && c->mapping != MPPI_MAP_HALFWARP && c->mapping != MPPI_MAP_CHAIN) {
+        set_error(nullptr, "batched contexts need the warp, half-warp or chain mapping");
+        return MPPI_ERR_UNSUPPORTED;
+    }
+    return MPPI_OK;
+}
+}  // namespace mppi
 
 extern "C" mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, const double* const* h_states,
                                         const float* const* h_warm, float* const* h_out_mean,
@@ -643,14 +710,8 @@ extern "C" mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, co
     for (int i = 0; i < count; ++i) {
         mppi_ctx* c = ctxs[i];
         if (!c || !h_states[i] || !h_out_mean[i]) return MPPI_ERR_INVALID_ARG;
-        if (c->device != dev) {
-            set_error(nullptr, "batched contexts must live on the current device");
-            return MPPI_ERR_UNSUPPORTED;
-        }
-        if (c->mapping != MPPI_MAP_WARP && c->mapping != MPPI_MAP_HALFWARP && c->mapping != MPPI_MAP_CHAIN) {
-            set_error(nullptr, "batched contexts need the warp, half-warp or chain mapping");
-            return MPPI_ERR_UNSUPPORTED;
-        }
+        mppi_status st = check_batchable(c, dev);
+        if (st != MPPI_OK) return st;
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) {
                 set_error(nullptr, "a context appears twice in one batch");

@@ -1,4 +1,5 @@
 // Lanes-per-chain rollout kernel (see rollout_chain.cuh).
+#pragma once
 #include "rollout_chain.cuh"
 
 namespace mppi {

@@ -2,6 +2,7 @@
 // chunked weights with FP64 partial knot sums (Eqs. omega-weights / softmax_minmax,
 // Eq. update-nominal) and the iteration's finalize (log-sum-exp, mean, best tracking of
 // Sec. III-D).
+#pragma once
 #include "internal.h"
 #include "noise.cuh"
 #include "reduce.cuh"

@@ -21,7 +21,7 @@ struct NoiseParams {
 };
 
 // Samples [n0, n0 + cnt) (cnt <= NOISE_SPB) by the whole block; eps: shared [NOISE_SPB][E].
-__device__ __forceinline__ void block_sample_knots(const NoiseParams& a, int n0, int cnt, float* eps) {
+__device__ __noinline__ void block_sample_knots(const NoiseParams& a, int n0, int cnt, float* eps) {
     const int E = a.nk * 2 * a.nj;
     const int B4 = (E + 3) / 4;
     for (int idx = threadIdx.x; idx < cnt * B4; idx += blockDim.x) {
@@ -47,8 +47,8 @@ __device__ __forceinline__ void block_sample_knots(const NoiseParams& a, int n0,
         const int k = rem / a.nj, j = rem - k * a.nj;
         const int eq = (2 * k) * a.nj + j, ev = eq + a.nj;
         const float sg = a.sigma_row[k];
-        float q = a.nominal[eq] + sg * a.scale_q * eps[nl * E + eq];
-        float v = a.nominal[ev] + sg * a.scale_v * eps[nl * E + ev];
+        float q = __fmaf_rn(__fmul_rn(sg, a.scale_q), eps[nl * E + eq], a.nominal[eq]);
+        float v = __fmaf_rn(__fmul_rn(sg, a.scale_v), eps[nl * E + ev], a.nominal[ev]);
         if (a.has_limits) {
             const float lo = a.model->q_min[j + 1], hi = a.model->q_max[j + 1];
             if (isfinite(lo) || isfinite(hi)) {

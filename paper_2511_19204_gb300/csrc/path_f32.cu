@@ -1,6 +1,12 @@
-// FP32 product instantiations of the warp-per-sample rollout and dynamics kernels.
+// Every FP32 kernel of the path in one translation unit: the per-iteration kernels, the
+// rollout kernels of every mapping and the persistent batched kernel call the same
+// non-inlined device functions (noise, rollouts, chunk weights, finalize), so a batched
+// instance and a single solve run identical machine code and produce identical bits.
 #include "internal.h"
 #include "rollout_warp.cuh"
+#include "iter_kernels.cuh"
+#include "chain_kernel.cuh"
+#include "batch_impl.cuh"
 
 namespace mppi {
 cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s) {

@@ -89,7 +89,7 @@ __device__ __forceinline__ double unnorm_weight(float c, const MinMax& mm, doubl
 // One (chunk, element tile) block: weights of the chunk and its partial knot sums.
 // e_out (nullable) [N], zq [nchunks][2], partial [nchunks][E]. Element tile ey covers
 // elements [ey * blockDim.x, (ey + 1) * blockDim.x).
-__device__ __forceinline__ void chunk_weights_average(const float* __restrict__ costs, const float* __restrict__ knots,
+__device__ __noinline__ void chunk_weights_average(const float* __restrict__ costs, const float* __restrict__ knots,
                                                       int N, int E, double lambda, int normalize, int c, int ey,
                                                       double* __restrict__ e_out, double* __restrict__ zq,
                                                       double* __restrict__ partial, DevIterInfo* __restrict__ info) {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void chunk_weights_average(const float* __restrict__ 
         double z = 0.0, q = 0.0;
         for (int i = 0; i < cn; ++i) {
             z += s_e[i];
-            q += s_e[i] * s_e[i];
+            q = fma(s_e[i], s_e[i], q);
         }
         zq[2 * c] = z;
         zq[2 * c + 1] = q;
@@ -149,7 +149,7 @@ __device__ __forceinline__ double chunk_total(const double* __restrict__ partial
 // End of one iteration (one block, any size): lse and ESS, mean = sum_c P_c / z,
 // best-trajectory tracking over the solve (Sec. III-D), next nominal, and at the last
 // iteration the outputs, the resident warm start and the noise counter.
-__device__ __forceinline__ void finalize_iteration(const FinalizeArgs& a) {
+__device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
     __shared__ int s_update;
     __shared__ double s_z;
     const int t = threadIdx.x;

@@ -20,7 +20,7 @@ __device__ __forceinline__ float gsum(float v) {
 }
 
 template <int NLEG, int LLEN>
-__device__ __forceinline__ float chain_rollout(const DevModel<float>& M, int g, const double* __restrict__ x0,
+__device__ __noinline__ float chain_rollout(const DevModel<float>& M, int g, const double* __restrict__ x0,
                                                const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                                double* __restrict__ xf) {
     const int nj = M.nb - 1, nq = 7 + nj;

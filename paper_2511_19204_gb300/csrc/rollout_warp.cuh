@@ -359,7 +359,7 @@ __device__ __forceinline__ void store_lane_state(const DevModel<T>& M, const Lan
 // knots [nk][2][nj] (global), returning the Kahan-compensated cost sum on every lane.
 // x0: initial state [nx] (global, FP32 or FP64). xf: optional final state.
 template <typename T, int G, typename XT>
-__device__ __forceinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>& L, int gl,
+__device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>& L, int gl,
                                           const XT* __restrict__ x0, const float* __restrict__ knots, int H, int nk,
                                           T dt, T dtk, T* __restrict__ contrib, XT* __restrict__ xf) {
     const int nj = M.nb - 1;

@@ -112,6 +112,7 @@ SIGNATURES = [
     ("mppi_server_destroy", None, [_P]),
     ("mppi_submit", C.c_int32, [_P, _P, _dp, _fp, _u64p]),
     ("mppi_poll", C.c_int32, [_P, C.c_uint64, _fp, _fp, C.POINTER(mppi_result), C.c_int64]),
+    ("mppi_next_completed", C.c_int32, [_P, C.c_int64, _u64p, _i64p]),
     ("mppi_server_stats", C.c_int32, [_P, _i64p]),
     ("mppi_autotune", C.c_int32, [_P, _ip, _ip, _fp]),
     ("mppi_ctx_set_mapping", C.c_int32, [_P, C.c_int32, C.c_int32]),
@@ -397,3 +398,79 @@ def average(knots, w):
     out = np.zeros(E)
     _check(load().mppi_average(K, E, _pf(k.reshape(K, E)), _pd(_d(w)), _pd(out)))
     return out.reshape(k.shape[1:])
+
+
+def solve_batch(ctrls, states, warms=None, check=True):
+    """mppi_solve_batch over Controllers: returns (status, means, bests, infos)."""
+    L = load()
+    n = len(ctrls)
+    hs = (C.c_void_p * n)(*[c.h for c in ctrls])
+    st = [_d(x) for x in states]
+    wa = [(_f(w).reshape(-1) if w is not None else None) for w in (warms or [None] * n)]
+    means = [np.zeros(c.E, np.float32) for c in ctrls]
+    bests = [np.zeros(c.E, np.float32) for c in ctrls]
+    ps = (_dp * n)(*[_pd(x) for x in st])
+    pw = (_fp * n)(*[_pf(w) if w is not None else None for w in wa])
+    pm = (_fp * n)(*[_pf(m) for m in means])
+    pb = (_fp * n)(*[_pf(b) for b in bests])
+    info = (mppi_result * n)()
+    rc = L.mppi_solve_batch(hs, n, ps, pw, pm, pb, info)
+    if check:
+        _check(rc, ok=(MPPI_OK, MPPI_ERR_ALL_COSTS_NONFINITE))
+    return rc, [m.reshape(c.nk, 2, c.nj) for m, c in zip(means, ctrls)], \
+        [b.reshape(c.nk, 2, c.nj) for b, c in zip(bests, ctrls)], [info[i].as_dict() for i in range(n)]
+
+
+class Server:
+    """Continuous-batching request loop (mppi_server_create / submit / poll)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 8 << 30, max_inflight: int = 4):
+        h = _P()
+        _check(load().mppi_server_create(device, mem_budget_bytes, max_inflight, C.byref(h)))
+        self.h = h
+
+    def submit(self, ctrl: Controller, state, warm=None) -> int:
+        t = C.c_uint64()
+        x = _d(state)
+        w = _f(warm).reshape(-1) if warm is not None else None
+        _check(load().mppi_submit(self.h, ctrl.h, _pd(x), _pf(w), C.byref(t)), ctrl.h)
+        return t.value
+
+    def poll(self, ticket: int, ctrl: Controller, timeout_us: int = -1):
+        """(status, mean, best, info) or None while pending."""
+        mean = np.zeros(ctrl.E, np.float32)
+        best = np.zeros(ctrl.E, np.float32)
+        info = mppi_result()
+        st = load().mppi_poll(self.h, ticket, _pf(mean), _pf(best), C.byref(info), timeout_us)
+        if st == MPPI_PENDING:
+            return None
+        if st == MPPI_ERR_NOT_FOUND:
+            raise _err(st)
+        return st, mean.reshape(ctrl.nk, 2, ctrl.nj), best.reshape(ctrl.nk, 2, ctrl.nj), info.as_dict()
+
+    def next_completed(self, timeout_us: int = 0):
+        """(ticket, submit_ns, done_ns) or None."""
+        t = C.c_uint64()
+        tm = np.zeros(2, np.int64)
+        st = load().mppi_next_completed(self.h, timeout_us, C.byref(t), tm.ctypes.data_as(_i64p))
+        if st == MPPI_PENDING:
+            return None
+        _check(st)
+        return t.value, int(tm[0]), int(tm[1])
+
+    def stats(self):
+        o = np.zeros(5, np.int64)
+        _check(load().mppi_server_stats(self.h, o.ctypes.data_as(_i64p)))
+        return dict(submitted=int(o[0]), completed=int(o[1]), launches=int(o[2]), peak_bytes=int(o[3]),
+                    deferred=int(o[4]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mppi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
