@@ -26,7 +26,7 @@
 #include "capi_internal.h"
 #include "noise.cuh"
 #include "reduce.cuh"
-#include "rollout_chain.cuh"
+#include "rollout_lanes.cuh"
 
 namespace mppi {
 
@@ -239,8 +239,10 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 const int g = threadIdx.x & 3;
                 const int n = n0 + (threadIdx.x >> 2);
                 const int ne = min(n, last_n);
-                const float c = chain_rollout<4, 3>(*M, g, I.x0, I.knots + (size_t)ne * I.E, I.H, I.nk, I.dt, I.dtk,
-                                                    nullptr);
+                const float* kn = I.knots + (size_t)ne * I.E;
+                const float c = M->topology == TOPO_QUADRUPED
+                                    ? lanes_rollout<3, false>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
+                                    : lanes_rollout<6, true>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
                 if (n <= last_n && g == 0) I.costs[n] = c;
             } else if (I.mapping == MPPI_MAP_HALFWARP) {
                 const int gl = threadIdx.x & 15;

@@ -42,10 +42,66 @@ mppi_status cuda_fail(mppi_ctx* ctx, cudaError_t e, const char* what) {
 // ------------------------------------------------------------------------------------
 // Models
 // ------------------------------------------------------------------------------------
+// Tree shapes with a lanes-per-chain kernel, and their lane plans. Bodies must be
+// numbered chain by chain: a chain is a run of bodies each the child of the previous.
+struct LanePlan {
+    int topology = TOPO_GENERIC;
+    int b0[4] = {0, 0, 0, 0}, len[4] = {0, 0, 0, 0};
+    int branch = 0;
+};
+
+static bool is_chain(const mppi_model_desc& d, int first, int len, int parent) {
+    if (len < 1 || first + len > d.nb || d.parent[first] != parent) return false;
+    for (int j = 1; j < len; ++j)
+        if (d.parent[first + j] != first + j - 1) return false;
+    return true;
+}
+
+static LanePlan detect_topology(const mppi_model_desc& d) {
+    LanePlan P;
+    if (d.fixed_base) return P;
+    // base + 4 chains of L <= 3
+    if ((d.nb - 1) % 4 == 0) {
+        const int L = (d.nb - 1) / 4;
+        bool ok = L >= 1 && L <= 3;
+        for (int l = 0; l < 4 && ok; ++l) ok = is_chain(d, 1 + l * L, L, 0);
+        if (ok) {
+            P.topology = TOPO_QUADRUPED;
+            for (int l = 0; l < 4; ++l) {
+                P.b0[l] = 1 + l * L;
+                P.len[l] = L;
+            }
+            return P;
+        }
+    }
+    // base + 2 chains of A <= 6, a branch body on the base, 2 chains of C <= 6 on it
+    for (int A = 1; A <= 6; ++A) {
+        const int rest = d.nb - 1 - 2 * A - 1;
+        if (rest < 2 || rest % 2) continue;
+        const int C = rest / 2, br = 1 + 2 * A;
+        if (C > 6) continue;
+        if (is_chain(d, 1, A, 0) && is_chain(d, 1 + A, A, 0) && d.parent[br] == 0 && is_chain(d, br + 1, C, br) &&
+            is_chain(d, br + 1 + C, C, br)) {
+            P.topology = TOPO_HUMANOID;
+            P.b0[0] = 1;
+            P.len[0] = A;
+            P.b0[1] = 1 + A;
+            P.len[1] = A;
+            P.b0[2] = br + 1;
+            P.len[2] = C;
+            P.b0[3] = br + 1 + C;
+            P.len[3] = C;
+            P.branch = br;
+            return P;
+        }
+    }
+    return P;
+}
+
 template <typename T>
 static void fill_model(const mppi_model_desc& d, const std::vector<int>& level, int nlevels,
                        const std::vector<std::vector<int>>& children, const std::vector<int>& corder,
-                       int topology, DevModel<T>& M) {
+                       const LanePlan& plan, DevModel<T>& M) {
     memset(&M, 0, sizeof(M));
     const int nb = d.nb;
     for (int b = 0; b < nb; ++b) {
@@ -95,7 +151,12 @@ static void fill_model(const mppi_model_desc& d, const std::vector<int>& level, 
     for (int j = 0; j < nb - 1; ++j)
         if (isfinite(d.q_min[j]) || isfinite(d.q_max[j])) lim = 1;
     M.has_limits = lim;
-    M.topology = topology;
+    M.topology = plan.topology;
+    for (int l = 0; l < 4; ++l) {
+        M.lane_b0[l] = plan.b0[l];
+        M.lane_len[l] = plan.len[l];
+    }
+    M.branch_body = plan.branch;
     M.contact_k = (T)d.contact_k;
     M.contact_c = (T)d.contact_c;
     M.mu = (T)d.mu;
@@ -107,21 +168,6 @@ static void fill_model(const mppi_model_desc& d, const std::vector<int>& level, 
     M.w_vx = (T)d.w_vx;
     M.w_tilt = (T)d.w_tilt;
     M.w_tau = (T)d.w_tau;
-}
-
-// Tree shapes with a specialised thread-per-sample kernel.
-static int detect_topology(const mppi_model_desc& d) {
-    // quadruped: base + 4 chains of 3 (bodies 1..12), one contact on each chain end
-    if (d.nb == 13 && !d.fixed_base && d.nc == 4) {
-        bool ok = true;
-        for (int l = 0; l < 4 && ok; ++l) {
-            const int h = 1 + 3 * l;
-            ok = d.parent[h] == 0 && d.parent[h + 1] == h && d.parent[h + 2] == h + 1;
-        }
-        for (int c = 0; c < 4 && ok; ++c) ok = d.contact_body[c] == 3 + 3 * c;
-        if (ok) return TOPO_QUADRUPED;
-    }
-    return TOPO_GENERIC;
 }
 
 }  // namespace mppi
@@ -199,9 +245,10 @@ mppi_status mppi_model_create(const mppi_model_desc* d, mppi_model** out) {
     m->nj = d->nb - 1;
     m->nc = d->nc;
     m->fixed_base = d->fixed_base != 0;
-    m->topology = detect_topology(*d);
-    fill_model(*d, level, nlevels, children, corder, m->topology, m->host_f);
-    fill_model(*d, level, nlevels, children, corder, m->topology, m->host_d);
+    const LanePlan plan = detect_topology(*d);
+    m->topology = plan.topology;
+    fill_model(*d, level, nlevels, children, corder, plan, m->host_f);
+    fill_model(*d, level, nlevels, children, corder, plan, m->host_d);
     m->q_init.assign(m->nj, 0.f);
     if (d->q_init)
         for (int j = 0; j < m->nj; ++j) m->q_init[j] = (float)d->q_init[j];

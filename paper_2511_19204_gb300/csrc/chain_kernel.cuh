@@ -1,39 +1,40 @@
-// Lanes-per-chain rollout kernel (see rollout_chain.cuh).
+// Lanes-per-chain rollout kernels (see rollout_lanes.cuh).
 #pragma once
-#include "rollout_chain.cuh"
+#include "rollout_lanes.cuh"
 
 namespace mppi {
 
-template <int NLEG, int LLEN>
-__global__ void __launch_bounds__(256) rollout_chain_kernel(RolloutArgs<float> a) {
+template <int LMAX, bool BRANCH>
+__global__ void __launch_bounds__(256) rollout_lanes_kernel(RolloutArgs<float> a) {
     __shared__ __align__(16) DevModel<float> Ms;
     __shared__ uint64_t mbar;
     if (!bulk_load_to_smem(&Ms, a.model, (uint32_t)sizeof(DevModel<float>), &mbar)) {
         if (threadIdx.x == 0 && a.status) atomicOr(a.status, DEV_ERR_TMA_TIMEOUT);
         return;
     }
-    const int g = threadIdx.x % NLEG;
-    const int n = (blockIdx.x * blockDim.x + threadIdx.x) / NLEG;
+    const int g = threadIdx.x % LANES;
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
     const bool active = n < a.N;
     const int ne = active ? n : a.N - 1;
     const int nj = Ms.nb - 1;
     const int E = a.nk * 2 * nj;
     const int nx = 13 + 2 * nj;
     double* xf = (active && a.finals) ? a.finals + (size_t)n * nx : nullptr;
-    const float c = chain_rollout<NLEG, LLEN>(Ms, g, a.x0, a.knots + (size_t)ne * E, a.H, a.nk, a.dt, a.dtk, xf);
+    const float c = lanes_rollout<LMAX, BRANCH>(Ms, g, a.x0, a.knots + (size_t)ne * E, a.H, a.nk, a.dt, a.dtk, xf);
     if (active && g == 0) a.costs[n] = c;
 }
 
-bool chain_mapping_supported(int topology) { return topology == TOPO_QUADRUPED; }
+bool chain_mapping_supported(int topology) { return topology == TOPO_QUADRUPED || topology == TOPO_HUMANOID; }
 
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, int block, cudaStream_t s) {
-    if (topology != TOPO_QUADRUPED) return cudaErrorNotSupported;
+    if (!chain_mapping_supported(topology)) return cudaErrorNotSupported;
     if (block <= 0) block = 128;
     if (block % 32 != 0 || block > 256) return cudaErrorInvalidValue;
-    const int spb = block / 4;
+    const int spb = block / LANES;
     const int grid = (a.N + spb - 1) / spb;
     if (grid == 0) return cudaSuccess;
-    rollout_chain_kernel<4, 3><<<grid, block, 0, s>>>(a);
+    if (topology == TOPO_QUADRUPED) rollout_lanes_kernel<3, false><<<grid, block, 0, s>>>(a);
+    else rollout_lanes_kernel<6, true><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

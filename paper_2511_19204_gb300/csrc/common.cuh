@@ -61,17 +61,19 @@ struct alignas(16) DevModel {
     int32_t child[MAXCH][MAXB];
     int32_t cfirst[MAXB];
     int32_t ccount[MAXB];
+    int32_t lane_b0[4];   // lanes-per-chain plan: first body of each lane's chain
+    int32_t lane_len[4];  // and its length
     int32_t nb, nc, nlevels, fixed_base;
-    int32_t cost_body, has_limits, topology, pad0;
+    int32_t cost_body, has_limits, topology, branch_body;
     T contact_k, contact_c, mu, eps_f;
     T gravity, z_des, vx_des, w_z;
     T w_vx, w_tilt, w_tau, pad1;
 };
 
-// Robot trees with a specialised thread-per-sample kernel.
+// Tree shapes with a lanes-per-chain kernel.
 constexpr int TOPO_GENERIC = 0;
-constexpr int TOPO_QUADRUPED = 1;   // 4 x (hip, thigh, calf) chains off the base, foot on calf
-constexpr int TOPO_HUMANOID = 2;
+constexpr int TOPO_QUADRUPED = 1;   // 4 chains of <= 3 bodies off the base
+constexpr int TOPO_HUMANOID = 2;    // 2 chains of <= 6 off the base + a branch body with 2 chains of <= 6
 
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64-bit

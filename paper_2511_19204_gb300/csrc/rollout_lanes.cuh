@@ -1,0 +1,439 @@
+// Lanes-per-chain rollout (device function): 4 lanes share one sample of a tree made of a
+// floating base, chains hanging from it, and optionally one branch body that carries two
+// of the chains (the quadruped: 4 leg chains of 3 bodies; the humanoid: 2 leg chains of 6
+// from the pelvis, and the torso carrying 2 arm chains of 4).
+//
+// Lane g runs its chain's three articulated-body passes serially in registers. The base
+// is replicated on the 4 lanes and the branch body on the two lanes whose chains hang
+// from it; the arm chains' articulated inertias meet at the branch by a pair shuffle, and
+// everything meets at the base by a 2-step butterfly. Those sums are commutative
+// exchanges, so every replica sees bitwise the same numbers and the replicated base and
+// branch never diverge. Equations as in the warp-per-sample kernel: Featherstone's
+// articulated-body algorithm, Sec. III-A Hermite setpoints, Sec. III-C PD tracking,
+// semi-implicit Euler, Kahan-summed running cost.
+#pragma once
+#include "internal.h"
+#include "rollout_warp.cuh"
+
+namespace mppi {
+
+constexpr int LANES = 4;
+
+__device__ __forceinline__ float lsum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1, LANES);
+    v += __shfl_xor_sync(0xffffffffu, v, 2, LANES);
+    return v;
+}
+
+// What a body keeps between passes. x0/x1 hold the bias (n, f) after pass 1 and the
+// scaled U_ang / D, U_lin / D after pass 2; uu = u / D.
+struct BodyMem {
+    float s, c;
+    V3<float> cw, cv;
+    V3<float> x0, x1;
+    float uu;
+};
+
+struct Pose {
+    M3<float> R;
+    V3<float> p, w, v;
+};
+
+__device__ __forceinline__ V3<float> axis_of(const DevModel<float>& M, int b) {
+    return v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
+}
+__device__ __forceinline__ V3<float> jpos_of(const DevModel<float>& M, int b) {
+    return v3(M.jpos[0][b], M.jpos[1][b], M.jpos[2][b]);
+}
+
+__device__ __forceinline__ void body_contacts(const DevModel<float>& M, int b, const Pose& P, V3<float>& fen,
+                                              V3<float>& fef) {
+    const int c0 = M.cfirst[b], cn = M.ccount[b];
+    for (int c = 0; c < cn; ++c) {
+        const int ci = c0 + c;
+        const V3<float> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
+        const V3<float> pc = P.p + mul(P.R, rc);
+        const float depth = -pc.z;
+        if (depth > 0.f) {
+            const V3<float> vw = mul(P.R, P.v + cross(P.w, rc));
+            const float fn = fmaxf(M.contact_k * depth - M.contact_c * vw.z, 0.f);
+            const float sc = -M.mu * fn / sqrtf(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
+            const V3<float> F = v3(sc * vw.x, sc * vw.y, fn);
+            const V3<float> fb = mulT(P.R, F);
+            fef = fef + fb;
+            fen = fen + cross(rc, fb);
+        }
+    }
+}
+
+// v x* (I v) - f_ext for body b (see the warp kernel for the exact-cancellation form).
+__device__ __forceinline__ void body_bias(const DevModel<float>& M, int b, const Pose& P, V3<float> fen, V3<float> fef,
+                                          V3<float>& pn, V3<float>& pf) {
+    const float Ao[6] = {M.Ao[0][b], M.Ao[1][b], M.Ao[2][b], M.Ao[3][b], M.Ao[4][b], M.Ao[5][b]};
+    const V3<float> mc = v3(M.mc[0][b], M.mc[1][b], M.mc[2][b]);
+    const V3<float> mcw = cross(mc, P.w);
+    const V3<float> hn = sym_mul(Ao, P.w) + cross(mc, P.v);
+    const V3<float> hf = M.mass[b] * P.v - mcw;
+    pn = cross(P.w, hn) - cross(P.v, mcw) - fen;
+    pf = cross(P.w, hf) - fef;
+}
+
+__device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Art<float>& IA) {
+    const V3<float> mc = v3(M.mc[0][b], M.mc[1][b], M.mc[2][b]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) IA.A[t] = M.Ao[t][b];
+    IA.B[0] = 0.f;
+    IA.B[1] = -mc.z;
+    IA.B[2] = mc.y;
+    IA.B[3] = mc.z;
+    IA.B[4] = 0.f;
+    IA.B[5] = -mc.x;
+    IA.B[6] = -mc.y;
+    IA.B[7] = mc.x;
+    IA.B[8] = 0.f;
+    IA.C[0] = IA.C[1] = IA.C[2] = M.mass[b];
+    IA.C[3] = IA.C[4] = IA.C[5] = 0.f;
+}
+
+// Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
+// the bias (contact forces included).
+__device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, float q, float qd, const Pose& Pp,
+                                           Pose& P, BodyMem& m) {
+    const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
+    sincosf(q, &m.s, &m.c);
+    const M3<float> Rj = axis_rotation(a, m.s, m.c);
+    P.R = mul(Pp.R, Rj);
+    P.p = Pp.p + mul(Pp.R, r);
+    P.w = mulT(Rj, Pp.w) + qd * a;
+    P.v = mulT(Rj, Pp.v - cross(r, Pp.w));
+    const V3<float> sa = qd * a;
+    m.cw = cross(P.w, sa);
+    m.cv = cross(P.v, sa);
+    V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
+    body_contacts(M, b, P, fen, fef);
+    body_bias(M, b, P, fen, fef, m.x0, m.x1);
+}
+
+// Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
+// then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D.
+__device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, float tau, BodyMem& m, bool has_carry,
+                                           Art<float>& carry, V3<float>& cpn, V3<float>& cpf) {
+    const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
+    Art<float> IA;
+    body_inertia(M, b, IA);
+    V3<float> pAn = m.x0, pAf = m.x1;
+    if (has_carry) {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) IA.A[t] += carry.A[t];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) IA.B[t] += carry.B[t];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) IA.C[t] += carry.C[t];
+        pAn = pAn + cpn;
+        pAf = pAf + cpf;
+    }
+    const V3<float> ua = sym_mul(IA.A, a);
+    const V3<float> ul = v3(IA.B[0] * a.x + IA.B[3] * a.y + IA.B[6] * a.z, IA.B[1] * a.x + IA.B[4] * a.y + IA.B[7] * a.z,
+                            IA.B[2] * a.x + IA.B[5] * a.y + IA.B[8] * a.z);
+    const float invD = 1.f / (dot(a, ua) + M.armature[b]);
+    const float u = tau - dot(a, pAn);
+    const float U[6] = {ua.x, ua.y, ua.z, ul.x, ul.y, ul.z};
+    Art<float> Ia;
+    Ia.A[0] = IA.A[0] - U[0] * U[0] * invD;
+    Ia.A[1] = IA.A[1] - U[1] * U[1] * invD;
+    Ia.A[2] = IA.A[2] - U[2] * U[2] * invD;
+    Ia.A[3] = IA.A[3] - U[0] * U[1] * invD;
+    Ia.A[4] = IA.A[4] - U[0] * U[2] * invD;
+    Ia.A[5] = IA.A[5] - U[1] * U[2] * invD;
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) Ia.B[3 * i2 + j2] = IA.B[3 * i2 + j2] - U[i2] * U[3 + j2] * invD;
+    Ia.C[0] = IA.C[0] - U[3] * U[3] * invD;
+    Ia.C[1] = IA.C[1] - U[4] * U[4] * invD;
+    Ia.C[2] = IA.C[2] - U[5] * U[5] * invD;
+    Ia.C[3] = IA.C[3] - U[3] * U[4] * invD;
+    Ia.C[4] = IA.C[4] - U[3] * U[5] * invD;
+    Ia.C[5] = IA.C[5] - U[4] * U[5] * invD;
+    const float ud = u * invD;
+    const M3<float>& Bm = *reinterpret_cast<const M3<float>*>(Ia.B);
+    const V3<float> pan = pAn + sym_mul(Ia.A, m.cw) + mul(Bm, m.cv) + ud * ua;
+    const V3<float> paf = pAf + mulT(Bm, m.cw) + sym_mul(Ia.C, m.cv) + ud * ul;
+    const M3<float> Rj = axis_rotation(a, m.s, m.c);
+    art_to_parent(Ia, Rj, r, carry);
+    cpf = mul(Rj, paf);
+    cpn = mul(Rj, pan) + cross(r, cpf);
+    m.x0 = invD * ua;
+    m.x1 = invD * ul;
+    m.uu = ud;
+}
+
+// Pass 3 of body b: from the parent's acceleration (apw, apv, offset by gravity) to its
+// own, and its joint acceleration.
+__device__ __forceinline__ float body_pass3(const DevModel<float>& M, int b, const BodyMem& m, V3<float>& apw,
+                                            V3<float>& apv) {
+    const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
+    const M3<float> Rj = axis_rotation(a, m.s, m.c);
+    const V3<float> a1w = mulT(Rj, apw) + m.cw;
+    const V3<float> a1v = mulT(Rj, apv - cross(r, apw)) + m.cv;
+    const float qdd = m.uu - dot(m.x0, a1w) - dot(m.x1, a1v);
+    apw = a1w + qdd * a;
+    apv = a1v;
+    return qdd;
+}
+
+__device__ __forceinline__ float hermite_pd(const DevModel<float>& M, int b, const float* __restrict__ knots, int nj,
+                                            int k, float s, float dtk, float inv_dtk, float q, float qd) {
+    const int j = b - 1;
+    const float q0 = knots[(k * 2 + 0) * nj + j], v0 = knots[(k * 2 + 1) * nj + j];
+    const float q1 = knots[((k + 1) * 2 + 0) * nj + j], v1 = knots[((k + 1) * 2 + 1) * nj + j];
+    const float s2 = s * s, s3 = s2 * s;
+    const float h00 = 2.f * s3 - 3.f * s2 + 1.f, h10 = s3 - 2.f * s2 + s;
+    const float h01 = -2.f * s3 + 3.f * s2, h11 = s3 - s2;
+    const float d00 = 6.f * s2 - 6.f * s, d10 = 3.f * s2 - 4.f * s + 1.f;
+    const float d01 = -6.f * s2 + 6.f * s, d11 = 3.f * s2 - 2.f * s;
+    const float qref = h00 * q0 + h10 * dtk * v0 + h01 * q1 + h11 * dtk * v1;
+    const float vref = (d00 * q0 + d01 * q1) * inv_dtk + d10 * v0 + d11 * v1;
+    return sc_clamp(M.kp[b] * (qref - q) + M.kd[b] * (vref - qd), -M.tau_max[b], M.tau_max[b]);
+}
+
+__device__ __forceinline__ void cost_terms(const DevModel<float>& M, const Pose& P, float& tz, float& tt) {
+    const float dz = P.p.z - M.z_des;
+    const float tilt = atan2f(sqrtf(P.R.m[2] * P.R.m[2] + P.R.m[5] * P.R.m[5]), P.R.m[8]);
+    tz = M.w_z * dz * dz;
+    tt = M.w_tilt * tilt * tilt;
+}
+
+// One sample's rollout by the 4 lanes of its group (g = lane within the group).
+// The lane plan (first body and length of each lane's chain, the branch body and which
+// lanes carry it) is in the model: lane_b0, lane_len, branch.
+template <int LMAX, bool BRANCH>
+__device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, const double* __restrict__ x0,
+                                            const float* __restrict__ knots, int H, int nk, float dt, float dtk,
+                                            double* __restrict__ xf) {
+    const int nj = M.nb - 1, nq = 7 + nj;
+    const int b0 = M.lane_b0[g], len = M.lane_len[g];
+    const int bb = BRANCH ? M.branch_body : 0;
+    const bool on_branch = BRANCH && g >= 2;  // lanes 2 and 3 carry the branch body
+    // base (replicated), branch joint (replicated on lanes 2, 3), chain joints
+    Pose B;
+    V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
+    float qw = (float)x0[3], qx = (float)x0[4], qy = (float)x0[5], qz = (float)x0[6];
+    V3<float> vl = v3((float)x0[nq], (float)x0[nq + 1], (float)x0[nq + 2]);
+    V3<float> w = v3((float)x0[nq + 3], (float)x0[nq + 4], (float)x0[nq + 5]);
+    float qb = 0.f, qdb = 0.f;
+    if (BRANCH) {
+        qb = (float)x0[7 + bb - 1];
+        qdb = (float)x0[nq + 6 + bb - 1];
+    }
+    float q[LMAX], qd[LMAX];
+#pragma unroll
+    for (int j = 0; j < LMAX; ++j) {
+        q[j] = j < len ? (float)x0[7 + b0 - 1 + j] : 0.f;
+        qd[j] = j < len ? (float)x0[nq + 6 + b0 - 1 + j] : 0.f;
+    }
+    const float inv_dtk = 1.0f / dtk;
+    float sum = 0.f, comp = 0.f;
+    const int cb = M.cost_body;
+    int cowner = 0;  // lane that owns the cost body (0 for the base: every lane has it)
+    for (int l = 0; l < LANES; ++l)
+        if (cb >= M.lane_b0[l] && cb < M.lane_b0[l] + M.lane_len[l]) cowner = l;
+    if (BRANCH && cb == bb) cowner = 2;
+    for (int h = 0; h < H; ++h) {
+        const int r = h * (nk - 1);
+        int k = r / H;
+        if (k > nk - 2) k = nk - 2;
+        const float s = (float)(r - k * H) / (float)H;
+        float tau[LMAX], taub = 0.f;
+#pragma unroll
+        for (int j = 0; j < LMAX; ++j)
+            tau[j] = j < len ? hermite_pd(M, b0 + j, knots, nj, k, s, dtk, inv_dtk, q[j], qd[j]) : 0.f;
+        if (on_branch) taub = hermite_pd(M, bb, knots, nj, k, s, dtk, inv_dtk, qb, qdb);
+        // ---- pass 1 ----
+        B.R = quat_to_R(qw, qx, qy, qz);
+        B.p = p;
+        B.w = M.fixed_base ? v3(0.f, 0.f, 0.f) : w;
+        B.v = M.fixed_base ? v3(0.f, 0.f, 0.f) : vl;
+        V3<float> p0n, p0f;
+        {
+            V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
+            body_contacts(M, 0, B, fen, fef);
+            body_bias(M, 0, B, fen, fef, p0n, p0f);
+        }
+        float tz = 0.f, tt = 0.f;
+        if (cb == 0) cost_terms(M, B, tz, tt);
+        BodyMem mb;
+        Pose PB;
+        if (on_branch) {
+            body_pass1(M, bb, qb, qdb, B, PB, mb);
+            if (cb == bb) cost_terms(M, PB, tz, tt);
+        }
+        BodyMem mem[LMAX];
+        {
+            Pose Pp = on_branch ? PB : B;
+#pragma unroll
+            for (int j = 0; j < LMAX; ++j) {
+                if (j < len) {
+                    Pose P;
+                    body_pass1(M, b0 + j, q[j], qd[j], Pp, P, mem[j]);
+                    if (cb == b0 + j) cost_terms(M, P, tz, tt);
+                    Pp = P;
+                }
+            }
+        }
+        if (cb != 0) {
+            tz = __shfl_sync(0xffffffffu, tz, cowner, LANES);
+            tt = __shfl_sync(0xffffffffu, tt, cowner, LANES);
+        }
+        // ---- pass 2 ----
+        Art<float> carry;
+        V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
+#pragma unroll
+        for (int j = LMAX - 1; j >= 0; --j)
+            if (j < len) body_pass2(M, b0 + j, tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+        if (BRANCH) {
+            // arms meet at the branch body: own + partner (lanes 2 <-> 3), identical on both
+            Art<float> sumc;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) sumc.A[t] = carry.A[t] + __shfl_xor_sync(0xffffffffu, carry.A[t], 1, LANES);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) sumc.B[t] = carry.B[t] + __shfl_xor_sync(0xffffffffu, carry.B[t], 1, LANES);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) sumc.C[t] = carry.C[t] + __shfl_xor_sync(0xffffffffu, carry.C[t], 1, LANES);
+            const V3<float> sn = v3(cpn.x + __shfl_xor_sync(0xffffffffu, cpn.x, 1, LANES),
+                                    cpn.y + __shfl_xor_sync(0xffffffffu, cpn.y, 1, LANES),
+                                    cpn.z + __shfl_xor_sync(0xffffffffu, cpn.z, 1, LANES));
+            const V3<float> sf = v3(cpf.x + __shfl_xor_sync(0xffffffffu, cpf.x, 1, LANES),
+                                    cpf.y + __shfl_xor_sync(0xffffffffu, cpf.y, 1, LANES),
+                                    cpf.z + __shfl_xor_sync(0xffffffffu, cpf.z, 1, LANES));
+            if (on_branch) {
+                carry = sumc;
+                cpn = sn;
+                cpf = sf;
+                body_pass2(M, bb, taub, mb, true, carry, cpn, cpf);
+                if (g == 3) {  // lane 2 alone hands the branch to the base
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) carry.A[t] = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) carry.B[t] = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) carry.C[t] = 0.f;
+                    cpn = v3(0.f, 0.f, 0.f);
+                    cpf = cpn;
+                }
+            }
+        }
+        // ---- base: every lane's contribution (butterfly), solve ----
+        Art<float> IA0;
+        body_inertia(M, 0, IA0);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) IA0.A[t] += lsum(carry.A[t]);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) IA0.B[t] += lsum(carry.B[t]);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) IA0.C[t] += lsum(carry.C[t]);
+        p0n = p0n + v3(lsum(cpn.x), lsum(cpn.y), lsum(cpn.z));
+        p0f = p0f + v3(lsum(cpf.x), lsum(cpf.y), lsum(cpf.z));
+        const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
+        V3<float> aw, av;
+        if (M.fixed_base) {
+            aw = v3(0.f, 0.f, 0.f);
+            av = v3(-g_b.x, -g_b.y, -g_b.z);
+        } else {
+            const float rhs[6] = {-p0n.x, -p0n.y, -p0n.z, -p0f.x, -p0f.y, -p0f.z};
+            float x[6];
+            art_solve(IA0, rhs, x);
+            aw = v3(x[0], x[1], x[2]);
+            av = v3(x[3], x[4], x[5]);
+        }
+        // ---- pass 3 ----
+        float qdd[LMAX], qddb = 0.f;
+        {
+            V3<float> apw = aw, apv = av;
+            if (on_branch) qddb = body_pass3(M, bb, mb, apw, apv);
+#pragma unroll
+            for (int j = 0; j < LMAX; ++j) qdd[j] = j < len ? body_pass3(M, b0 + j, mem[j], apw, apv) : 0.f;
+        }
+        // ---- running cost on the pre-step state ----
+        float te = 0.f;
+#pragma unroll
+        for (int j = 0; j < LMAX; ++j) te += tau[j] * tau[j];
+        if (g == 2) te += taub * taub;
+        te = lsum(te);
+        {
+            const float vx = M.fixed_base ? 0.f : (B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z);
+            const float dv = vx - M.vx_des;
+            const float c = tz + M.w_vx * dv * dv + tt + M.w_tau * te;
+            const float y = c - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        // ---- semi-implicit Euler ----
+#pragma unroll
+        for (int j = 0; j < LMAX; ++j) {
+            qd[j] += dt * qdd[j];
+            q[j] += dt * qd[j];
+        }
+        if (on_branch) {
+            qdb += dt * qddb;
+            qb += dt * qdb;
+        }
+        if (!M.fixed_base) {
+            w = w + dt * aw;
+            vl = vl + dt * (av + g_b);
+            p = p + dt * mul(B.R, vl);
+            const float wn = sqrtf(dot(w, w));
+            float dq0, dqs;
+            if (wn * dt < 1e-12f) {
+                dq0 = 1.f;
+                dqs = 0.5f * dt;
+            } else {
+                float sh, ch;
+                sincosf(0.5f * wn * dt, &sh, &ch);
+                dq0 = ch;
+                dqs = sh / wn;
+            }
+            const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
+            const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
+            const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
+            const float ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
+            const float nz = qw * dz + qx * dy - qy * dx + qz * dq0;
+            const float inv = 1.f / sqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
+            qw = nw * inv;
+            qx = nx * inv;
+            qy = ny * inv;
+            qz = nz * inv;
+        }
+    }
+    if (xf) {
+        if (g == 0) {
+            xf[0] = p.x;
+            xf[1] = p.y;
+            xf[2] = p.z;
+            xf[3] = qw;
+            xf[4] = qx;
+            xf[5] = qy;
+            xf[6] = qz;
+            xf[nq] = vl.x;
+            xf[nq + 1] = vl.y;
+            xf[nq + 2] = vl.z;
+            xf[nq + 3] = w.x;
+            xf[nq + 4] = w.y;
+            xf[nq + 5] = w.z;
+        }
+        if (BRANCH && g == 2) {
+            xf[7 + bb - 1] = qb;
+            xf[nq + 6 + bb - 1] = qdb;
+        }
+#pragma unroll
+        for (int j = 0; j < LMAX; ++j)
+            if (j < len) {
+                xf[7 + b0 - 1 + j] = q[j];
+                xf[nq + 6 + b0 - 1 + j] = qd[j];
+            }
+    }
+    return sum;
+}
+
+}  // namespace mppi

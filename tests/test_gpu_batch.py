@@ -25,7 +25,7 @@ def _mix(M):
     specs = [  # (model, robot, mapping, K, H, nk, iters, lam, seed)
         (mq, quad, 2, 97, 60, 4, 1, 0.1, 1), (mq, quad, 2, 256, 120, 6, 3, 0.2, 2),
         (mq, quad, 1, 33, 50, 5, 1, 0.3, 3), (mq, quad, 0, 40, 40, 4, 2, 0.1, 4),
-        (mh, hum, 0, 70, 50, 8, 1, 0.05, 5), (mh, hum, 0, 129, 30, 7, 2, 0.5, 6),
+        (mh, hum, 0, 70, 50, 8, 1, 0.05, 5), (mh, hum, 2, 129, 30, 7, 2, 0.5, 6), (mh, hum, 2, 300, 40, 4, 1, 0.2, 9),
         (mq, quad, 2, 1, 20, 4, 1, 0.1, 7), (mq, quad, 2, 65, 100, 8, 1, 0.25, 8),
     ]
     out = []

@@ -117,7 +117,8 @@ def _lifted(m, seed):
     return x
 
 
-@pytest.mark.parametrize("name,mapping", [("quadruped", 0), ("quadruped", 1), ("quadruped", 2), ("humanoid", 0)])
+@pytest.mark.parametrize("name,mapping", [("quadruped", 0), ("quadruped", 1), ("quadruped", 2), ("humanoid", 0),
+                                          ("humanoid", 2)])
 def test_rollout_contact_free(M, orc, name, mapping):
     # 50 steps in the air: no contact ever acts, so FP32 stays within 1e-4 of FP64
     m = S.MODELS[name]()
@@ -174,8 +175,7 @@ def test_rollout_with_contact_fp64_check(M, orc, cfg):
     else:
         assert err_c.max() < 1e-9 and err_f.max() < 1e-9
     c.set_fp64_check(False)
-    if m.name == "quadruped":
-        c.set_mapping(M.MPPI_MAP_CHAIN)
+    c.set_mapping(M.MPPI_MAP_CHAIN)
     c32 = c.rollout_explicit(p.state, kn32)
     err = np.abs(c32 - ref_c) / np.abs(ref_c)
     print(f"{cfg}: FP32 contact-rollout cost rel. error median {np.median(err):.2e} max {err.max():.2e}")
@@ -192,22 +192,25 @@ def test_rollout_with_contact_fp64_check(M, orc, cfg):
         assert err.max() <= 10 * env.max() + 1e-6
 
 
-@pytest.mark.parametrize("n,block", [(1, 0), (37, 32), (300, 64), (1000, 128), (2049, 256)])
-def test_mappings_agree(M, orc, n, block):
+@pytest.mark.parametrize("robot,n,block", [("quadruped", 1, 0), ("quadruped", 37, 32), ("quadruped", 300, 64),
+                                           ("quadruped", 1000, 128), ("quadruped", 2049, 256), ("humanoid", 1, 0),
+                                           ("humanoid", 77, 64), ("humanoid", 513, 256)])
+def test_mappings_agree(M, orc, robot, n, block):
     # every rollout mapping runs the same algorithm: on the well-conditioned dt = 0.005
-    # workload they agree with each other and with the oracle to FP32 accuracy
-    p = S.scale_quadruped(n=n)
-    p.horizon = 120
+    # workloads they agree with each other and with the oracle to FP32 accuracy
+    p = S.scale_quadruped(n=n) if robot == "quadruped" else S.humanoid_problem(n=n)
+    p.horizon = 120 if robot == "quadruped" else 60
     kn = orc.sample_knots(p.model.nj, p.nk, n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed).astype(np.float32)
     c = M.Controller.from_problem(M.Model(p.model), p, mapping=0)
+    maps = (0, 1, 2) if robot == "quadruped" else (0, 2)
     out = {}
-    for mapping in (0, 1, 2):
+    for mapping in maps:
         c.set_mapping(mapping, block if (block or mapping != 1) else 0)
         out[mapping], fin = c.rollout_explicit(p.state, kn, finals=True)
         assert np.all(np.isfinite(fin))
     idx = np.arange(n) if n <= 64 else np.r_[0:16, n - 16:n]
     ref = orc.rollout_batch(p.model, p.state, kn.astype(np.float64)[idx], p.horizon, p.dt)
-    for mapping in (0, 1, 2):
+    for mapping in maps:
         err = np.abs(out[mapping][idx] - ref) / np.abs(ref)
         assert err.max() < 1e-4, (mapping, err.max())
         assert np.max(np.abs(out[mapping] - out[0]) / np.abs(out[0])) < 1e-4

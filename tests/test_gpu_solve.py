@@ -72,10 +72,11 @@ def test_ragged_sizes_and_three_iterations(M, orc):
         assert c.iter_counter == it
 
 
-def test_humanoid_solve_matches_oracle(M, orc):
+@pytest.mark.parametrize("mapping", [0, 2])
+def test_humanoid_solve_matches_oracle(M, orc, mapping):
     p = S.humanoid_problem(n=256)
     p.horizon = 100
-    c = M.Controller.from_problem(M.Model(p.model), p, mapping=M.MPPI_MAP_WARP)
+    c = M.Controller.from_problem(M.Model(p.model), p, mapping=mapping)
     mean, best, info = c.solve(p.state, warm=p.nominal.astype(np.float32))
     ref = orc.solve(p.model, p.n, p.nk, p.horizon, p.iters, p.dt, p.lam, p.sigma, p.state,
                     p.nominal.astype(np.float32).astype(np.float64), seed=p.seed)
