@@ -227,6 +227,24 @@ mppi_status mppi_weights(int32_t K, const float* h_costs, double lambda, int32_t
 mppi_status mppi_average(int32_t K, int32_t E, const float* h_knots, const double* h_w,
                          double* h_out);
 
+/* Allocation-free variant of mppi_average, for callers that cannot call cudaMalloc where
+ * they need the average: real-time loops that must not block on the allocator
+ * (cudaMalloc / cudaFree can synchronise the device), code with a fixed pre-reserved
+ * footprint, hosts whose allocator belongs to another framework. The paper has no
+ * counterpart; this is a deployment convenience.
+ * d_knots [K][E] FP32, d_w [K] FP64 and d_out [E] FP64 are the caller's device buffers;
+ * the work is enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and
+ * nothing is allocated or freed. The FP64 partial sums live in one file-scope device
+ * array of 2^20 doubles (8 MiB held on every device that loads the library), so
+ * ceil(K / 64) * E must not exceed 1048576 (else MPPI_ERR_INVALID_ARG). The first call on
+ * each device looks up that array's device address (cudaGetSymbolAddress, with the
+ * device current); make that first call before any stream capture. Every call shares
+ * the array and leaves its contents behind; each call writes every element it reads
+ * before reading it, so nothing needs clearing, but calls that overlap on the GPU (on
+ * different streams) race. Results equal mppi_average's. */
+mppi_status mppi_average_noalloc(int32_t K, int32_t E, const float* d_knots, const double* d_w, double* d_out,
+                                 void* stream);
+
 /* Single-step state derivative: generalised accelerations h_acc [n][nv] (base spatial
  * acceleration (w_dot, v_dot) in body coordinates, then qdd) of n states under
  * torques h_tau [n][nj], contact forces included, by the warp-per-sample articulated-

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
     ("mppi_average", C.c_int32, [C.c_int32, C.c_int32, _fp, _dp, _dp]),
+    ("mppi_average_noalloc", C.c_int32, [C.c_int32, C.c_int32, _P, _P, _P, _P]),
     ("mppi_forward_dynamics", C.c_int32, [_P, C.c_int32, _dp, _dp, _dp]),
     ("mppi_forward_dynamics_ex", C.c_int32, [_P, C.c_int32, _dp, _dp, _dp, C.c_int32]),
     ("mppi_solve_batch", C.c_int32, [C.POINTER(_P), C.c_int32, C.POINTER(_dp), C.POINTER(_fp),
