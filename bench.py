@@ -139,6 +139,41 @@ class Clocks:
 
 
 # ------------------------------------------------------------------------------------
+# DRAM traffic of the dominant kernel, from a committed ncu summary
+# ------------------------------------------------------------------------------------
+TRAFFIC_SOURCES = ["rollout_lanes.cuh", "chain_kernel.cuh", "common.cuh", "rollout_warp.cuh", "internal.h"]
+
+
+def sources_sha256(names=TRAFFIC_SOURCES) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2511_19204_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(name: str, samples: int):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from profiles/<name>.md,
+    scaled to `samples` if the capture used another count; None when the kernel's
+    sources changed since the capture (the summary records their SHA-256)."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source-sha256") != sources_sha256():
+        return None
+    try:
+        return float(vals["dram-bytes-per-launch"]) * samples / float(vals["samples"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on the host cores
 # ------------------------------------------------------------------------------------
 def cpu_baseline(n_samples: int):
@@ -252,7 +287,8 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1
     """Continuous-batching server under Poisson load: 512 closed-loop controllers (70 %
     quadruped, K log-uniform 256-2048, H 100-200, 4-8 knots), each request = current
     state + resident warm start; a controller's next request waits for its previous
-    result. Latency = server completion time - arrival time (CLOCK_MONOTONIC)."""
+    result. Latency = server completion time - arrival time (CLOCK_MONOTONIC) of the
+    requests arriving in the measurement window; throughput = completions inside it."""
     import heapq
     import math
 
@@ -291,7 +327,7 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1
         busy = [None] * n_ctrl          # outstanding ticket
         backlog = [[] for _ in range(n_ctrl)]  # arrival times waiting for the controller
         owner, arrival = {}, {}
-        lat, units = [], 0
+        lat, units, done_in_window = [], 0, 0
         t_end = now0 + int((seconds + warm_s) * 1e9)
         t_meas = now0 + int(warm_s * 1e9)
         s0 = srv.stats()
@@ -324,6 +360,8 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1
                 busy[i] = None
                 if t_arr >= t_meas and t_arr < t_end:
                     lat.append((t_done - t_arr) / 1e6)
+                if t_meas <= t_done < t_end:
+                    done_in_window += 1
                     units += work[i]
                 if backlog[i] and time.monotonic_ns() < t_end:
                     submit(i, backlog[i].pop(0))
@@ -335,7 +373,8 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1
         q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
         launches = s1["launches"] - s0["launches"]
         completed = s1["completed"] - s0["completed"]
-        out["loads"].append({"offered_req_per_s": load, "completed_req_per_s": len(lat) / seconds,
+        out["loads"].append({"offered_req_per_s": load, "completed_req_per_s": done_in_window / seconds,
+                             "saturated": done_in_window / seconds < 0.95 * load,
                              "rollout_steps_per_s": units / seconds, "latency_ms_p50": q(0.5),
                              "latency_ms_p99": q(0.99), "latency_ms_p999": q(0.999),
                              "mean_requests_per_launch": completed / max(launches, 1)})
@@ -436,7 +475,10 @@ def run_ours(args, rank, world, local):
                  "h2d_bytes_per_step": 8 * nx, "d2h_bytes_per_step": 4 * 2 * E + 48,
                  "ms_per_step": 1e3 * e2e_local / len(e2e_t)} if e2e_t else None),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "rollout",
+                     "frac": achieved / peak,
+                     "traffic": (profiled_traffic("rollout_lanes_quadruped", p.n)
+                                 if info["mapping"] == mppi.MPPI_MAP_CHAIN else None),
+                     "kernel": "rollout",
                      "flops_per_step_sample": fl_step, "launch_ms": roll_ms,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts and max clock)"},
         "gpu_launches": args.steps * ctrl.kernels_per_solve,

@@ -68,9 +68,10 @@ cudaError_t launch_weights_average(const float* costs, const float* knots, int N
 __global__ void normalize_weights_kernel(const double* __restrict__ e, const double* __restrict__ zq, int N,
                                          double* __restrict__ w, DevIterInfo* info) {
     __shared__ double s_z;
+    double zt = 0.0, qt = 0.0;
+    block_total_zq(zq, num_chunks(N), &zt, &qt);
     if (threadIdx.x == 0) {
-        double z = 0.0, q = 0.0;
-        total_zq(zq, num_chunks(N), &z, &q);
+        const double z = zt, q = qt;
         s_z = z;
         const bool ok = info->status == MPPI_OK;
         info->lse = ok ? log(z) : NAN;

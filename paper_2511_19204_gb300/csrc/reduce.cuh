@@ -128,15 +128,35 @@ __device__ __noinline__ void chunk_weights_average(const float* __restrict__ cos
     __syncthreads();
 }
 
-// z = sum of the chunks' z_c (increasing c), and sum of q_c.
-__device__ __forceinline__ void total_zq(const double* __restrict__ zq, int nchunks, double* z, double* q) {
-    double a = 0.0, b = 0.0;
-    for (int c = 0; c < nchunks; ++c) {
-        a += zq[2 * c];
-        b += zq[2 * c + 1];
+constexpr int FIN_SPLIT = 8;   // interleaved sub-sums per total in the finalize
+constexpr int FIN_TILE = 128;  // elements per finalize tile
+
+// Block-wide: z = sum_c z_c and q = sum_c q_c as FIN_SPLIT interleaved sub-sums (chunks
+// s, s + FIN_SPLIT, ... in increasing order) combined in sub-sum order; every thread
+// receives the totals. Needs blockDim.x >= 2 * FIN_SPLIT.
+__device__ __forceinline__ void block_total_zq(const double* __restrict__ zq, int nchunks, double* z, double* q) {
+    __shared__ double s_part[2 * FIN_SPLIT];
+    __shared__ double s_tot[2];
+    const int t = threadIdx.x;
+    if (t < 2 * FIN_SPLIT) {
+        const int sidx = t % FIN_SPLIT, which = t / FIN_SPLIT;
+        double acc = 0.0;
+        for (int c = sidx; c < nchunks; c += FIN_SPLIT) acc += zq[2 * c + which];
+        s_part[t] = acc;
     }
-    *z = a;
-    *q = b;
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0;
+        for (int sidx = 0; sidx < FIN_SPLIT; ++sidx) {
+            a += s_part[sidx];
+            b += s_part[FIN_SPLIT + sidx];
+        }
+        s_tot[0] = a;
+        s_tot[1] = b;
+    }
+    __syncthreads();
+    *z = s_tot[0];
+    *q = s_tot[1];
 }
 
 // Sum of the partials of element e over chunks in increasing order.
@@ -155,9 +175,9 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
     const int t = threadIdx.x;
     DevIterInfo inf = *a.info;
     const bool ok = inf.status == MPPI_OK;
+    double z = 0.0, q = 0.0;
+    block_total_zq(a.zq, a.nchunks, &z, &q);
     if (t == 0) {
-        double z = 0.0, q = 0.0;
-        total_zq(a.zq, a.nchunks, &z, &q);
         s_z = z;
         inf.lse = ok ? log(z) : NAN;
         inf.ess = ok ? z * z / q : 0.0;
@@ -178,16 +198,35 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
         s_update = upd;
     }
     __syncthreads();
-    const double z = s_z;
+    z = s_z;
     const bool last = a.iter == a.iters - 1;
-    for (int e = t; e < a.E; e += blockDim.x) {
-        float m = a.nominal[e];
-        if (ok) m = (float)(chunk_total(a.partial, a.nchunks, a.E, e) / z);
-        if (s_update) a.best_out[e] = a.knots[(size_t)inf.best * a.E + e];
-        if (last) a.mean_out[e] = m;
-        a.nominal[e] = m;
+    // chunk totals: FIN_SPLIT interleaved sub-sums per element (chunks c = s, s + FIN_SPLIT,
+    // ... in increasing order) spread over the block, then combined in sub-sum order
+    __shared__ double s_sub[FIN_SPLIT * FIN_TILE];
+    for (int e0 = 0; e0 < a.E; e0 += FIN_TILE) {
+        if (ok)
+            for (int task = t; task < FIN_SPLIT * FIN_TILE; task += blockDim.x) {
+                const int sidx = task / FIN_TILE, el = task - sidx * FIN_TILE, e = e0 + el;
+                double acc = 0.0;
+                if (e < a.E)
+                    for (int c = sidx; c < a.nchunks; c += FIN_SPLIT) acc += a.partial[(size_t)c * a.E + e];
+                s_sub[task] = acc;
+            }
+        __syncthreads();
+        for (int el = t; el < FIN_TILE && e0 + el < a.E; el += blockDim.x) {
+            const int e = e0 + el;
+            float m = a.nominal[e];
+            if (ok) {
+                double tot = 0.0;
+                for (int sidx = 0; sidx < FIN_SPLIT; ++sidx) tot += s_sub[sidx * FIN_TILE + el];
+                m = (float)(tot / z);
+            }
+            if (s_update) a.best_out[e] = a.knots[(size_t)inf.best * a.E + e];
+            if (last) a.mean_out[e] = m;
+            a.nominal[e] = m;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (last) {
         if (a.warm_from == MPPI_WARM_BEST && a.solve->best_index >= 0)
             for (int e = t; e < a.E; e += blockDim.x) a.nominal[e] = a.best_out[e];

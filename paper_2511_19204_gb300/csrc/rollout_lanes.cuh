@@ -26,13 +26,22 @@ __device__ __forceinline__ float lsum(float v) {
 }
 
 // What a body keeps between passes. x0/x1 hold the bias (n, f) after pass 1 and the
-// scaled U_ang / D, U_lin / D after pass 2; uu = u / D.
+// scaled U_ang / D, U_lin / D after pass 2; uu = u / D. The joint rotation is kept
+// whole (R) for short chains, else as its sine and cosine and rebuilt when needed (the
+// same expression either way, so the numbers are identical).
 struct BodyMem {
     float s, c;
+    M3<float> R;
     V3<float> cw, cv;
     V3<float> x0, x1;
     float uu;
 };
+
+template <bool KEEP>
+__device__ __forceinline__ M3<float> joint_rot(const DevModel<float>& M, int b, const BodyMem& m) {
+    if (KEEP) return m.R;
+    return axis_rotation(v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]), m.s, m.c);
+}
 
 struct Pose {
     M3<float> R;
@@ -97,11 +106,13 @@ __device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Ar
 
 // Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
 // the bias (contact forces included).
+template <bool KEEP>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, float q, float qd, const Pose& Pp,
                                            Pose& P, BodyMem& m) {
     const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
     sincosf(q, &m.s, &m.c);
     const M3<float> Rj = axis_rotation(a, m.s, m.c);
+    if (KEEP) m.R = Rj;
     P.R = mul(Pp.R, Rj);
     P.p = Pp.p + mul(Pp.R, r);
     P.w = mulT(Rj, Pp.w) + qd * a;
@@ -116,6 +127,7 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, floa
 
 // Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
 // then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D.
+template <bool KEEP>
 __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, float tau, BodyMem& m, bool has_carry,
                                            Art<float>& carry, V3<float>& cpn, V3<float>& cpf) {
     const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
@@ -159,7 +171,7 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
     const M3<float>& Bm = *reinterpret_cast<const M3<float>*>(Ia.B);
     const V3<float> pan = pAn + sym_mul(Ia.A, m.cw) + mul(Bm, m.cv) + ud * ua;
     const V3<float> paf = pAf + mulT(Bm, m.cw) + sym_mul(Ia.C, m.cv) + ud * ul;
-    const M3<float> Rj = axis_rotation(a, m.s, m.c);
+    const M3<float> Rj = joint_rot<KEEP>(M, b, m);
     art_to_parent(Ia, Rj, r, carry);
     cpf = mul(Rj, paf);
     cpn = mul(Rj, pan) + cross(r, cpf);
@@ -170,10 +182,11 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
 
 // Pass 3 of body b: from the parent's acceleration (apw, apv, offset by gravity) to its
 // own, and its joint acceleration.
+template <bool KEEP>
 __device__ __forceinline__ float body_pass3(const DevModel<float>& M, int b, const BodyMem& m, V3<float>& apw,
                                             V3<float>& apv) {
     const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
-    const M3<float> Rj = axis_rotation(a, m.s, m.c);
+    const M3<float> Rj = joint_rot<KEEP>(M, b, m);
     const V3<float> a1w = mulT(Rj, apw) + m.cw;
     const V3<float> a1v = mulT(Rj, apv - cross(r, apw)) + m.cv;
     const float qdd = m.uu - dot(m.x0, a1w) - dot(m.x1, a1v);
@@ -182,11 +195,19 @@ __device__ __forceinline__ float body_pass3(const DevModel<float>& M, int b, con
     return qdd;
 }
 
-__device__ __forceinline__ float hermite_pd(const DevModel<float>& M, int b, const float* __restrict__ knots, int nj,
-                                            int k, float s, float dtk, float inv_dtk, float q, float qd) {
+struct SegKnots {
+    float q0, v0, q1, v1;
+};
+
+__device__ __forceinline__ SegKnots seg_knots(const float* __restrict__ knots, int nj, int k, int b) {
     const int j = b - 1;
-    const float q0 = knots[(k * 2 + 0) * nj + j], v0 = knots[(k * 2 + 1) * nj + j];
-    const float q1 = knots[((k + 1) * 2 + 0) * nj + j], v1 = knots[((k + 1) * 2 + 1) * nj + j];
+    return SegKnots{knots[(k * 2 + 0) * nj + j], knots[(k * 2 + 1) * nj + j], knots[((k + 1) * 2 + 0) * nj + j],
+                    knots[((k + 1) * 2 + 1) * nj + j]};
+}
+
+__device__ __forceinline__ float hermite_pd(const DevModel<float>& M, int b, const SegKnots& K, float s, float dtk,
+                                            float inv_dtk, float q, float qd) {
+    const float q0 = K.q0, v0 = K.v0, q1 = K.q1, v1 = K.v1;
     const float s2 = s * s, s3 = s2 * s;
     const float h00 = 2.f * s3 - 3.f * s2 + 1.f, h10 = s3 - 2.f * s2 + s;
     const float h01 = -2.f * s3 + 3.f * s2, h11 = s3 - s2;
@@ -211,6 +232,7 @@ template <int LMAX, bool BRANCH>
 __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, const double* __restrict__ x0,
                                             const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                             double* __restrict__ xf) {
+    constexpr bool KEEP = LMAX <= 3;  // short chains keep rotations and segment knots in registers
     const int nj = M.nb - 1, nq = 7 + nj;
     const int b0 = M.lane_b0[g], len = M.lane_len[g];
     const int bb = BRANCH ? M.branch_body : 0;
@@ -239,16 +261,26 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
     for (int l = 0; l < LANES; ++l)
         if (cb >= M.lane_b0[l] && cb < M.lane_b0[l] + M.lane_len[l]) cowner = l;
     if (BRANCH && cb == bb) cowner = 2;
+    SegKnots kc[KEEP ? LMAX : 1];
+    int kcur = -1;
     for (int h = 0; h < H; ++h) {
         const int r = h * (nk - 1);
         int k = r / H;
         if (k > nk - 2) k = nk - 2;
         const float s = (float)(r - k * H) / (float)H;
+        if (KEEP && k != kcur) {
+            kcur = k;
+#pragma unroll
+            for (int j = 0; j < (KEEP ? LMAX : 1); ++j)
+                if (j < len) kc[j] = seg_knots(knots, nj, k, b0 + j);
+        }
         float tau[LMAX], taub = 0.f;
 #pragma unroll
         for (int j = 0; j < LMAX; ++j)
-            tau[j] = j < len ? hermite_pd(M, b0 + j, knots, nj, k, s, dtk, inv_dtk, q[j], qd[j]) : 0.f;
-        if (on_branch) taub = hermite_pd(M, bb, knots, nj, k, s, dtk, inv_dtk, qb, qdb);
+            tau[j] = j < len ? hermite_pd(M, b0 + j, KEEP ? kc[KEEP ? j : 0] : seg_knots(knots, nj, k, b0 + j), s, dtk,
+                                          inv_dtk, q[j], qd[j])
+                             : 0.f;
+        if (on_branch) taub = hermite_pd(M, bb, seg_knots(knots, nj, k, bb), s, dtk, inv_dtk, qb, qdb);
         // ---- pass 1 ----
         B.R = quat_to_R(qw, qx, qy, qz);
         B.p = p;
@@ -265,7 +297,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         BodyMem mb;
         Pose PB;
         if (on_branch) {
-            body_pass1(M, bb, qb, qdb, B, PB, mb);
+            body_pass1<KEEP>(M, bb, qb, qdb, B, PB, mb);
             if (cb == bb) cost_terms(M, PB, tz, tt);
         }
         BodyMem mem[LMAX];
@@ -275,7 +307,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             for (int j = 0; j < LMAX; ++j) {
                 if (j < len) {
                     Pose P;
-                    body_pass1(M, b0 + j, q[j], qd[j], Pp, P, mem[j]);
+                    body_pass1<KEEP>(M, b0 + j, q[j], qd[j], Pp, P, mem[j]);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
@@ -290,7 +322,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
 #pragma unroll
         for (int j = LMAX - 1; j >= 0; --j)
-            if (j < len) body_pass2(M, b0 + j, tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+            if (j < len) body_pass2<KEEP>(M, b0 + j, tau[j], mem[j], j < len - 1, carry, cpn, cpf);
         if (BRANCH) {
             // arms meet at the branch body: own + partner (lanes 2 <-> 3), identical on both
             Art<float> sumc;
@@ -310,7 +342,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 carry = sumc;
                 cpn = sn;
                 cpf = sf;
-                body_pass2(M, bb, taub, mb, true, carry, cpn, cpf);
+                body_pass2<KEEP>(M, bb, taub, mb, true, carry, cpn, cpf);
                 if (g == 3) {  // lane 2 alone hands the branch to the base
 #pragma unroll
                     for (int t = 0; t < 6; ++t) carry.A[t] = 0.f;
@@ -350,9 +382,9 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         float qdd[LMAX], qddb = 0.f;
         {
             V3<float> apw = aw, apv = av;
-            if (on_branch) qddb = body_pass3(M, bb, mb, apw, apv);
+            if (on_branch) qddb = body_pass3<KEEP>(M, bb, mb, apw, apv);
 #pragma unroll
-            for (int j = 0; j < LMAX; ++j) qdd[j] = j < len ? body_pass3(M, b0 + j, mem[j], apw, apv) : 0.f;
+            for (int j = 0; j < LMAX; ++j) qdd[j] = j < len ? body_pass3<KEEP>(M, b0 + j, mem[j], apw, apv) : 0.f;
         }
         // ---- running cost on the pre-step state ----
         float te = 0.f;
