@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-instance workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other single-instance configurations")
     return ap.parse_args()
 
 
@@ -224,6 +225,64 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
+def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1):
+    """One instance's solve timed on its stream (CUDA events, L2 flushed between solves),
+    plus its rollout kernel's in-graph duration."""
+    stream = torch.cuda.Stream()
+    ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream, mapping=mapping)
+    if mapping == -1:
+        ctrl.autotune()
+    ctrl.profile(True)
+    x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
+    out = torch.zeros(ctrl.E, dtype=torch.float32, device="cuda")
+    w = torch.tensor(p.nominal.reshape(-1), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        ctrl.solve_device(x.data_ptr(), out.data_ptr(), d_warm=w.data_ptr())
+    torch.cuda.synchronize()
+    ms, roll = [], []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctrl.solve_device(x.data_ptr(), out.data_ptr(), d_warm=w.data_ptr())
+            e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        roll.extend(float(v) for v in ctrl.rollout_ms())
+    host = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ctrl.solve(p.state, warm=p.nominal)
+        host.append(1e3 * (time.perf_counter() - t0))
+    ms.sort()
+    host.sort()
+    units = p.n * p.horizon * p.iters
+    fl = flops.flops_per_step(p.model) * p.n * p.horizon
+    achieved = fl / (statistics.mean(roll) * 1e-3) / 1e12
+    info = ctrl.info()
+    return {"samples": p.n, "horizon": p.horizon, "knots": p.nk, "iters": p.iters, "dt": p.dt,
+            "mapping": mppi.MAPPING_NAMES.get(info["mapping"]), "block": info["block"],
+            "rollout_steps_per_s": units / (statistics.mean(ms) * 1e-3),
+            "solves_per_s": 1e3 / statistics.mean(ms),
+            "device_latency_ms": {"p50": ms[len(ms) // 2], "p99": ms[min(len(ms) - 1, int(0.99 * len(ms)))]},
+            "host_latency_ms": {"p50": host[len(host) // 2], "p99": host[min(len(host) - 1, int(0.99 * len(host)))]},
+            "rollout_launch_ms": statistics.mean(roll),
+            "rollout_tflops": achieved, "rollout_frac_fp32_peak": achieved / flops.fp32_peak_tflops(),
+            "flops_per_step_sample": flops.flops_per_step(p.model)}
+
+
+def other_configs(mppi, synth, torch, flops):
+    out = {}
+    out["plain_quadruped_K32"] = single_instance(mppi, synth, torch, flops, synth.plain_quadruped())
+    for n in (1024, 4096):
+        out[f"scale_quadruped_K{n}"] = single_instance(mppi, synth, torch, flops, synth.scale_quadruped(n=n))
+    out["humanoid_K2048"] = single_instance(mppi, synth, torch, flops, synth.humanoid_problem())
+    return out
+
+
 def batched_extra(mppi, synth, torch, count=256, reps=5):
     """Batched uneven instances: one persistent graph-captured launch per solve of all
     instances vs the same instances as sequential plain launches (one CUDA graph each,
@@ -484,6 +543,11 @@ def run_ours(args, rank, world, local):
         "gpu_launches": args.steps * ctrl.kernels_per_solve,
         "clocks": clk,
     }
+    if not args.no_configs:
+        try:
+            line["other_configs"] = other_configs(mppi, synth, torch, flops)
+        except Exception as exc:  # reported, never silently dropped
+            line["other_configs"] = {"error": repr(exc)}
     if not args.no_batched:
         try:
             line["batched_uneven"] = batched_extra(mppi, synth, torch)

@@ -162,6 +162,15 @@ mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t k
                         const mppi_params* params, mppi_ctx** out);
 void mppi_destroy(mppi_ctx* ctx);
 
+/* The annealed noise schedule of Sec. III-B Eq. (overall-noise-kernel), computed once on
+ * the host as the paper caches it: h_sigma[it][k] = scale * exp(-(I - i)/(beta1 I) -
+ * (K - k)/(beta2 K)) for iterations i = I..1 (row it = I - i: the first iteration uses
+ * factor 1 on the trajectory term) and knots k = 0..K-1 (K = knots). The isotropic factor
+ * of the covariance is used as the per-knot standard-deviation factor, the table
+ * mppi_create takes. Errors: INVALID_ARG (iters, knots < 1, beta <= 0, scale < 0). */
+mppi_status mppi_noise_schedule(int32_t iters, int32_t knots, double beta1, double beta2, double scale,
+                                float* h_sigma);
+
 /* One MPPI update (Alg. 1 inner loop over `iters` iterations) from state h_state.
  * h_warm_start [knots][2][nj] replaces the resident nominal if non-NULL; NULL keeps the
  * resident one (initially theta^q = q_init, theta^v = 0; after each solve the best
@@ -206,6 +215,37 @@ mppi_status mppi_set_iter_counter(mppi_ctx* ctx, uint32_t value);
  * Call with buf = NULL to query *len. */
 mppi_status mppi_export_state(const mppi_ctx* ctx, void* buf, size_t* len);
 mppi_status mppi_import_state(mppi_ctx* ctx, const void* buf, size_t len);
+
+/* ---------------------------------------------------------------------------------- */
+/* Receding horizon (Sec. III-E)                                                        */
+/* ---------------------------------------------------------------------------------- */
+
+/* State prediction over the compute delay, Eq. of Sec. III-E: the state the robot reaches
+ * after `steps` control steps (steps * dt seconds; steps = floor(delay / dt)) from
+ * h_state while it executes the resident warm start (tau_best after a solve under
+ * MPPI_WARM_BEST), simulated with the rollout's dynamics and PD tracking of the first
+ * `steps` of the H steps (FP32; FP64 under mppi_ctx_set_fp64_check). 0 <= steps <= H;
+ * steps = 0 returns h_state. h_state, h_out [nx] FP64 host, may alias. Blocks.
+ * Errors: INVALID_ARG, NONFINITE_STATE, CUDA, TIMEOUT (a bounded device wait gave up). */
+mppi_status mppi_predict_state(mppi_ctx* ctx, const double* h_state, int32_t steps, double* h_out);
+
+/* Same on device buffers, enqueued on the context's stream after any solve enqueued
+ * there (so it reads that solve's warm start): d_state, d_out [nx] FP64 device. The
+ * result can be passed straight to mppi_solve_device. A bounded-wait failure is
+ * reported by the next mppi_sync. Errors: INVALID_ARG, CUDA. */
+mppi_status mppi_predict_state_device(mppi_ctx* ctx, const double* d_state, int32_t steps, double* d_out);
+
+/* Shift of the resident warm start by `steps` executed actions, Sec. III-E, with the tail
+ * padded. The knots parameterise a spline over T = H dt with knot j at t_j = j T /
+ * (knots - 1); the shifted knot j is the old spline's value and time derivative at
+ * t_j + steps dt, and past T the final knot is repeated. steps = 0 leaves the knots
+ * unchanged; steps >= H repeats the final knot everywhere. Evaluated in FP64 from the
+ * FP32 knots, rounded once; enqueued on the context's stream. Errors: INVALID_ARG
+ * (steps < 0), CUDA. */
+mppi_status mppi_shift_warm_start(mppi_ctx* ctx, int32_t steps);
+
+/* Copy of the resident warm start [knots][2][nj] to h_out (synchronises the stream). */
+mppi_status mppi_get_warm_start(const mppi_ctx* ctx, float* h_out);
 
 /* ---------------------------------------------------------------------------------- */
 /* Kernel-level entry points (each runs one kernel of the path on host buffers)         */
@@ -271,6 +311,14 @@ mppi_status mppi_forward_dynamics_ex(const mppi_model* model, int32_t n, const d
 mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, const double* const* h_states,
                              const float* const* h_warm, float* const* h_out_mean,
                              float* const* h_out_best, mppi_result* h_info);
+
+/* Self-test of failure detection: launches the persistent kernel on a queue whose only
+ * item is never published. Its bounded wait must give up after budget_us (1 us .. 10 s)
+ * and set the error word; the call then returns MPPI_ERR_TIMEOUT and writes the device
+ * error bits (2 = queue wait timed out) to h_error_bits (nullable). Nothing traps or
+ * faults and the device stays usable. Returns MPPI_OK only if the wait did not give up
+ * (which would be a defect). */
+mppi_status mppi_selftest_queue_timeout(int64_t budget_us, int32_t* h_error_bits);
 
 /* ---------------------------------------------------------------------------------- */
 /* Serving: continuous batching of controller requests on one GPU                       */

@@ -62,6 +62,7 @@ def lib():
         L.orc_sample_knots.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
                                        C.c_double, C.c_double, C.c_uint64, C.c_uint32, C.c_uint32,
                                        _dp, _dp, _dp]
+        L.orc_noise_schedule.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         L.orc_segment.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), _dp]
         L.orc_hermite.argtypes = [C.c_double] * 6 + [_dp, _dp]
         L.orc_forward_dynamics.argtypes = [mp, _dp, _dp, _dp]
@@ -80,6 +81,9 @@ def lib():
         L.orc_rollout.restype = C.c_double
         L.orc_rollout_batch.argtypes = [mp, C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_double, _dp,
                                         _dp, C.c_int]
+        L.orc_predict_state.argtypes = [mp, _dp, _dp, C.c_int, C.c_int, C.c_int, C.c_double, _dp]
+        L.orc_predict_state.restype = C.c_int
+        L.orc_shift_knots.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp]
         L.orc_weights.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp]
         L.orc_weights.restype = C.c_int
         L.orc_average.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
@@ -159,6 +163,13 @@ def sample_knots(nu, nk, N, H, dt, nominal, sigma_row, scale_q=1.0, scale_v=0.0,
     hi = _d(q_max) if q_max is not None else None
     lib().orc_sample_knots(nu, nk, N, H, dt, _ptr(nom), _ptr(sr), scale_q, scale_v, seed, iter_ctr,
                            inst, _ptr(lo), _ptr(hi), _ptr(out))
+    return out
+
+
+def noise_schedule(iters, knots, beta1, beta2, scale=1.0) -> np.ndarray:
+    """Sec. III-B Eq. (overall-noise-kernel) as a [iters][knots] standard-deviation table."""
+    out = np.zeros((iters, knots))
+    lib().orc_noise_schedule(iters, knots, beta1, beta2, scale, _ptr(out))
     return out
 
 
@@ -264,6 +275,24 @@ def rollout_batch(m, x0, knots, H, dt, finals=False, nthreads=None):
     nt = nthreads or os.cpu_count() or 1
     lib().orc_rollout_batch(om.ref, N, _ptr(_d(x0)), _ptr(kn), nk, H, dt, _ptr(costs), _ptr(fin), nt)
     return (costs, fin) if finals else costs
+
+
+def predict_state(m, x0, knots, H, nsteps, dt) -> np.ndarray:
+    """Sec. III-E: the state after the first nsteps steps of the knots' spline."""
+    om = _om(m)
+    kn = _d(knots)
+    out = np.zeros(om.nx)
+    lib().orc_predict_state(om.ref, _ptr(_d(x0)), _ptr(kn), kn.shape[0], H, nsteps, dt, _ptr(out))
+    return out
+
+
+def shift_knots(knots, H, steps, dt) -> np.ndarray:
+    """Sec. III-E: shift by `steps` actions, tail held at the horizon end."""
+    kn = _d(knots)
+    nk, _, nu = kn.shape
+    out = np.zeros_like(kn)
+    lib().orc_shift_knots(nu, nk, H, steps, dt, _ptr(kn), _ptr(out))
+    return out
 
 
 # ------------------------------------------------------------------------------------

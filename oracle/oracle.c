@@ -87,6 +87,19 @@ void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+/* Sec. III-B Eq. (overall-noise-kernel): the isotropic per-knot factor
+ * exp(-(I - i)/(beta1 I) - (K - k)/(beta2 K)) for iterations i = I..1 and knots
+ * k = 0..K-1, used as the standard-deviation factor sigma[it][k] with it = I - i (so the
+ * first iteration, i = I, is row 0), times `scale`. out [iters][knots]. */
+void orc_noise_schedule(int iters, int knots, double beta1, double beta2, double scale, double* out) {
+    for (int it = 0; it < iters; ++it) {
+        int i = iters - it;
+        for (int k = 0; k < knots; ++k)
+            out[it * knots + k] =
+                scale * exp(-(double)(iters - i) / (beta1 * iters) - (double)(knots - k) / (beta2 * knots));
+    }
+}
+
 /* Box-Muller on two 32-bit words: u1 in (0,1], u2 in [0,1). */
 static void box_muller(uint32_t wa, uint32_t wb, double* ea, double* eb) {
     const double two_m24 = 1.0 / 16777216.0;
@@ -775,6 +788,43 @@ double orc_rollout(const orc_model* m, const double* x0, const double* knots, in
     if (x_final) memcpy(x_final, x, sizeof(double) * nx);
     free(K);
     return S;
+}
+
+/* Sec. III-E state prediction: simulate the first `nsteps` steps of the spline defined by
+ * knots over a horizon of H steps (knot times as in the rollout) from x0; x_out [nx]. */
+int orc_predict_state(const orc_model* m, const double* x0, const double* knots, int nk, int H, int nsteps,
+                      double dt, double* x_out) {
+    const int nj = m->nb - 1, nq = 7 + nj, nx = nq + 6 + nj;
+    double* tr = (double*)malloc(sizeof(double) * (size_t)(H + 1) * nx);
+    double S = orc_rollout(m, x0, knots, nk, H, dt, NULL, tr);
+    (void)S;
+    if (nsteps > H) nsteps = H;
+    memcpy(x_out, tr + (size_t)nsteps * nx, sizeof(double) * nx);
+    free(tr);
+    return 0;
+}
+
+/* Sec. III-E shift of tau_best by `steps` actions with the tail held: the new knot j is
+ * the old spline (value and time derivative) at time t_j + steps dt, capped at the
+ * horizon end T = H dt. In the rollout's integer units r = t / dt * (nk - 1):
+ * r_j = min(j H + steps (nk - 1), H (nk - 1)), segment k = min(floor(r_j / H), nk - 2),
+ * s = (r_j - k H) / H. knots in/out [nk][2][nu] (may not alias). */
+void orc_shift_knots(int nu, int nk, int H, int steps, double dt, const double* in, double* out) {
+    const double dtk = knot_dt(nk, H, dt);
+    for (int j = 0; j < nk; ++j) {
+        long r = (long)j * H + (long)steps * (nk - 1);
+        if (r > (long)H * (nk - 1)) r = (long)H * (nk - 1);
+        long k = r / H;
+        if (k > nk - 2) k = nk - 2;
+        double s = (double)(r - k * (long)H) / (double)H;
+        for (int i = 0; i < nu; ++i) {
+            double q, qd;
+            orc_hermite(s, dtk, in[(k * 2 + 0) * nu + i], in[(k * 2 + 1) * nu + i], in[((k + 1) * 2 + 0) * nu + i],
+                        in[((k + 1) * 2 + 1) * nu + i], &q, &qd);
+            out[(j * 2 + 0) * nu + i] = q;
+            out[(j * 2 + 1) * nu + i] = qd;
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 LaneConst<float> L;
                 load_lane_const(*M, gl, L);
                 const float c = warp_rollout<float, 16, double>(*M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H,
-                                                                I.nk, I.dt, I.dtk, work, nullptr);
+                                                                I.H, I.nk, I.dt, I.dtk, work, nullptr);
                 if (n <= last_n && gl == 0) I.costs[n] = c;
             } else {
                 const int gl = threadIdx.x & 31;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 LaneConst<float> L;
                 load_lane_const(*M, gl, L);
                 const float c = warp_rollout<float, 32, double>(*M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H,
-                                                                I.nk, I.dt, I.dtk, work, nullptr);
+                                                                I.H, I.nk, I.dt, I.dtk, work, nullptr);
                 if (n <= last_n && gl == 0) I.costs[n] = c;
             }
             __threadfence();
@@ -731,4 +731,47 @@ extern "C" mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, co
     BatchPlan* P = get_plan(ctxs, count, &st);
     if (!P) return st;
     return run_plan(P, ctxs, h_states, h_warm, h_out_mean, h_out_best, h_info);
+}
+
+namespace mppi {
+// Self-test of the persistent kernel's bounded wait: a queue of one item that is never
+// published. The block that takes it must give up after budget_us and set the error word.
+mppi_status queue_timeout_selftest(int64_t budget_us, int32_t* observed) {
+    unsigned char* d = nullptr;
+    const size_t bytes = 256 + 256;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest allocation");
+    BatchQueue hq;
+    memset(&hq, 0, sizeof hq);
+    hq.total = 1;
+    hq.nprefill = 0;
+    QueueItem hi;
+    memset(&hi, 0, sizeof hi);
+    e = cudaMemcpy(d, &hq, sizeof hq, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 256, &hi, sizeof hi, cudaMemcpyHostToDevice);
+    size_t smem = 0;
+    int per_sm = 0;
+    if (e == cudaSuccess) e = prepare_batch_kernel(8, &smem, &per_sm);
+    if (e == cudaSuccess) {
+        persistent_kernel<<<1, BATCH_THREADS, smem>>>(nullptr, nullptr, reinterpret_cast<QueueItem*>(d + 256),
+                                                    reinterpret_cast<BatchQueue*>(d), (uint64_t)budget_us * 1000ull);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    uint32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, d + offsetof(BatchQueue, error), sizeof err, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest launch");
+    if (observed) *observed = (int32_t)err;
+    if (err & DEV_ERR_QUEUE_TIMEOUT) {
+        set_error(nullptr, "the persistent kernel's queue wait gave up as designed");
+        return MPPI_ERR_TIMEOUT;
+    }
+    return MPPI_OK;
+}
+}  // namespace mppi
+
+extern "C" mppi_status mppi_selftest_queue_timeout(int64_t budget_us, int32_t* h_error_bits) {
+    if (budget_us < 1 || budget_us > 10000000) return MPPI_ERR_INVALID_ARG;
+    return mppi::queue_timeout_selftest(budget_us, h_error_bits);
 }

@@ -765,6 +765,82 @@ mppi_status mppi_import_state(mppi_ctx* c, const void* buf, size_t len) {
     return MPPI_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Receding horizon (Sec. III-E): state prediction over the compute delay and the shift
+// of the resident warm start. Both run on the context's stream, after any solve already
+// enqueued there.
+// ------------------------------------------------------------------------------------
+static mppi_status enqueue_predict(mppi_ctx* c, const double* d_state, int32_t steps, double* d_out) {
+    cudaError_t e = cudaSuccess;
+    if (steps == 0) {
+        if (d_out != d_state)
+            e = cudaMemcpyAsync(d_out, d_state, sizeof(double) * c->nx, cudaMemcpyDeviceToDevice, c->stream);
+    } else if (c->fp64_check) {
+        e = launch_predict_f64((const DevModel<double>*)c->model->d_d, d_state, c->d_nominal, c->H, steps, c->nk,
+                               c->dt, c->dtk, d_out, &c->d_solve->dev_error, c->stream);
+    } else {
+        e = launch_predict_f32((const DevModel<float>*)c->model->d_f, d_state, c->d_nominal, c->H, steps, c->nk,
+                               (float)c->dt, (float)c->dtk, d_out, &c->d_solve->dev_error, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "predict_state");
+    return MPPI_OK;
+}
+
+mppi_status mppi_predict_state_device(mppi_ctx* c, const double* d_state, int32_t steps, double* d_out) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    if (!d_state || !d_out || steps < 0 || steps > c->H) {
+        set_error(c, "mppi_predict_state_device: needs device state and output and 0 <= steps <= H");
+        return MPPI_ERR_INVALID_ARG;
+    }
+    return enqueue_predict(c, d_state, steps, d_out);
+}
+
+mppi_status mppi_predict_state(mppi_ctx* c, const double* h_state, int32_t steps, double* h_out) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    if (!h_state || !h_out || steps < 0 || steps > c->H) {
+        set_error(c, "mppi_predict_state: needs state and output and 0 <= steps <= H");
+        return MPPI_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < c->nx; ++i)
+        if (!isfinite(h_state[i])) {
+            set_error(c, "mppi_predict_state: state is not finite");
+            return MPPI_ERR_NONFINITE_STATE;
+        }
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * 2 * c->nx);
+    if (e != cudaSuccess) return cuda_fail(c, e, "predict_state: cudaMalloc");
+    e = cudaMemcpyAsync(d, h_state, sizeof(double) * c->nx, cudaMemcpyHostToDevice, c->stream);
+    mppi_status st = e == cudaSuccess ? enqueue_predict(c, d, steps, d + c->nx) : cuda_fail(c, e, "predict_state");
+    if (st == MPPI_OK) {
+        e = cudaMemcpyAsync(h_out, d + c->nx, sizeof(double) * c->nx, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "predict_state");
+    }
+    cudaFree(d);
+    if (st == MPPI_OK) st = mppi_sync(c);
+    return st;
+}
+
+mppi_status mppi_shift_warm_start(mppi_ctx* c, int32_t steps) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    if (steps < 0) {
+        set_error(c, "mppi_shift_warm_start: steps must be >= 0");
+        return MPPI_ERR_INVALID_ARG;
+    }
+    if (steps == 0) return MPPI_OK;
+    cudaError_t e = launch_shift_knots(c->d_nominal, c->nj, c->nk, c->H, steps > c->H ? c->H : steps, c->dtk, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "shift_warm_start");
+    return MPPI_OK;
+}
+
+mppi_status mppi_get_warm_start(const mppi_ctx* c, float* h_out) {
+    if (!c || !h_out) return MPPI_ERR_INVALID_ARG;
+    mppi_ctx* cc = const_cast<mppi_ctx*>(c);
+    CK(cc, cudaStreamSynchronize(c->stream));
+    CK(cc, cudaMemcpy(h_out, c->d_nominal, sizeof(float) * c->E, cudaMemcpyDeviceToHost));
+    return MPPI_OK;
+}
+
 mppi_status mppi_philox_words(int32_t n, const uint32_t* h_ctr, const uint32_t* h_key, uint32_t* h_out) {
     if (n < 0 || (n > 0 && (!h_ctr || !h_key || !h_out))) return MPPI_ERR_INVALID_ARG;
     if (n == 0) return MPPI_OK;
@@ -920,6 +996,19 @@ mppi_status mppi_ctx_rollout_ms(mppi_ctx* c, float* h_ms) {
     if (!c || !h_ms || !c->profile) return MPPI_ERR_INVALID_ARG;
     CK(c, cudaStreamSynchronize(c->stream));
     for (int it = 0; it < c->iters; ++it) CK(c, cudaEventElapsedTime(&h_ms[it], c->ev[2 * it], c->ev[2 * it + 1]));
+    return MPPI_OK;
+}
+
+mppi_status mppi_noise_schedule(int32_t iters, int32_t knots, double beta1, double beta2, double scale,
+                                float* h_sigma) {
+    if (iters < 1 || knots < 1 || !h_sigma || !(beta1 > 0) || !(beta2 > 0) || !(scale >= 0) || !isfinite(scale))
+        return MPPI_ERR_INVALID_ARG;
+    for (int it = 0; it < iters; ++it) {
+        const int i = iters - it;  // iterations run i = I..1
+        for (int k = 0; k < knots; ++k)
+            h_sigma[it * knots + k] =
+                (float)(scale * exp(-(double)(iters - i) / (beta1 * iters) - (double)(knots - k) / (beta2 * knots)));
+    }
     return MPPI_OK;
 }
 

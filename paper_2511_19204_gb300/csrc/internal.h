@@ -65,6 +65,13 @@ cudaError_t launch_rollout_thread_f32(const RolloutArgs<float>& a, int topology,
 bool thread_mapping_supported(int topology);
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, int block, cudaStream_t s);
 bool chain_mapping_supported(int topology);
+// state after the first nsteps steps of knots [nk][2][nj] from x0 (one warp, Sec. III-E)
+cudaError_t launch_predict_f32(const DevModel<float>* m, const double* x0, const float* knots, int H, int nsteps,
+                               int nk, float dt, float dtk, double* out, uint32_t* status, cudaStream_t s);
+cudaError_t launch_predict_f64(const DevModel<double>* m, const double* x0, const float* knots, int H, int nsteps,
+                               int nk, double dt, double dtk, double* out, uint32_t* status, cudaStream_t s);
+// in-place shift of knots [nk][2][nj] by `steps` control steps, tail held (Sec. III-E)
+cudaError_t launch_shift_knots(float* knots, int nj, int nk, int H, int steps, double dtk, cudaStream_t s);
 cudaError_t prepare_warp_f32();
 cudaError_t prepare_warp_f64();
 cudaError_t prepare_thread_f32();

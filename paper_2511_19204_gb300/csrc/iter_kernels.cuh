@@ -149,6 +149,48 @@ cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* bes
 }
 
 // ------------------------------------------------------------------------------------
+// Shift of the warm start (Sec. III-E). The knots define a spline over the horizon
+// T = H dt with knot j at t_j = j T / (nk - 1). Shifting the action sequence by `steps`
+// control steps makes the new knot j the old spline's value and time derivative at
+// t_j + steps dt; beyond T the spline's end point (the last knot) is repeated. In the
+// rollout's integer time units r = t (nk - 1) / dt the read time is
+// r_j = min(j H + steps (nk - 1), H (nk - 1)), its segment k = min(floor(r_j / H), nk - 2)
+// and s = (r_j - k H) / H. Evaluated in FP64 from the FP32 knots, rounded once.
+// One block; in place through shared memory.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) shift_knots_kernel(float* knots, int nj, int nk, int H, int steps, double dtk) {
+    __shared__ float old[MAXK * 2 * (MAXB - 1)];
+    const int E = nk * 2 * nj;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) old[e] = knots[e];
+    __syncthreads();
+    const long long rmax = (long long)H * (nk - 1);
+    for (int e = threadIdx.x; e < nk * nj; e += blockDim.x) {
+        const int j = e / nj, i = e - (e / nj) * nj;
+        long long r = (long long)j * H + (long long)steps * (nk - 1);
+        if (r > rmax) r = rmax;
+        int k = (int)(r / H);
+        if (k > nk - 2) k = nk - 2;
+        const double s = (double)(r - (long long)k * H) / (double)H;
+        const double p0 = old[(2 * k) * nj + i], m0 = old[(2 * k + 1) * nj + i];
+        const double p1 = old[(2 * k + 2) * nj + i], m1 = old[(2 * k + 3) * nj + i];
+        const double s2 = s * s, s3 = s2 * s;
+        // cubic Hermite basis and its derivative in s (Eq. hermite_segment)
+        const double q = (2.0 * s3 - 3.0 * s2 + 1.0) * p0 + (s3 - 2.0 * s2 + s) * dtk * m0 +
+                         (3.0 * s2 - 2.0 * s3) * p1 + (s3 - s2) * dtk * m1;
+        const double v = ((6.0 * s2 - 6.0 * s) * (p0 - p1)) / dtk + (3.0 * s2 - 4.0 * s + 1.0) * m0 +
+                         (3.0 * s2 - 2.0 * s) * m1;
+        knots[(2 * j) * nj + i] = (float)q;
+        knots[(2 * j + 1) * nj + i] = (float)v;
+    }
+}
+
+cudaError_t launch_shift_knots(float* knots, int nj, int nk, int H, int steps, double dtk, cudaStream_t s) {
+    if (nj < 1 || nk < 2 || nk > MAXK || nj > MAXB - 1 || H < 1 || steps < 0) return cudaErrorInvalidValue;
+    shift_knots_kernel<<<1, 256, 0, s>>>(knots, nj, nk, H, steps, dtk);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
 // Philox words for a list of counters (bit-exactness checks).
 // ------------------------------------------------------------------------------------
 __global__ void philox_words_kernel(int n, const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,

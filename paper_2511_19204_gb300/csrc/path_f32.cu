@@ -18,5 +18,9 @@ cudaError_t launch_dynamics_f32(const DevModel<float>* m, int n, const double* x
                                 cudaStream_t s) {
     return launch_dynamics_t<float>(m, n, x, tau, acc, s);
 }
+cudaError_t launch_predict_f32(const DevModel<float>* m, const double* x0, const float* knots, int H, int nsteps,
+                               int nk, float dt, float dtk, double* out, uint32_t* status, cudaStream_t s) {
+    return launch_predict_t<float>(m, x0, knots, H, nsteps, nk, dt, dtk, out, status, s);
+}
 cudaError_t prepare_warp_f32() { return prepare_warp_kernels<float>(); }
 }  // namespace mppi

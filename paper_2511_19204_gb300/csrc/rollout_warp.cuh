@@ -355,13 +355,15 @@ __device__ __forceinline__ void store_lane_state(const DevModel<T>& M, const Lan
     }
 }
 
-// Full rollout of one sample by its group: H steps tracking the Hermite setpoints of
-// knots [nk][2][nj] (global), returning the Kahan-compensated cost sum on every lane.
-// x0: initial state [nx] (global, FP32 or FP64). xf: optional final state.
+// Rollout of one sample by its group: the first nsteps (<= H) of the H steps tracking the
+// Hermite setpoints of knots [nk][2][nj] (global), returning the Kahan-compensated cost
+// sum on every lane. x0: initial state [nx] (global, FP32 or FP64). xf: optional state
+// after the last step simulated.
 template <typename T, int G, typename XT>
 __device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>& L, int gl,
-                                          const XT* __restrict__ x0, const float* __restrict__ knots, int H, int nk,
-                                          T dt, T dtk, T* __restrict__ contrib, XT* __restrict__ xf) {
+                                          const XT* __restrict__ x0, const float* __restrict__ knots, int H,
+                                          int nsteps, int nk, T dt, T dtk, T* __restrict__ contrib,
+                                          XT* __restrict__ xf) {
     const int nj = M.nb - 1;
     LaneState<T> S;
     load_lane_state(M, L, gl, x0, S);
@@ -370,7 +372,7 @@ __device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>&
     int kcur = -1;
     T q0 = T(0), v0 = T(0), q1 = T(0), v1 = T(0);
     const int j = gl - 1;
-    for (int h = 0; h < H; ++h) {
+    for (int h = 0; h < nsteps; ++h) {
         // segment by integer arithmetic: r = h (nk-1), k = floor(r / H), s = (r - k H) / H
         const int r = h * (nk - 1);
         int k = r / H;
@@ -451,8 +453,8 @@ __global__ void __launch_bounds__(256) rollout_warp_kernel(RolloutArgs<T> a) {
     const int nx = 13 + 2 * nj;
     const int E = a.nk * 2 * nj;
     double* xf = (active && a.finals) ? a.finals + (size_t)n * nx : nullptr;
-    const T c = warp_rollout<T, G, double>(*M, L, gl, a.x0, a.knots + (size_t)ne * E, a.H, a.nk, a.dt, a.dtk,
-                                           contrib, xf);
+    const T c = warp_rollout<T, G, double>(*M, L, gl, a.x0, a.knots + (size_t)ne * E, a.H, a.H, a.nk, a.dt,
+                                           a.dtk, contrib, xf);
     if (active && gl == 0) a.costs[n] = c;
 }
 
@@ -490,6 +492,35 @@ __global__ void __launch_bounds__(256) dynamics_kernel(const DevModel<T>* gm, in
     }
 }
 
+// State prediction (Sec. III-E): one warp simulates the first nsteps steps of the
+// spline of knots [nk][2][nj] over a horizon of H steps from x0 and writes the state
+// reached to out [nx].
+template <typename T>
+__global__ void __launch_bounds__(32) predict_kernel(const DevModel<T>* gm, const double* __restrict__ x0,
+                                                     const float* __restrict__ knots, int H, int nsteps, int nk, T dt,
+                                                     T dtk, double* __restrict__ out, uint32_t* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    DevModel<T>* M = reinterpret_cast<DevModel<T>*>(smem);
+    T* contrib = reinterpret_cast<T*>(smem + sizeof(DevModel<T>));
+    if (!bulk_load_to_smem(M, gm, (uint32_t)sizeof(DevModel<T>), &mbar)) {
+        if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_TMA_TIMEOUT);
+        return;
+    }
+    const int gl = threadIdx.x;
+    LaneConst<T> L;
+    load_lane_const(*M, gl, L);
+    (void)warp_rollout<T, 32, double>(*M, L, gl, x0, knots, H, nsteps, nk, dt, dtk, contrib, out);
+}
+
+template <typename T>
+cudaError_t launch_predict_t(const DevModel<T>* m, const double* x0, const float* knots, int H, int nsteps, int nk,
+                             T dt, T dtk, double* out, uint32_t* status, cudaStream_t s) {
+    if (nsteps < 0 || nsteps > H) return cudaErrorInvalidValue;
+    predict_kernel<T><<<1, 32, warp_smem_bytes<T>(32), s>>>(m, x0, knots, H, nsteps, nk, dt, dtk, out, status);
+    return cudaGetLastError();
+}
+
 template <typename T, int G>
 cudaError_t launch_rollout_warp_t(const RolloutArgs<T>& a, int block, cudaStream_t s) {
     if (block <= 0) block = 128;
@@ -522,6 +553,9 @@ cudaError_t prepare_warp_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(rollout_warp_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(dynamics_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(predict_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)warp_smem_bytes<T>(32));
     return e;
 }
 

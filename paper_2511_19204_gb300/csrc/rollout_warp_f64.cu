@@ -14,5 +14,9 @@ cudaError_t launch_dynamics_f64(const DevModel<double>* m, int n, const double* 
                                 cudaStream_t s) {
     return launch_dynamics_t<double>(m, n, x, tau, acc, s);
 }
+cudaError_t launch_predict_f64(const DevModel<double>* m, const double* x0, const float* knots, int H, int nsteps,
+                               int nk, double dt, double dtk, double* out, uint32_t* status, cudaStream_t s) {
+    return launch_predict_t<double>(m, x0, knots, H, nsteps, nk, dt, dtk, out, status, s);
+}
 cudaError_t prepare_warp_f64() { return prepare_warp_kernels<double>(); }
 }  // namespace mppi

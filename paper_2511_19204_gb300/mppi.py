@@ -92,6 +92,7 @@ SIGNATURES = [
     ("mppi_create", C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _fp, C.c_int32,
                                 C.POINTER(mppi_params), C.POINTER(_P)]),
     ("mppi_destroy", None, [_P]),
+    ("mppi_noise_schedule", C.c_int32, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _fp]),
     ("mppi_solve", C.c_int32, [_P, _dp, _fp, _fp, _fp, C.POINTER(mppi_result)]),
     ("mppi_solve_device", C.c_int32, [_P, _P, _P, _P, _P, _P]),
     ("mppi_sync", C.c_int32, [_P]),
@@ -101,6 +102,10 @@ SIGNATURES = [
     ("mppi_set_iter_counter", C.c_int32, [_P, C.c_uint32]),
     ("mppi_export_state", C.c_int32, [_P, _P, C.POINTER(C.c_size_t)]),
     ("mppi_import_state", C.c_int32, [_P, _P, C.c_size_t]),
+    ("mppi_predict_state", C.c_int32, [_P, _dp, C.c_int32, _dp]),
+    ("mppi_predict_state_device", C.c_int32, [_P, _P, C.c_int32, _P]),
+    ("mppi_shift_warm_start", C.c_int32, [_P, C.c_int32]),
+    ("mppi_get_warm_start", C.c_int32, [_P, _fp]),
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
     ("mppi_average", C.c_int32, [C.c_int32, C.c_int32, _fp, _dp, _dp]),
@@ -109,6 +114,7 @@ SIGNATURES = [
     ("mppi_forward_dynamics_ex", C.c_int32, [_P, C.c_int32, _dp, _dp, _dp, C.c_int32]),
     ("mppi_solve_batch", C.c_int32, [C.POINTER(_P), C.c_int32, C.POINTER(_dp), C.POINTER(_fp),
                                      C.POINTER(_fp), C.POINTER(_fp), C.POINTER(mppi_result)]),
+    ("mppi_selftest_queue_timeout", C.c_int32, [C.c_int64, _ip]),
     ("mppi_server_create", C.c_int32, [C.c_int32, C.c_size_t, C.c_int32, C.POINTER(_P)]),
     ("mppi_server_destroy", None, [_P]),
     ("mppi_submit", C.c_int32, [_P, _P, _dp, _fp, _u64p]),
@@ -328,6 +334,26 @@ class Controller:
         buf = C.create_string_buffer(blob, len(blob))
         _check(load().mppi_import_state(self.h, buf, len(blob)), self.h)
 
+    def predict_state(self, state, steps):
+        """Sec. III-E: state after `steps` control steps of the resident warm start."""
+        x = _d(state).copy()
+        out = np.zeros(self.nx)
+        _check(load().mppi_predict_state(self.h, _pd(x), int(steps), _pd(out)), self.h)
+        return out
+
+    def predict_state_device(self, d_state_ptr, steps, d_out_ptr):
+        _check(load().mppi_predict_state_device(self.h, C.c_void_p(d_state_ptr), int(steps),
+                                                C.c_void_p(d_out_ptr)), self.h)
+
+    def shift_warm_start(self, steps):
+        """Sec. III-E: shift the resident warm start by `steps` executed actions."""
+        _check(load().mppi_shift_warm_start(self.h, int(steps)), self.h)
+
+    def warm_start(self):
+        out = np.zeros(self.E, np.float32)
+        _check(load().mppi_get_warm_start(self.h, _pf(out)), self.h)
+        return out.reshape(self.nk, 2, self.nj)
+
     def set_mapping(self, mapping, block=0):
         _check(load().mppi_ctx_set_mapping(self.h, mapping, block), self.h)
 
@@ -372,6 +398,13 @@ class Controller:
             self.close()
         except Exception:
             pass
+
+
+def noise_schedule(iters, knots, beta1, beta2, scale=1.0):
+    """mppi_noise_schedule: [iters][knots] float32 standard deviations."""
+    out = np.zeros((iters, knots), np.float32)
+    _check(load().mppi_noise_schedule(iters, knots, beta1, beta2, scale, _pf(out)))
+    return out
 
 
 def philox_words(ctr, key):

@@ -615,3 +615,66 @@ def test_config_rollouts_finite(orc):
     r = orc.solve_problem(p, keep=True)
     assert r["status"] == 0
     assert np.all(np.isfinite(r["costs"])) and np.all(r["costs"] < 1e4)
+
+
+# ------------------------------------------------------------------------------------
+# Eq. (overall-noise-kernel)
+# ------------------------------------------------------------------------------------
+def test_noise_schedule_structure(orc):
+    I, K, b1, b2 = 3, 6, 0.7, 1.3
+    s = orc.noise_schedule(I, K, b1, b2)
+    # the first iteration (i = I) carries factor 1 on the trajectory term; the last knot
+    # (k = K - 1) the largest action factor exp(-1 / (beta2 K))
+    assert s[0, K - 1] == pytest.approx(math.exp(-1.0 / (b2 * K)), rel=1e-15)
+    # multiplicative separability: constant ratios along knots and along iterations
+    np.testing.assert_allclose(s[:, 1:] / s[:, :-1], math.exp(1.0 / (b2 * K)), rtol=1e-13)
+    np.testing.assert_allclose(s[1:, :] / s[:-1, :], math.exp(-1.0 / (b1 * I)), rtol=1e-13)
+    # larger variance for later knots and earlier iterations
+    assert np.all(np.diff(s, axis=1) > 0) and np.all(np.diff(s, axis=0) < 0)
+    # the scale multiplies every entry
+    np.testing.assert_allclose(orc.noise_schedule(I, K, b1, b2, 0.3), 0.3 * s, rtol=1e-15)
+
+
+def test_library_noise_schedule_matches_oracle(orc):
+    # host-side helper of the library (no GPU needed)
+    from paper_2511_19204_gb300 import build, mppi
+    build.build()
+    for I, K, b1, b2, sc in ((3, 6, 0.7, 1.3, 0.3), (1, 4, 2.0, 0.5, 1.0), (5, 8, 0.25, 4.0, 0.05)):
+        got = mppi.noise_schedule(I, K, b1, b2, sc)
+        np.testing.assert_allclose(got, orc.noise_schedule(I, K, b1, b2, sc), rtol=2e-7)
+    with pytest.raises(mppi.MppiError):
+        mppi.noise_schedule(0, 4, 1.0, 1.0)
+
+
+# ------------------------------------------------------------------------------------
+# Sec. III-E: state prediction and shift of tau_best
+# ------------------------------------------------------------------------------------
+def test_shift_identity_and_cubic(orc):
+    rng = np.random.default_rng(21)
+    H, nk, dt = 200, 6, 0.005
+    T = H * dt
+    dtk = T / (nk - 1)
+    kn = rng.normal(size=(nk, 2, 3))
+    np.testing.assert_array_equal(orc.shift_knots(kn, H, 0, dt), kn)       # no delay: unchanged
+    # knots sampled from cubics: the shifted knots are the cubics at t_j + delay, and past
+    # the horizon end the end point (value and slope at T) is held
+    polys = [np.polynomial.Polynomial(rng.normal(size=4)) for _ in range(3)]
+    for i, p in enumerate(polys):
+        for j in range(nk):
+            kn[j, 0, i] = p(j * dtk)
+            kn[j, 1, i] = p.deriv()(j * dtk)
+    for steps in (1, 7, 40, 199, 260):
+        sh = orc.shift_knots(kn, H, steps, dt)
+        for i, p in enumerate(polys):
+            for j in range(nk):
+                t = min(j * dtk + steps * dt, T)
+                assert sh[j, 0, i] == pytest.approx(p(t), rel=1e-11, abs=1e-11)
+                assert sh[j, 1, i] == pytest.approx(p.deriv()(t), rel=1e-10, abs=1e-10)
+
+
+def test_prediction_is_the_rollout_prefix(orc):
+    p = S.scale_quadruped(n=4)
+    kn = orc.sample_knots(p.model.nj, p.nk, 4, p.horizon, p.dt, p.nominal, p.sigma[0], seed=3)[2]
+    _, _, tr = orc.rollout(p.model, p.state, kn, p.horizon, p.dt, traj=True)
+    for d in (0, 1, 4, 10, p.horizon):
+        np.testing.assert_array_equal(orc.predict_state(p.model, p.state, kn, p.horizon, d, p.dt), tr[d])
