@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-samples", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-instance workload")
+    ap.add_argument("--no-receding", action="store_true", help="skip the receding-horizon cycle timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--no-configs", action="store_true", help="skip the other single-instance configurations")
     return ap.parse_args()
@@ -281,6 +282,52 @@ def other_configs(mppi, synth, torch, flops):
         out[f"scale_quadruped_K{n}"] = single_instance(mppi, synth, torch, flops, synth.scale_quadruped(n=n))
     out["humanoid_K2048"] = single_instance(mppi, synth, torch, flops, synth.humanoid_problem())
     return out
+
+
+def receding_extra(mppi, synth, torch, p, reps=20, warmup=3, delays=(1, 5, 20)):
+    """The receding-horizon cycle of Sec. III-E on device buffers: predict the state after
+    the compute delay from the resident warm start, shift the warm start by the delay,
+    solve from the prediction. Timed on the controller's stream (CUDA events, L2 flushed
+    before each timed cycle)."""
+    stream = torch.cuda.Stream()
+    ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream)
+    ctrl.autotune()
+    x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
+    xp = torch.zeros_like(x)
+    out = torch.zeros(ctrl.E, dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ms = []
+        for i in range(warmup + reps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    solve_ms = timed(lambda: ctrl.solve_device(x.data_ptr(), out.data_ptr()))
+    res = {"workload": f"{p.n} samples, H {p.horizon}, {p.nk} knots, {p.iters} iterations, dt {p.dt}",
+           "solve_ms": solve_ms, "delay_steps_at_solve_latency": int(solve_ms * 1e-3 / p.dt), "delays": {}}
+    for d in delays:
+        def cycle():
+            ctrl.predict_state_device(x.data_ptr(), d, xp.data_ptr())
+            ctrl.shift_warm_start(d)
+            ctrl.solve_device(xp.data_ptr(), out.data_ptr())
+        res["delays"][str(d)] = {
+            "cycle_ms": timed(cycle),
+            "predict_ms": timed(lambda: ctrl.predict_state_device(x.data_ptr(), d, xp.data_ptr())),
+            "shift_ms": timed(lambda: ctrl.shift_warm_start(d))}
+    ctrl.sync()
+    res["kernels_per_cycle"] = 2 + ctrl.kernels_per_solve
+    return res
 
 
 def batched_extra(mppi, synth, torch, count=256, reps=5):
@@ -548,6 +595,11 @@ def run_ours(args, rank, world, local):
             line["other_configs"] = other_configs(mppi, synth, torch, flops)
         except Exception as exc:  # reported, never silently dropped
             line["other_configs"] = {"error": repr(exc)}
+    if not args.no_receding:
+        try:
+            line["receding_horizon"] = receding_extra(mppi, synth, torch, p)
+        except Exception as exc:  # reported, never silently dropped
+            line["receding_horizon"] = {"error": repr(exc)}
     if not args.no_batched:
         try:
             line["batched_uneven"] = batched_extra(mppi, synth, torch)
