@@ -281,6 +281,7 @@ def other_configs(mppi, synth, torch, flops):
     for n in (1024, 4096):
         out[f"scale_quadruped_K{n}"] = single_instance(mppi, synth, torch, flops, synth.scale_quadruped(n=n))
     out["humanoid_K2048"] = single_instance(mppi, synth, torch, flops, synth.humanoid_problem())
+    out["paper_cost_walking_K8192"] = single_instance(mppi, synth, torch, flops, synth.paper_walking())
     return out
 
 

@@ -78,11 +78,22 @@ typedef int32_t mppi_status;
  * (Eq. pd-controller; Eq. vel-clamp uses q_min/q_max, +-INFINITY disables it).
  * Contacts are points contact_pos[c] on body contact_body[c] against the ground plane
  * z = 0: f_n = max(0, k*depth - c*v_z), f_t = -mu f_n v_t / sqrt(|v_t|^2 + eps_f^2).
- * Running cost c(x_h, u_h) = w_z (z - z_des)^2 + w_vx (vx - vx_des)^2 + w_tilt tilt^2
- * + w_tau |u|^2 with z and tilt of body cost_body and vx the world-x velocity of the
- * base origin (Sec. IV-A cost sum, quadratic terms of the synthetic workloads).
+ * Cost S = sum_{h<H} c(x_h, u_h) + c_T(x_H) (Sec. IV-A) on the pre-step state of each
+ * step. c sums two groups of terms; a zero weight disables its term.
+ *  - Quadratic terms of the synthetic workloads: w_z (z - z_des)^2 + w_vx (vx - vx_des)^2
+ *    + w_tilt tilt^2 + w_tau |u|^2, with z and tilt of body cost_body and vx the world-x
+ *    velocity of the base origin.
+ *  - The modular running cost of Sec. IV-A (Eq. running cost): w_h |p_base,z - z_des|
+ *    + w_orient ||log3(R_base^T R_des)||^2 + w_q ||q - q_init||^2
+ *    + w_cvel sum_c ||v_c||_1 + w_cforce sum_c ||f_c - f0||_1, with R_des the rotation of
+ *    the unit quaternion quat_des (w, x, y, z), v_c the world velocity of contact point c
+ *    summed over the points in contact (depth > 0), f_c its world contact force (zero
+ *    off contact) summed over all points, f0 the same for every point.
+ *  - Terminal cost c_T = w_term ||p_base(x_H) - p_target||_1 with
+ *    p_target = p_base(x_0) + pdot_des H dt (Sec. IV-A Eq. terminal cost).
  * q_init (nullable, [nj]) seeds the initial nominal theta^q = q_init, theta^v = 0
- * (Alg. 1 initialisation); NULL means zeros. All arrays are read during the call only.
+ * (Alg. 1 initialisation) and is q0 of the w_q term; NULL means zeros. All arrays are
+ * read during the call only. Weights must be finite and >= 0.
  */
 typedef struct mppi_model_desc {
     int32_t nb;                   /* bodies, 1..MPPI_MAX_BODIES */
@@ -106,6 +117,11 @@ typedef struct mppi_model_desc {
     const double* q_init;         /* [nb-1] or NULL */
     double contact_k, contact_c, mu, eps_f, gravity;
     double z_des, vx_des, w_z, w_vx, w_tilt, w_tau;
+    /* modular cost of Sec. IV-A (Tab. II weight sets) */
+    double w_h, w_orient, w_q, w_cvel, w_cforce, w_term;
+    double quat_des[4];           /* R_des as a quaternion (w, x, y, z), normalised here; all zeros = identity */
+    double f0[3];                 /* f0, world frame */
+    double pdot_des[3];           /* desired base velocity of p_target, world frame */
 } mppi_model_desc;
 
 typedef struct mppi_params {

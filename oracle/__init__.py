@@ -43,7 +43,11 @@ class _Model(C.Structure):
                 ("contact_k", C.c_double), ("contact_c", C.c_double), ("mu", C.c_double),
                 ("eps_f", C.c_double), ("gravity", C.c_double),
                 ("z_des", C.c_double), ("vx_des", C.c_double), ("w_z", C.c_double),
-                ("w_vx", C.c_double), ("w_tilt", C.c_double), ("w_tau", C.c_double)]
+                ("w_vx", C.c_double), ("w_tilt", C.c_double), ("w_tau", C.c_double),
+                ("w_h", C.c_double), ("w_orient", C.c_double), ("w_q", C.c_double),
+                ("w_cvel", C.c_double), ("w_cforce", C.c_double), ("w_term", C.c_double),
+                ("quat_des", C.c_double * 4), ("f0", C.c_double * 3), ("pdot_des", C.c_double * 3),
+                ("q0", _dp)]
 
 
 _lib = None
@@ -116,6 +120,9 @@ class OracleModel:
             contact_pos=_d(m.contact_pos).reshape(-1, 3) if m.nc else np.zeros((1, 3)))
         if m.nc == 0:
             self._keep["contact_body"] = np.zeros(1, dtype=np.int32)
+        self._keep["q0"] = _d(m.q_stand) if m.q_stand is not None and m.nj else np.zeros(max(m.nj, 1))
+        qd = np.asarray(getattr(m, "quat_des", (1.0, 0.0, 0.0, 0.0)), dtype=np.float64)
+        qd = qd / np.linalg.norm(qd) if np.linalg.norm(qd) > 0 else np.array([1.0, 0.0, 0.0, 0.0])
         k = self._keep
         self.s = _Model(nb=m.nb, nc=m.nc, fixed_base=int(m.fixed_base), cost_body=m.cost_body,
                         parent=k["parent"].ctypes.data_as(_ip), axis=_ptr(k["axis"]),
@@ -127,7 +134,11 @@ class OracleModel:
                         contact_pos=_ptr(k["contact_pos"]),
                         contact_k=m.contact_k, contact_c=m.contact_c, mu=m.mu, eps_f=m.eps_f,
                         gravity=m.gravity, z_des=m.z_des, vx_des=m.vx_des, w_z=m.w_z,
-                        w_vx=m.w_vx, w_tilt=m.w_tilt, w_tau=m.w_tau)
+                        w_vx=m.w_vx, w_tilt=m.w_tilt, w_tau=m.w_tau,
+                        w_h=m.w_h, w_orient=m.w_orient, w_q=m.w_q, w_cvel=m.w_cvel,
+                        w_cforce=m.w_cforce, w_term=m.w_term,
+                        quat_des=(C.c_double * 4)(*qd), f0=(C.c_double * 3)(*m.f0),
+                        pdot_des=(C.c_double * 3)(*m.pdot_des), q0=_ptr(k["q0"]))
         self.ref = C.byref(self.s)
         self.nj = m.nj
         self.nx = m.nx

@@ -23,8 +23,9 @@
  *              contact and smooth Coulomb friction, semi-implicit Euler; these stand in
  *              for the paper's simulator (Sec. III-C, Sec. IV-A).
  *              CRBA + RNEA (ibid. ch. 5-6) are here only as an independent check.
- *   cost       Sec. IV-A cost sum S = sum_{h<H} c(x_h, u_h) (+ zero terminal cost) with
- *              the quadratic running cost of the synthetic workloads.
+ *   cost       Sec. IV-A cost sum S = sum_{h<H} c(x_h, u_h) + c_T(x_H): the quadratic
+ *              running terms of the synthetic workloads plus the paper's modular
+ *              running and terminal cost (zero weights disable a term).
  *   weights    Sec. III-C Eq. (omega-weights) and the min-max normalised
  *              Eq. (softmax_minmax), evaluated as a log-sum-exp.
  *   average    Sec. III-C Eq. (update-nominal) on the knots.
@@ -60,6 +61,12 @@ typedef struct {
     const double* contact_pos;   /* [nc][3] */
     double contact_k, contact_c, mu, eps_f, gravity;
     double z_des, vx_des, w_z, w_vx, w_tilt, w_tau;
+    /* modular cost of Sec. IV-A */
+    double w_h, w_orient, w_q, w_cvel, w_cforce, w_term;
+    double quat_des[4];        /* (w, x, y, z), unit */
+    double f0[3];
+    double pdot_des[3];
+    const double* q0;          /* [nb-1] or NULL (zeros) */
 } orc_model;
 
 /* ------------------------------------------------------------------------------------ */
@@ -706,6 +713,61 @@ static double running_cost(const orc_model* m, const double* x, const orc_kin* K
            m->w_tilt * tilt * tilt + m->w_tau * tt;
 }
 
+/* Modular running cost of Sec. IV-A (Eq. running cost), on the pre-step state:
+ *   w_h |p_base,z - z_des| + w_orient ||log3(R_base^T R_des)||^2 + w_q ||q - q0||^2
+ *   + w_cvel sum_{c in contact} ||v_c||_1 + w_cforce sum_c ||f_c - f0||_1.
+ * ||log3(R_base^T R_des)|| is the rotation angle of the relative quaternion
+ * conj(q_base) * q_des: 2 atan2(|vector part|, |scalar part|). A contact point is in
+ * contact when it penetrates the ground (depth > 0); v_c is its world velocity and f_c
+ * its world contact force (zero when not in contact). */
+static double modular_cost(const orc_model* m, const double* x, const orc_kin* K) {
+    const int nj = m->nb - 1;
+    double S = 0;
+    S += m->w_h * fabs(x[2] - m->z_des);
+    const double* qb = x + 3;
+    const double* qd = m->quat_des;
+    /* conj(qb) * qd */
+    double rw = qb[0] * qd[0] + qb[1] * qd[1] + qb[2] * qd[2] + qb[3] * qd[3];
+    double rx = qb[0] * qd[1] - qb[1] * qd[0] - qb[2] * qd[3] + qb[3] * qd[2];
+    double ry = qb[0] * qd[2] + qb[1] * qd[3] - qb[2] * qd[0] - qb[3] * qd[1];
+    double rz = qb[0] * qd[3] - qb[1] * qd[2] + qb[2] * qd[1] - qb[3] * qd[0];
+    double th = 2.0 * atan2(sqrt(rx * rx + ry * ry + rz * rz), fabs(rw));
+    S += m->w_orient * th * th;
+    for (int j = 0; j < nj; ++j) {
+        double d = x[7 + j] - (m->q0 ? m->q0[j] : 0.0);
+        S += m->w_q * d * d;
+    }
+    for (int c = 0; c < m->nc; ++c) {
+        int b = m->contact_body[c];
+        const double* rc = &m->contact_pos[3 * c];
+        double pw[3], vloc[3], vw[3], t[3], F[3] = {0, 0, 0};
+        m3_vec(K->R[b], rc, t);
+        for (int a = 0; a < 3; ++a) pw[a] = K->p[b][a] + t[a];
+        cross3(K->v[b], rc, vloc);
+        for (int a = 0; a < 3; ++a) vloc[a] += K->v[b][3 + a];
+        m3_vec(K->R[b], vloc, vw);
+        if (-pw[2] > 0) {
+            double fn = m->contact_k * (-pw[2]) - m->contact_c * vw[2];
+            if (fn < 0) fn = 0;
+            double sc = -m->mu * fn / sqrt(vw[0] * vw[0] + vw[1] * vw[1] + m->eps_f * m->eps_f);
+            F[0] = sc * vw[0];
+            F[1] = sc * vw[1];
+            F[2] = fn;
+            S += m->w_cvel * (fabs(vw[0]) + fabs(vw[1]) + fabs(vw[2]));
+        }
+        S += m->w_cforce * (fabs(F[0] - m->f0[0]) + fabs(F[1] - m->f0[1]) + fabs(F[2] - m->f0[2]));
+    }
+    return S;
+}
+
+/* Terminal cost of Sec. IV-A (Eq. terminal cost): w_term ||p_base(x_H) - p_target||_1,
+ * p_target = p_base(x_0) + pdot_des H dt. */
+static double terminal_cost(const orc_model* m, const double* x0, const double* xH, int H, double dt) {
+    double S = 0;
+    for (int a = 0; a < 3; ++a) S += fabs(xH[a] - (x0[a] + m->pdot_des[a] * H * dt));
+    return m->w_term * S;
+}
+
 /* Semi-implicit Euler: velocities first, then positions with the new velocities; base
  * orientation by the quaternion exponential of the new body angular velocity. */
 static void integrate(const orc_model* m, double* x, const double* acc, double dt) {
@@ -756,8 +818,8 @@ int orc_step(const orc_model* m, double* x, const double* tau, double dt) {
 }
 
 /* Rollout of one sample (Alg. 1 "simulate"): H steps from x0 tracking the Hermite
- * setpoints of knots [nk][2][nu]; returns S = sum_h c(x_h, u_h). x_final [nx] and
- * traj [(H+1)][nx] are optional. */
+ * setpoints of knots [nk][2][nu]; returns S = sum_h c(x_h, u_h) + c_T(x_H) (Sec. IV-A).
+ * x_final [nx] and traj [(H+1)][nx] are optional. */
 double orc_rollout(const orc_model* m, const double* x0, const double* knots, int nk, int H,
                    double dt, double* x_final, double* traj) {
     const int nj = m->nb - 1, nq = 7 + nj, nx = nq + 6 + nj;
@@ -781,10 +843,11 @@ double orc_rollout(const orc_model* m, const double* x0, const double* knots, in
             S = NAN;
             break;
         }
-        S += running_cost(m, x, K, tau);
+        S += running_cost(m, x, K, tau) + modular_cost(m, x, K);
         integrate(m, x, acc, dt);
         if (traj) memcpy(traj + (size_t)(h + 1) * nx, x, sizeof(double) * nx);
     }
+    if (H > 0 && isfinite(S)) S += terminal_cost(m, x0, x, H, dt);
     if (x_final) memcpy(x_final, x, sizeof(double) * nx);
     free(K);
     return S;

@@ -168,6 +168,37 @@ static void fill_model(const mppi_model_desc& d, const std::vector<int>& level, 
     M.w_vx = (T)d.w_vx;
     M.w_tilt = (T)d.w_tilt;
     M.w_tau = (T)d.w_tau;
+    M.w_h = (T)d.w_h;
+    M.w_orient = (T)d.w_orient;
+    M.w_q = (T)d.w_q;
+    M.w_cvel = (T)d.w_cvel;
+    M.w_cforce = (T)d.w_cforce;
+    M.w_term = (T)d.w_term;
+    M.cf_off = (T)(d.w_cforce * (fabs(d.f0[0]) + fabs(d.f0[1]) + fabs(d.f0[2])));
+    for (int k = 0; k < 3; ++k) {
+        M.f0[k] = (T)d.f0[k];
+        M.pdot_des[k] = (T)d.pdot_des[k];
+    }
+    // R_des from the normalised quaternion (all zeros = identity)
+    double qw = d.quat_des[0], qx = d.quat_des[1], qy = d.quat_des[2], qz = d.quat_des[3];
+    const double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+    if (qn > 0) {
+        qw /= qn;
+        qx /= qn;
+        qy /= qn;
+        qz /= qn;
+    } else {
+        qw = 1;
+        qx = qy = qz = 0;
+    }
+    const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz),     2 * (qx * qz + qw * qy),
+                         2 * (qx * qy + qw * qz),     1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                         2 * (qx * qz - qw * qy),     2 * (qy * qz + qw * qx),     1 - 2 * (qx * qx + qy * qy)};
+    for (int k = 0; k < 9; ++k) M.Rdes[k] = (T)R[k];
+    M.paper_cost = (d.w_h != 0 || d.w_orient != 0 || d.w_q != 0 || d.w_cvel != 0 || d.w_cforce != 0 ||
+                    d.w_term != 0)
+                       ? 1
+                       : 0;
 }
 
 }  // namespace mppi
@@ -212,6 +243,16 @@ mppi_status mppi_model_create(const mppi_model_desc* d, mppi_model** out) {
     if (d->nc > 0 && (!d->contact_body || !d->contact_pos)) return bad("null contact array");
     if (d->parent[0] != -1) return bad("parent[0] must be -1");
     if (d->cost_body < 0 || d->cost_body >= d->nb) return bad("cost_body out of range");
+    {
+        const double w[10] = {d->w_z, d->w_vx, d->w_tilt, d->w_tau, d->w_h, d->w_orient, d->w_q, d->w_cvel,
+                              d->w_cforce, d->w_term};
+        for (double v : w)
+            if (!(v >= 0) || !isfinite(v)) return bad("cost weights must be finite and >= 0");
+        for (int k = 0; k < 4; ++k)
+            if (!isfinite(d->quat_des[k])) return bad("quat_des must be finite");
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(d->f0[k]) || !isfinite(d->pdot_des[k])) return bad("f0 and pdot_des must be finite");
+    }
     std::vector<int> level(d->nb, 0);
     std::vector<std::vector<int>> children(d->nb);
     int nlevels = 1;

@@ -29,6 +29,8 @@ __device__ __forceinline__ float sc_atan2(float y, float x) { return atan2f(y, x
 __device__ __forceinline__ double sc_atan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ float sc_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double sc_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float sc_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double sc_abs(double a) { return fabs(a); }
 __device__ __forceinline__ float sc_min(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double sc_min(double a, double b) { return fmin(a, b); }
 template <typename T>
@@ -68,6 +70,13 @@ struct alignas(16) DevModel {
     T contact_k, contact_c, mu, eps_f;
     T gravity, z_des, vx_des, w_z;
     T w_vx, w_tilt, w_tau, pad1;
+    // modular cost of Sec. IV-A; paper_cost = 0 when every one of its weights is zero
+    T w_h, w_orient, w_q, w_cvel;
+    T w_cforce, w_term, cf_off, pad2;   // cf_off = w_cforce ||f0||_1 (a point off contact)
+    T f0[4];
+    T pdot_des[4];
+    T Rdes[12];                         // R_des row-major (9 used)
+    int32_t paper_cost, pad3[3];
 };
 
 // Tree shapes with a lanes-per-chain kernel.
@@ -195,6 +204,46 @@ __device__ __forceinline__ M3<T> quat_to_R(T w, T x, T y, T z) {
     R.m[7] = T(2) * (y * z + w * x);
     R.m[8] = T(1) - T(2) * (x * x + y * y);
     return R;
+}
+
+// ------------------------------------------------------------------------------------
+// Modular cost of Sec. IV-A (Eq. running cost, Eq. terminal cost), the parts shared by
+// the rollout mappings.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T abs1(V3<T> a) {
+    return sc_abs(a.x) + sc_abs(a.y) + sc_abs(a.z);
+}
+
+// One contact point in contact (depth > 0), world velocity vw and force F:
+// w_cvel ||v_c||_1 + w_cforce ||f_c - f0||_1. Off contact the point adds M.cf_off.
+template <typename T>
+__device__ __forceinline__ T contact_cost(const DevModel<T>& M, V3<T> vw, V3<T> F) {
+    return M.w_cvel * abs1(vw) + M.w_cforce * abs1(F - v3(M.f0[0], M.f0[1], M.f0[2]));
+}
+
+// Base terms of the running cost: w_h |p_z - z_des| + w_orient theta^2 with theta the
+// rotation angle of Q = R^T R_des (||log3 Q|| = theta): cos theta = (tr Q - 1) / 2,
+// sin theta = |(Q21 - Q12, Q02 - Q20, Q10 - Q01)| / 2.
+template <typename T>
+__device__ __forceinline__ T base_cost(const DevModel<T>& M, const M3<T>& R, V3<T> p) {
+    T Q[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Q[3 * a + b] = R.m[a] * M.Rdes[b] + R.m[3 + a] * M.Rdes[3 + b] + R.m[6 + a] * M.Rdes[6 + b];
+    const T vx = Q[7] - Q[5], vy = Q[2] - Q[6], vz = Q[3] - Q[1];
+    const T th = sc_atan2(sc_sqrt(vx * vx + vy * vy + vz * vz), Q[0] + Q[4] + Q[8] - T(1));
+    return M.w_h * sc_abs(p.z - M.z_des) + M.w_orient * th * th;
+}
+
+// Terminal cost: w_term ||p_H - (p_0 + pdot_des H dt)||_1.
+template <typename T>
+__device__ __forceinline__ T terminal_cost(const DevModel<T>& M, V3<T> pH, V3<T> p0, int H, T dt) {
+    const T hd = (T)H * dt;
+    const V3<T> tgt = p0 + hd * v3(M.pdot_des[0], M.pdot_des[1], M.pdot_des[2]);
+    return M.w_term * abs1(pH - tgt);
 }
 
 // ------------------------------------------------------------------------------------

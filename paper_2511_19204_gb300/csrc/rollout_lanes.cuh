@@ -55,9 +55,12 @@ __device__ __forceinline__ V3<float> jpos_of(const DevModel<float>& M, int b) {
     return v3(M.jpos[0][b], M.jpos[1][b], M.jpos[2][b]);
 }
 
+// Contact forces of body b's points; with the modular cost on, `count` lanes also add
+// the points' running-cost terms to pcost (a replicated body counts on one lane).
 __device__ __forceinline__ void body_contacts(const DevModel<float>& M, int b, const Pose& P, V3<float>& fen,
-                                              V3<float>& fef) {
+                                              V3<float>& fef, float& pcost, bool count) {
     const int c0 = M.cfirst[b], cn = M.ccount[b];
+    const bool paper = count && M.paper_cost != 0;
     for (int c = 0; c < cn; ++c) {
         const int ci = c0 + c;
         const V3<float> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
@@ -71,6 +74,9 @@ __device__ __forceinline__ void body_contacts(const DevModel<float>& M, int b, c
             const V3<float> fb = mulT(P.R, F);
             fef = fef + fb;
             fen = fen + cross(rc, fb);
+            if (paper) pcost += contact_cost(M, vw, F);
+        } else if (paper) {
+            pcost += M.cf_off;
         }
     }
 }
@@ -108,7 +114,7 @@ __device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Ar
 // the bias (contact forces included).
 template <bool KEEP>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, float q, float qd, const Pose& Pp,
-                                           Pose& P, BodyMem& m) {
+                                           Pose& P, BodyMem& m, float& pcost, bool count) {
     const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
     sincosf(q, &m.s, &m.c);
     const M3<float> Rj = axis_rotation(a, m.s, m.c);
@@ -121,8 +127,12 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, floa
     m.cw = cross(P.w, sa);
     m.cv = cross(P.v, sa);
     V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-    body_contacts(M, b, P, fen, fef);
+    body_contacts(M, b, P, fen, fef, pcost, count);
     body_bias(M, b, P, fen, fef, m.x0, m.x1);
+    if (count && M.paper_cost) {
+        const float dq = q - M.q_init[b];
+        pcost += M.w_q * dq * dq;
+    }
 }
 
 // Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
@@ -240,6 +250,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
     // base (replicated), branch joint (replicated on lanes 2, 3), chain joints
     Pose B;
     V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
+    const V3<float> p_start = p;
     float qw = (float)x0[3], qx = (float)x0[4], qy = (float)x0[5], qz = (float)x0[6];
     V3<float> vl = v3((float)x0[nq], (float)x0[nq + 1], (float)x0[nq + 2]);
     V3<float> w = v3((float)x0[nq + 3], (float)x0[nq + 4], (float)x0[nq + 5]);
@@ -287,17 +298,19 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         B.w = M.fixed_base ? v3(0.f, 0.f, 0.f) : w;
         B.v = M.fixed_base ? v3(0.f, 0.f, 0.f) : vl;
         V3<float> p0n, p0f;
+        float pcost = 0.f;  // this lane's share of the modular running cost
         {
             V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-            body_contacts(M, 0, B, fen, fef);
+            body_contacts(M, 0, B, fen, fef, pcost, g == 0);
             body_bias(M, 0, B, fen, fef, p0n, p0f);
         }
+        if (M.paper_cost && g == 0) pcost += base_cost(M, B.R, B.p);
         float tz = 0.f, tt = 0.f;
         if (cb == 0) cost_terms(M, B, tz, tt);
         BodyMem mb;
         Pose PB;
         if (on_branch) {
-            body_pass1<KEEP>(M, bb, qb, qdb, B, PB, mb);
+            body_pass1<KEEP>(M, bb, qb, qdb, B, PB, mb, pcost, g == 2);
             if (cb == bb) cost_terms(M, PB, tz, tt);
         }
         BodyMem mem[LMAX];
@@ -307,7 +320,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             for (int j = 0; j < LMAX; ++j) {
                 if (j < len) {
                     Pose P;
-                    body_pass1<KEEP>(M, b0 + j, q[j], qd[j], Pp, P, mem[j]);
+                    body_pass1<KEEP>(M, b0 + j, q[j], qd[j], Pp, P, mem[j], pcost, true);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
@@ -392,10 +405,11 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         for (int j = 0; j < LMAX; ++j) te += tau[j] * tau[j];
         if (g == 2) te += taub * taub;
         te = lsum(te);
+        if (M.paper_cost) pcost = lsum(pcost);
         {
             const float vx = M.fixed_base ? 0.f : (B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z);
             const float dv = vx - M.vx_des;
-            const float c = tz + M.w_vx * dv * dv + tt + M.w_tau * te;
+            const float c = tz + M.w_vx * dv * dv + tt + M.w_tau * te + pcost;
             const float y = c - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
@@ -437,6 +451,12 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             qy = ny * inv;
             qz = nz * inv;
         }
+    }
+    if (M.paper_cost) {  // terminal cost (every lane holds the base)
+        const float y = terminal_cost(M, p, p_start, H, dt) - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
     }
     if (xf) {
         if (g == 0) {

@@ -68,6 +68,7 @@ struct StepOut {
     V3<T> aw, av;     // root lane: true base spatial acceleration (body coordinates)
     M3<T> R0;         // root lane: base rotation (pre-step)
     T cost_z, cost_tilt;  // cost-body terms (valid on every lane after the broadcast)
+    T cost_paper;         // modular running-cost terms of Sec. IV-A (every lane; 0 when off)
 };
 
 // One evaluation of the forward dynamics for the group's sample under joint torque tau
@@ -127,6 +128,8 @@ __device__ __forceinline__ void warp_dynamics(const DevModel<T>& M, const LaneCo
     }
     // ---- contact forces (ground plane z = 0), external spatial force in body frame ----
     V3<T> fe_n = v3(T(0), T(0), T(0)), fe_f = fe_n;
+    const bool paper = M.paper_cost != 0;
+    T pcost = T(0);  // this lane's share of the modular running cost
     for (int c = 0; c < L.ccount; ++c) {
         const int ci = L.cfirst + c;
         const V3<T> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
@@ -140,8 +143,21 @@ __device__ __forceinline__ void warp_dynamics(const DevModel<T>& M, const LaneCo
             const V3<T> fb = mulT(R, F);
             fe_f = fe_f + fb;
             fe_n = fe_n + cross(rc, fb);
+            if (paper) pcost += contact_cost(M, vw, F);
+        } else if (paper) {
+            pcost += M.cf_off;
         }
     }
+    if (paper) {
+        if (L.joint) {
+            const T dq = S.q - M.q_init[gl];
+            pcost += M.w_q * dq * dq;
+        }
+        if (gl == 0) pcost += base_cost(M, R, p);
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) pcost += __shfl_xor_sync(0xffffffffu, pcost, off, G);
+    }
+    out.cost_paper = pcost;
     // ---- bias pA = v x* (I v) - f_ext ; articulated inertia starts at the body's ----
     // h = I v = (Ao w + mc x vl, m vl - mc x w); v x* h = (w x hn + vl x hf, w x hf) with
     // vl x hf = -vl x (mc x w) exactly (vl x vl = 0), written so FP32 does not leave a
@@ -367,6 +383,7 @@ __device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>&
     const int nj = M.nb - 1;
     LaneState<T> S;
     load_lane_state(M, L, gl, x0, S);
+    const V3<T> p_start = S.p;
     const T inv_dtk = T(1) / dtk;
     T sum = T(0), comp = T(0);
     int kcur = -1;
@@ -407,13 +424,19 @@ __device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>&
         if (gl == 0) {
             const T vx = M.fixed_base ? T(0) : (o.R0.m[0] * S.vl.x + o.R0.m[1] * S.vl.y + o.R0.m[2] * S.vl.z);
             const T dv = vx - M.vx_des;
-            const T c = o.cost_z + M.w_vx * dv * dv + o.cost_tilt + M.w_tau * tt;
+            const T c = o.cost_z + M.w_vx * dv * dv + o.cost_tilt + M.w_tau * tt + o.cost_paper;
             const T y = c - comp;
             const T t = sum + y;
             comp = (t - sum) - y;
             sum = t;
         }
         integrate_lane(M, L, gl, o, dt, S);
+    }
+    if (M.paper_cost && nsteps == H && gl == 0) {  // terminal cost of a full rollout
+        const T y = terminal_cost(M, S.p, p_start, H, dt) - comp;
+        const T t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
     }
     if (xf) store_lane_state(M, L, gl, S, xf);
     return gshfl<T, G>(sum, 0);

@@ -23,19 +23,32 @@ Per contact point in penetration: position 18, velocity 27, normal force 4,
 Per floating base: rotation from quaternion 25, bias 78, 6x6 Cholesky solve 161,
   gravity 6, integration 94 (velocities 12, position 21, quaternion exponential
   and product 61), running cost 42                                              406
+With the modular cost of Sec. IV-A on (any of its weights non-zero), in addition:
+  per joint: (q - q0)^2 weighted and accumulated                                   4
+  per contact point: ||v_c||_1 5, ||f_c - f0||_1 8, weights and accumulation 4    17
+  per base: height term 3, R^T R_des 54, rotation angle (vee 3, norm 6, trace 3,
+  arctangent 1), theta^2 term 2, reduction 3                                      75
+  (the terminal term, ~15 flops per rollout, is not counted per step)
 """
 from __future__ import annotations
 
 PER_JOINT = 55 + 31 + 111 + 21 + 78 + 565 + 27 + 67 + 4 + 2
 PER_CONTACT = 18 + 27 + 4 + 12 + 15 + 12
 PER_BASE = 25 + 78 + 161 + 6 + 94 + 42
+MOD_JOINT = 4
+MOD_CONTACT = 5 + 8 + 4
+MOD_BASE = 3 + 54 + 3 + 6 + 3 + 1 + 2 + 3
+MOD_WEIGHTS = ("w_h", "w_orient", "w_q", "w_cvel", "w_cforce", "w_term")
 
 
 def flops_per_step(model, contacts_active=None) -> int:
     """Flops of one step of one sample. ``contacts_active`` defaults to every contact
     point (the standing / walking regime); pass a number for another regime."""
     nc = model.nc if contacts_active is None else contacts_active
-    return PER_JOINT * model.nj + PER_CONTACT * nc + PER_BASE
+    f = PER_JOINT * model.nj + PER_CONTACT * nc + PER_BASE
+    if any(getattr(model, w, 0.0) for w in MOD_WEIGHTS):
+        f += MOD_JOINT * model.nj + MOD_CONTACT * model.nc + MOD_BASE
+    return f
 
 
 def fp32_peak_tflops(sms: int = 152, clock_mhz: float = 2070.0) -> float:

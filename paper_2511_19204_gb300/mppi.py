@@ -65,7 +65,10 @@ class mppi_model_desc(C.Structure):
                 ("contact_k", C.c_double), ("contact_c", C.c_double), ("mu", C.c_double),
                 ("eps_f", C.c_double), ("gravity", C.c_double), ("z_des", C.c_double),
                 ("vx_des", C.c_double), ("w_z", C.c_double), ("w_vx", C.c_double),
-                ("w_tilt", C.c_double), ("w_tau", C.c_double)]
+                ("w_tilt", C.c_double), ("w_tau", C.c_double),
+                ("w_h", C.c_double), ("w_orient", C.c_double), ("w_q", C.c_double),
+                ("w_cvel", C.c_double), ("w_cforce", C.c_double), ("w_term", C.c_double),
+                ("quat_des", C.c_double * 4), ("f0", C.c_double * 3), ("pdot_des", C.c_double * 3)]
 
 
 class mppi_params(C.Structure):
@@ -219,7 +222,10 @@ class Model:
                             contact_pos=_pd(k["contact_pos"]), q_init=_pd(k["q_init"]),
                             contact_k=m.contact_k, contact_c=m.contact_c, mu=m.mu, eps_f=m.eps_f,
                             gravity=m.gravity, z_des=m.z_des, vx_des=m.vx_des, w_z=m.w_z, w_vx=m.w_vx,
-                            w_tilt=m.w_tilt, w_tau=m.w_tau)
+                            w_tilt=m.w_tilt, w_tau=m.w_tau, w_h=m.w_h, w_orient=m.w_orient, w_q=m.w_q,
+                            w_cvel=m.w_cvel, w_cforce=m.w_cforce, w_term=m.w_term,
+                            quat_des=(C.c_double * 4)(*m.quat_des), f0=(C.c_double * 3)(*m.f0),
+                            pdot_des=(C.c_double * 3)(*m.pdot_des))
         h = _P()
         _check(L.mppi_model_create(C.byref(d), C.byref(h)))
         self.h = h

@@ -83,8 +83,18 @@ class RobotModel:
     w_vx: float = 1.0
     w_tilt: float = 1.0
     w_tau: float = 1.0e-3
-    q_stand: np.ndarray = None  # f64 [nj]
+    q_stand: np.ndarray = None  # f64 [nj]; also q0 of the w_q cost term
     base_z0: float = 0.0
+    # modular cost of Sec. IV-A (zero weights disable a term)
+    w_h: float = 0.0
+    w_orient: float = 0.0
+    w_q: float = 0.0
+    w_cvel: float = 0.0
+    w_cforce: float = 0.0
+    w_term: float = 0.0
+    quat_des: tuple = (1.0, 0.0, 0.0, 0.0)
+    f0: tuple = (0.0, 0.0, 0.0)
+    pdot_des: tuple = (0.0, 0.0, 0.0)
 
     @property
     def nb(self) -> int:
@@ -354,6 +364,36 @@ def point_mass(m: float = 1.0, k: float = 2.0e4, c: float = 200.0, mu: float = 0
                    eps_f=eps_f, w_tau=0.0)
 
 
+# --------------------------------------------------------------------------------------
+# The modular cost of Sec. IV-A with the weight sets of Tab. II
+# --------------------------------------------------------------------------------------
+# (w_h, w_orient, w_q, w_c,vel, w_c,force, w_H) per task, Tab. II
+TAB2_WEIGHTS = {
+    "walking": (1e2, 10.0, 0.0, 0.5, 5e-2, 2.5e3),
+    "jumping": (1.0, 0.5, 0.3, 1.0, 5e-4, 2e3),
+    "handstand": (50.0, 10.0, 0.3, 1.0, 5e-4, 0.0),
+    "backflip": (1.0, 0.5, 0.3, 1.0, 5e-4, 2e3),
+    "bipedal": (10.0, 1.0, 0.3, 1.0, 5e-4, 2e2),
+}
+
+
+def with_paper_cost(m: RobotModel, task: str, pdot_des=(0.0, 0.0, 0.0), z_des: float | None = None,
+                    quat_des=(1.0, 0.0, 0.0, 0.0), keep_quadratic: bool = False) -> RobotModel:
+    """A copy of m costed by the modular running and terminal cost with Tab. II's weights
+    for `task`; f0 is the standing load per contact point (total weight / nc, vertical)
+    and the quadratic terms are switched off unless keep_quadratic."""
+    w = TAB2_WEIGHTS[task]
+    total = float(np.sum(m.mass)) * m.gravity
+    kw = dict(w_h=w[0], w_orient=w[1], w_q=w[2], w_cvel=w[3], w_cforce=w[4], w_term=w[5],
+              quat_des=tuple(float(v) for v in quat_des), pdot_des=tuple(float(v) for v in pdot_des),
+              f0=(0.0, 0.0, total / max(m.nc, 1)))
+    if z_des is not None:
+        kw["z_des"] = float(z_des)
+    if not keep_quadratic:
+        kw.update(w_z=0.0, w_vx=0.0, w_tilt=0.0, w_tau=0.0)
+    return dataclasses.replace(m, name=m.name + "_" + task, **kw)
+
+
 MODELS = {"quadruped": quadruped, "humanoid": humanoid, "pendulum": pendulum, "chain2": chain2,
           "free_body": free_body, "branch3": branch3, "point_mass": point_mass}
 
@@ -451,6 +491,14 @@ def scale_quadruped(n: int = 8192, seed_state: int = 20, seed_noise: int = 1) ->
                    sigma=linear_sigma(6, 3),
                    state=standing_state(m, jitter=0.02, base_vel=0.5, seed=seed_state),
                    nominal=nominal_knots(m, 6), seed=seed_noise)
+
+
+def paper_walking(n: int = 8192, v: float = 0.5, seed_state: int = 20, seed_noise: int = 1) -> Problem:
+    """The scale workload (6 knots over 1.0 s, dt 0.005, 3 iterations) costed by the
+    modular cost with Tab. II's walking weights, forward target velocity v."""
+    p = scale_quadruped(n=n, seed_state=seed_state, seed_noise=seed_noise)
+    p.model = with_paper_cost(p.model, "walking", pdot_des=(v, 0.0, 0.0))
+    return p
 
 
 def humanoid_problem(n: int = 2048, seed_noise: int = 3) -> Problem:

@@ -678,3 +678,119 @@ def test_prediction_is_the_rollout_prefix(orc):
     _, _, tr = orc.rollout(p.model, p.state, kn, p.horizon, p.dt, traj=True)
     for d in (0, 1, 4, 10, p.horizon):
         np.testing.assert_array_equal(orc.predict_state(p.model, p.state, kn, p.horizon, d, p.dt), tr[d])
+
+
+# ------------------------------------------------------------------------------------
+# Modular cost of Sec. IV-A (Eq. running cost, Eq. terminal cost)
+# ------------------------------------------------------------------------------------
+_NO_QUAD = dict(w_z=0.0, w_vx=0.0, w_tilt=0.0, w_tau=0.0)
+
+
+def _axis_quat(axis, ang):
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    return np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * a])
+
+
+def test_modular_cost_drifting_body(orc):
+    # a free body without gravity drifts at constant velocity (zero acceleration, exact
+    # under semi-implicit Euler): p_h = p0 + h dt v. Height term, terminal term and the
+    # orientation term (fixed attitude alpha about an axis, R_des = identity) in closed form.
+    alpha = 0.35
+    m = S.free_body().copy(gravity=0.0, w_h=3.0, w_orient=2.0, w_term=7.0, z_des=0.4,
+                           pdot_des=(0.2, -0.1, 0.05), **_NO_QUAD)
+    x = np.zeros(m.nx)
+    x[3:7] = _axis_quat((1.0, 2.0, -0.5), alpha)
+    x[0:3] = [0.1, 0.2, 1.0]
+    v = np.array([0.6, 0.3, -0.4])
+    x[m.nq:m.nq + 3] = _quat_R(x[3:7]).T @ v
+    H, dt = 40, 0.01
+    S_or, xf = orc.rollout(m, x, np.zeros((2, 2, 0)), H, dt)
+    Sx = sum(3.0 * abs(1.0 + h * dt * v[2] - 0.4) + 2.0 * alpha ** 2 for h in range(H))
+    Sx += 7.0 * np.sum(np.abs(H * dt * (v - np.array([0.2, -0.1, 0.05]))))
+    assert S_or == pytest.approx(Sx, rel=1e-12)
+    np.testing.assert_allclose(xf[0:3], x[0:3] + H * dt * v, atol=1e-13)
+
+
+def test_modular_cost_orientation_is_the_geodesic_angle(orc):
+    # ||log3(R^T R_des)|| against scipy's rotation magnitude for random attitude pairs
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(8)
+    H, dt = 1, 0.01
+    for _ in range(20):
+        qb = rng.normal(size=4)
+        qd = rng.normal(size=4)
+        qb /= np.linalg.norm(qb)
+        qd /= np.linalg.norm(qd)
+        m = S.free_body().copy(gravity=0.0, w_orient=1.0, quat_des=tuple(qd), **_NO_QUAD)
+        x = np.zeros(m.nx)
+        x[3:7] = qb
+        S_or, _ = orc.rollout(m, x, np.zeros((2, 2, 0)), H, dt)
+        rb = Rotation.from_quat([qb[1], qb[2], qb[3], qb[0]])
+        rd = Rotation.from_quat([qd[1], qd[2], qd[3], qd[0]])
+        th = (rb.inv() * rd).magnitude()
+        assert S_or == pytest.approx(th * th, rel=1e-10, abs=1e-14)
+
+
+def test_modular_cost_joint_term(orc):
+    # a torque-free pendulum without gravity spins at constant rate: q_h = q(0) + h dt w
+    m = S.pendulum().copy(gravity=0.0, w_q=1.5, q_stand=np.array([0.3]), **_NO_QUAD)
+    x = np.zeros(m.nx)
+    x[7] = -0.2
+    x[m.nq + 6] = 2.0
+    H, dt = 30, 0.01
+    kn = np.zeros((2, 2, 1))
+    S_or, _ = orc.rollout(m, x, kn, H, dt)
+    Sx = sum(1.5 * (-0.2 + h * dt * 2.0 - 0.3) ** 2 for h in range(H))
+    assert S_or == pytest.approx(Sx, rel=1e-12)
+
+
+def test_modular_cost_contact_terms(orc):
+    # a point mass resting at its equilibrium depth m g / k carries f_c = (0, 0, m g); with
+    # no friction it slides at constant speed vx with contact velocity (vx, 0, 0)
+    m0 = S.point_mass(mu=0.0)
+    g, mass, k = m0.gravity, float(m0.mass[0]), m0.contact_k
+    H, dt = 25, 0.005
+    vx = 0.7
+    x = np.zeros(m0.nx)
+    x[3] = 1.0
+    x[2] = -mass * g / k
+    x[m0.nq] = vx
+    kn = np.zeros((2, 2, 0))
+    m = m0.copy(w_cforce=0.5, f0=(0.0, 0.0, 0.0), **_NO_QUAD)
+    assert orc.rollout(m, x, kn, H, dt)[0] == pytest.approx(H * 0.5 * mass * g, rel=1e-9)
+    m = m0.copy(w_cforce=0.5, f0=(0.1, -0.2, mass * g), **_NO_QUAD)
+    assert orc.rollout(m, x, kn, H, dt)[0] == pytest.approx(H * 0.5 * 0.3, rel=1e-9)
+    m = m0.copy(w_cvel=2.0, **_NO_QUAD)
+    assert orc.rollout(m, x, kn, H, dt)[0] == pytest.approx(H * 2.0 * vx, rel=1e-9)
+    # off the ground (no gravity, at rest above the plane): no contact velocity term, and
+    # the force term is ||f0||_1 per step
+    y = x.copy()
+    y[2] = 0.5
+    m = m0.copy(gravity=0.0, w_cvel=2.0, w_cforce=0.5, f0=(0.1, -0.2, 3.0), **_NO_QUAD)
+    assert orc.rollout(m, y, kn, H, dt)[0] == pytest.approx(H * 0.5 * 3.3, rel=1e-12)
+
+
+def test_terminal_cost_ballistic(orc):
+    # terminal term on the discrete ballistic closed form z_H = z0 + H dt v0 - g dt^2 H (H + 1) / 2
+    m = S.free_body().copy(w_term=4.0, pdot_des=(0.3, 0.0, 0.0), **_NO_QUAD)
+    x = np.zeros(m.nx)
+    x[3] = 1.0
+    x[0:3] = [0.0, 0.1, 2.0]
+    v0 = np.array([0.5, 0.0, 1.2])
+    x[m.nq:m.nq + 3] = v0
+    H, dt = 30, 0.01
+    S_or, _ = orc.rollout(m, x, np.zeros((2, 2, 0)), H, dt)
+    zH = 2.0 + H * dt * 1.2 - 9.81 * dt * dt * H * (H + 1) / 2
+    Sx = 4.0 * (abs(H * dt * 0.5 - 0.3 * H * dt) + abs(zH - 2.0))
+    assert S_or == pytest.approx(Sx, rel=1e-12)
+
+
+def test_tab2_weights_and_standing_load():
+    # the weight sets and the derived per-point standing load
+    p = S.paper_walking(n=4)
+    m = p.model
+    assert (m.w_h, m.w_orient, m.w_q, m.w_cvel, m.w_cforce, m.w_term) == (1e2, 10.0, 0.0, 0.5, 5e-2, 2.5e3)
+    assert m.w_z == m.w_vx == m.w_tilt == m.w_tau == 0.0
+    assert m.f0[2] * m.nc == pytest.approx(float(np.sum(m.mass)) * m.gravity)
+    assert m.pdot_des == (0.5, 0.0, 0.0)
