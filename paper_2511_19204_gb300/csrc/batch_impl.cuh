@@ -240,9 +240,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 const int n = n0 + (threadIdx.x >> 2);
                 const int ne = min(n, last_n);
                 const float* kn = I.knots + (size_t)ne * I.E;
-                const float c = M->topology == TOPO_QUADRUPED
-                                    ? lanes_rollout<3, false>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
-                                    : lanes_rollout<6, true>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+                float c;
+                if (M->topology == TOPO_QUADRUPED)
+                    c = M->paper_cost ? lanes_rollout<3, false, true>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
+                                      : lanes_rollout<3, false, false>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+                else
+                    c = M->paper_cost ? lanes_rollout<6, true, true>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
+                                      : lanes_rollout<6, true, false>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
                 if (n <= last_n && g == 0) I.costs[n] = c;
             } else if (I.mapping == MPPI_MAP_HALFWARP) {
                 const int gl = threadIdx.x & 15;

@@ -363,7 +363,8 @@ cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knot
     switch (c->mapping) {
         case MPPI_MAP_WARP: return launch_rollout_warp_f32(a, 32, c->block, s);
         case MPPI_MAP_HALFWARP: return launch_rollout_warp_f32(a, 16, c->block, s);
-        case MPPI_MAP_CHAIN: return launch_rollout_chain_f32(a, c->model->topology, c->block, s);
+        case MPPI_MAP_CHAIN:
+            return launch_rollout_chain_f32(a, c->model->topology, c->model->host_f.paper_cost != 0, c->block, s);
         case MPPI_MAP_THREAD: return launch_rollout_thread_f32(a, c->model->topology, c->block, s);
         default: return cudaErrorInvalidValue;
     }

@@ -55,12 +55,13 @@ __device__ __forceinline__ V3<float> jpos_of(const DevModel<float>& M, int b) {
     return v3(M.jpos[0][b], M.jpos[1][b], M.jpos[2][b]);
 }
 
-// Contact forces of body b's points; with the modular cost on, `count` lanes also add
-// the points' running-cost terms to pcost (a replicated body counts on one lane).
+// Contact forces of body b's points; with the modular cost (PAPER), `count` lanes also
+// add the points' running-cost terms to pcost (a replicated body counts on one lane).
+template <bool PAPER>
 __device__ __forceinline__ void body_contacts(const DevModel<float>& M, int b, const Pose& P, V3<float>& fen,
                                               V3<float>& fef, float& pcost, bool count) {
     const int c0 = M.cfirst[b], cn = M.ccount[b];
-    const bool paper = count && M.paper_cost != 0;
+    const bool paper = PAPER && count;
     for (int c = 0; c < cn; ++c) {
         const int ci = c0 + c;
         const V3<float> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
@@ -112,7 +113,7 @@ __device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Ar
 
 // Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
 // the bias (contact forces included).
-template <bool KEEP>
+template <bool KEEP, bool PAPER>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, float q, float qd, const Pose& Pp,
                                            Pose& P, BodyMem& m, float& pcost, bool count) {
     const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
@@ -127,9 +128,9 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, floa
     m.cw = cross(P.w, sa);
     m.cv = cross(P.v, sa);
     V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-    body_contacts(M, b, P, fen, fef, pcost, count);
+    body_contacts<PAPER>(M, b, P, fen, fef, pcost, count);
     body_bias(M, b, P, fen, fef, m.x0, m.x1);
-    if (count && M.paper_cost) {
+    if (PAPER && count) {
         const float dq = q - M.q_init[b];
         pcost += M.w_q * dq * dq;
     }
@@ -237,8 +238,9 @@ __device__ __forceinline__ void cost_terms(const DevModel<float>& M, const Pose&
 
 // One sample's rollout by the 4 lanes of its group (g = lane within the group).
 // The lane plan (first body and length of each lane's chain, the branch body and which
-// lanes carry it) is in the model: lane_b0, lane_len, branch.
-template <int LMAX, bool BRANCH>
+// lanes carry it) is in the model: lane_b0, lane_len, branch. PAPER compiles the
+// modular cost of Sec. IV-A in (models with any of its weights non-zero).
+template <int LMAX, bool BRANCH, bool PAPER>
 __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, const double* __restrict__ x0,
                                             const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                             double* __restrict__ xf) {
@@ -301,16 +303,16 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         float pcost = 0.f;  // this lane's share of the modular running cost
         {
             V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-            body_contacts(M, 0, B, fen, fef, pcost, g == 0);
+            body_contacts<PAPER>(M, 0, B, fen, fef, pcost, g == 0);
             body_bias(M, 0, B, fen, fef, p0n, p0f);
         }
-        if (M.paper_cost && g == 0) pcost += base_cost(M, B.R, B.p);
+        if (PAPER && g == 0) pcost += base_cost(M, B.R, B.p);
         float tz = 0.f, tt = 0.f;
         if (cb == 0) cost_terms(M, B, tz, tt);
         BodyMem mb;
         Pose PB;
         if (on_branch) {
-            body_pass1<KEEP>(M, bb, qb, qdb, B, PB, mb, pcost, g == 2);
+            body_pass1<KEEP, PAPER>(M, bb, qb, qdb, B, PB, mb, pcost, g == 2);
             if (cb == bb) cost_terms(M, PB, tz, tt);
         }
         BodyMem mem[LMAX];
@@ -320,7 +322,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             for (int j = 0; j < LMAX; ++j) {
                 if (j < len) {
                     Pose P;
-                    body_pass1<KEEP>(M, b0 + j, q[j], qd[j], Pp, P, mem[j], pcost, true);
+                    body_pass1<KEEP, PAPER>(M, b0 + j, q[j], qd[j], Pp, P, mem[j], pcost, true);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
@@ -405,11 +407,12 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         for (int j = 0; j < LMAX; ++j) te += tau[j] * tau[j];
         if (g == 2) te += taub * taub;
         te = lsum(te);
-        if (M.paper_cost) pcost = lsum(pcost);
+        if (PAPER) pcost = lsum(pcost);
         {
             const float vx = M.fixed_base ? 0.f : (B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z);
             const float dv = vx - M.vx_des;
-            const float c = tz + M.w_vx * dv * dv + tt + M.w_tau * te + pcost;
+            float c = tz + M.w_vx * dv * dv + tt + M.w_tau * te;
+            if (PAPER) c += pcost;
             const float y = c - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
@@ -452,7 +455,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             qz = nz * inv;
         }
     }
-    if (M.paper_cost) {  // terminal cost (every lane holds the base)
+    if (PAPER) {  // terminal cost (every lane holds the base)
         const float y = terminal_cost(M, p, p_start, H, dt) - comp;
         const float t = sum + y;
         comp = (t - sum) - y;
