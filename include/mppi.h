@@ -62,6 +62,14 @@ typedef int32_t mppi_status;
 #define MPPI_WARM_BEST 0      /* Alg. 1: tau_0 <- tau_best at every control step      */
 #define MPPI_WARM_MEAN 1      /* the last weighted mean                               */
 
+/* Spline parameterisation of the joint references (Sec. III-A; the variants of the
+ * ablation of Sec. IV-D). Under the position-only variants the velocity knots are not
+ * sampled: every sample's (and the nominal's) velocity knots are set to the variant
+ * spline's node derivatives, so knots stay [knots][2][nj] and the rollout is the same. */
+#define MPPI_SPLINE_HERMITE 0    /* cubic Hermite, positions and velocities sampled     */
+#define MPPI_SPLINE_CUBIC 1      /* natural cubic spline through the position nodes     */
+#define MPPI_SPLINE_QUADRATIC 2  /* C1 quadratic spline through the nodes, from rest    */
+
 #define MPPI_MAX_BODIES 32
 #define MPPI_MAX_CONTACTS 32
 #define MPPI_MAX_CHILDREN 8
@@ -134,7 +142,7 @@ typedef struct mppi_params {
     uint32_t instance_id; /* Philox counter word 3: results depend on it, not on scheduling */
     int32_t mapping;      /* MPPI_MAP_* */
     int32_t block_size;   /* threads per block of the rollout kernel, 0 = default */
-    int32_t reserved;
+    int32_t spline;       /* MPPI_SPLINE_* (default MPPI_SPLINE_HERMITE) */
     void* stream;         /* cudaStream_t for all work of this context, NULL = own stream */
 } mppi_params;
 

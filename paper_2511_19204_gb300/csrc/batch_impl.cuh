@@ -48,7 +48,7 @@ struct BatchInst {
     DevSolve* solve;
     mppi_result* result;
     double lambda;
-    int N, H, nk, nj, E, iters, mapping, tile, ntiles, nchunks, normalize, warm_from, has_limits;
+    int N, H, nk, nj, E, iters, mapping, tile, ntiles, nchunks, normalize, warm_from, has_limits, spline;
     float dt, dtk, scale_q, scale_v;
     uint32_t inst, seed_lo, seed_hi;
     // packed host <-> device exchange
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
             np.scale_q = I.scale_q;
             np.scale_v = I.scale_v;
             np.dtk = I.dtk;
+            np.spline = I.spline;
             for (int s0 = 0; s0 < cnt; s0 += NOISE_SPB) block_sample_knots(np, n0 + s0, min(NOISE_SPB, cnt - s0), work);
             // rollouts of the tile with the instance's mapping
             const int last_n = n0 + cnt - 1;
@@ -472,6 +473,7 @@ void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double*
         I.normalize = c->normalize;
         I.warm_from = c->warm_from;
         I.has_limits = c->model->host_f.has_limits;
+        I.spline = c->spline;
         I.dt = (float)c->dt;
         I.dtk = (float)c->dtk;
         I.scale_q = (float)c->scale_q;

@@ -390,6 +390,7 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
     sa.scale_q = (float)c->scale_q;
     sa.scale_v = (float)c->scale_v;
     sa.dtk = (float)c->dtk;
+    sa.spline = c->spline;
     cudaError_t e = launch_sample_knots(sa, s);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it], s, cudaEventRecordExternal);
     if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s);
@@ -505,6 +506,8 @@ mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t k
     if (!(p->dt > 0) || !isfinite(p->dt)) return bad("dt must be positive");
     if (p->normalize != MPPI_NORM_MINMAX && p->normalize != MPPI_NORM_RAW) return bad("normalize");
     if (p->warm_from != MPPI_WARM_BEST && p->warm_from != MPPI_WARM_MEAN) return bad("warm_from");
+    if (p->spline != MPPI_SPLINE_HERMITE && p->spline != MPPI_SPLINE_CUBIC && p->spline != MPPI_SPLINE_QUADRATIC)
+        return bad("spline");
     if ((int64_t)H * (knots - 1) > 0x7fffffff) return bad("H too large");
     for (int i = 0; i < iters * knots; ++i)
         if (!(h_sigma[i] >= 0) || !isfinite(h_sigma[i])) return bad("sigma must be finite and >= 0");
@@ -534,6 +537,7 @@ mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t k
     c->scale_v = p->scale_v > 0 ? p->scale_v : 1.0 / c->dtk;
     c->normalize = p->normalize;
     c->warm_from = p->warm_from;
+    c->spline = p->spline;
     c->seed = p->seed;
     c->instance_id = p->instance_id;
     c->mapping = mapping;
@@ -749,6 +753,7 @@ mppi_status mppi_sample_knots(mppi_ctx* c, int32_t iter, uint32_t iter_counter, 
         sa.scale_q = (float)c->scale_q;
         sa.scale_v = (float)c->scale_v;
         sa.dtk = (float)c->dtk;
+        sa.spline = c->spline;
         e = launch_sample_knots(sa, c->stream);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, sizeof(float) * NE, cudaMemcpyDeviceToHost, c->stream);

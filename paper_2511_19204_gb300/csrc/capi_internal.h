@@ -26,7 +26,7 @@ struct mppi_ctx {
     int device = 0;
     int N = 0, H = 0, nk = 0, iters = 0, nj = 0, E = 0, nx = 0;
     double lambda = 0, dt = 0, dtk = 0, scale_q = 1, scale_v = 0;
-    int normalize = 0, warm_from = 0;
+    int normalize = 0, warm_from = 0, spline = 0;
     uint64_t seed = 0;
     uint32_t instance_id = 0;
     int mapping = 0, block = 0;

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs
     p.scale_q = a.scale_q;
     p.scale_v = a.scale_v;
     p.dtk = a.dtk;
+    p.spline = a.spline;
     block_sample_knots(p, blockIdx.x * NOISE_SPB, NOISE_SPB, eps);
 }
 

@@ -18,7 +18,43 @@ struct NoiseParams {
     uint32_t it, inst, seed_lo, seed_hi;
     int N, nk, nj, has_limits;
     float scale_q, scale_v, dtk;
+    int spline;              // MPPI_SPLINE_*
 };
+
+// Node derivatives of the position-only spline variants of the ablation (Sec. IV-D):
+// MPPI_SPLINE_CUBIC, the natural cubic spline through the nodes (second derivative zero
+// at both ends); MPPI_SPLINE_QUADRATIC, the C1 piecewise-quadratic spline through the
+// nodes starting from rest (d_0 = 0, d_{k+1} = 2 (q_{k+1} - q_k) / h - d_k). Each segment
+// of either spline is a polynomial of degree <= 3 fixed by its end values and end slopes,
+// so it is exactly the cubic Hermite segment (Eq. hermite_segment) with these node
+// slopes: the rollout evaluates every variant unchanged. q, d: nk values with stride st.
+__device__ __forceinline__ void spline_slopes(int spline, int nk, float h, const float* q, int st, float* d) {
+    if (spline == MPPI_SPLINE_QUADRATIC) {
+        float dk = 0.f;
+        d[0] = 0.f;
+        for (int k = 0; k + 1 < nk; ++k) {
+            dk = 2.f * (q[(k + 1) * st] - q[k * st]) / h - dk;
+            d[(k + 1) * st] = dk;
+        }
+        return;
+    }
+    // natural cubic: M_{k-1} + 4 M_k + M_{k+1} = 6 (q_{k+1} - 2 q_k + q_{k-1}) / h^2 for
+    // k = 1..nk-2, M_0 = M_{nk-1} = 0, by the Thomas algorithm
+    float cp[MAXK], rp[MAXK], M[MAXK];
+    const float s6 = 6.f / (h * h);
+    M[0] = 0.f;
+    M[nk - 1] = 0.f;
+    for (int k = 1; k + 1 < nk; ++k) {
+        const float r = s6 * (q[(k + 1) * st] - 2.f * q[k * st] + q[(k - 1) * st]);
+        const float den = (k == 1) ? 4.f : 4.f - cp[k - 1];
+        cp[k] = 1.f / den;
+        rp[k] = (k == 1) ? r / den : (r - rp[k - 1]) / den;
+    }
+    for (int k = nk - 2; k >= 1; --k) M[k] = (k == nk - 2) ? rp[k] : rp[k] - cp[k] * M[k + 1];
+    for (int k = 0; k + 1 < nk; ++k)
+        d[k * st] = (q[(k + 1) * st] - q[k * st]) / h - h * (2.f * M[k] + M[k + 1]) / 6.f;
+    d[(nk - 1) * st] = (q[(nk - 1) * st] - q[(nk - 2) * st]) / h + h * (M[nk - 2] + 2.f * M[nk - 1]) / 6.f;
+}
 
 // Samples [n0, n0 + cnt) (cnt <= NOISE_SPB) by the whole block; eps: shared [NOISE_SPB][E].
 __device__ __noinline__ void block_sample_knots(const NoiseParams& a, int n0, int cnt, float* eps) {
@@ -62,6 +98,17 @@ __device__ __noinline__ void block_sample_knots(const NoiseParams& a, int n0, in
         a.knots[(size_t)n * E + ev] = v;
     }
     __syncthreads();
+    if (a.spline != MPPI_SPLINE_HERMITE) {
+        // position-only variants: the velocity knots become the spline's node slopes
+        for (int idx = threadIdx.x; idx < cnt * a.nj; idx += blockDim.x) {
+            const int nl = idx / a.nj, j = idx - nl * a.nj;
+            const int n = n0 + nl;
+            if (n >= a.N) continue;
+            float* kn = a.knots + (size_t)n * E;
+            spline_slopes(a.spline, a.nk, a.dtk, kn + j, 2 * a.nj, kn + a.nj + j);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace mppi

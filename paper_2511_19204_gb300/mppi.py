@@ -41,6 +41,9 @@ MPPI_NORM_MINMAX = 0
 MPPI_NORM_RAW = 1
 MPPI_WARM_BEST = 0
 MPPI_WARM_MEAN = 1
+MPPI_SPLINE_HERMITE = 0
+MPPI_SPLINE_CUBIC = 1
+MPPI_SPLINE_QUADRATIC = 2
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -75,7 +78,7 @@ class mppi_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("scale_q", C.c_double), ("scale_v", C.c_double),
                 ("normalize", C.c_int32), ("warm_from", C.c_int32), ("seed", C.c_uint64),
                 ("instance_id", C.c_uint32), ("mapping", C.c_int32), ("block_size", C.c_int32),
-                ("reserved", C.c_int32), ("stream", C.c_void_p)]
+                ("spline", C.c_int32), ("stream", C.c_void_p)]
 
 
 class mppi_result(C.Structure):
@@ -257,7 +260,7 @@ class Controller:
     def __init__(self, model: Model, n: int, horizon: int, nk: int, lam: float, sigma, iters: int = 1,
                  dt: float = 0.01, scale_q: float = 1.0, scale_v: float = 0.0, normalize: int = MPPI_NORM_MINMAX,
                  warm_from: int = MPPI_WARM_BEST, seed: int = 1, instance: int = 0,
-                 mapping: int = MPPI_MAP_AUTO, block: int = 0, stream=None):
+                 mapping: int = MPPI_MAP_AUTO, block: int = 0, stream=None, spline: int = 0):
         L = load()
         self.model = model
         self.n, self.horizon, self.nk, self.iters = n, horizon, nk, iters
@@ -266,7 +269,7 @@ class Controller:
         self.nx = model.nx
         self.sigma = _f(sigma).reshape(iters, nk)
         p = mppi_params(dt=dt, scale_q=scale_q, scale_v=scale_v, normalize=normalize, warm_from=warm_from,
-                        seed=seed, instance_id=instance, mapping=mapping, block_size=block, reserved=0,
+                        seed=seed, instance_id=instance, mapping=mapping, block_size=block, spline=spline,
                         stream=C.c_void_p(stream) if stream else None)
         h = _P()
         _check(L.mppi_create(model.h, n, horizon, nk, lam, _pf(self.sigma), iters, C.byref(p), C.byref(h)))
