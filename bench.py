@@ -226,11 +226,12 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
-def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1):
+def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1, spline=0):
     """One instance's solve timed on its stream (CUDA events, L2 flushed between solves),
     plus its rollout kernel's in-graph duration."""
     stream = torch.cuda.Stream()
-    ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream, mapping=mapping)
+    ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream, mapping=mapping,
+                                        spline=spline)
     if mapping == -1:
         ctrl.autotune()
     ctrl.profile(True)
@@ -282,6 +283,8 @@ def other_configs(mppi, synth, torch, flops):
         out[f"scale_quadruped_K{n}"] = single_instance(mppi, synth, torch, flops, synth.scale_quadruped(n=n))
     out["humanoid_K2048"] = single_instance(mppi, synth, torch, flops, synth.humanoid_problem())
     out["paper_cost_walking_K8192"] = single_instance(mppi, synth, torch, flops, synth.paper_walking())
+    out["scale_quadruped_K8192_natural_cubic_spline"] = single_instance(mppi, synth, torch, flops,
+                                                                        synth.scale_quadruped(), spline=1)
     return out
 
 

@@ -52,6 +52,8 @@ class _Model(C.Structure):
 
 _lib = None
 
+SPLINE_HERMITE, SPLINE_CUBIC, SPLINE_QUADRATIC = 0, 1, 2   # Sec. IV-D variants
+
 
 def lib():
     global _lib
@@ -83,8 +85,14 @@ def lib():
         L.orc_step.restype = C.c_int
         L.orc_rollout.argtypes = [mp, _dp, _dp, C.c_int, C.c_int, C.c_double, _dp, _dp]
         L.orc_rollout.restype = C.c_double
+        L.orc_rollout_ex.argtypes = [mp, _dp, _dp, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp]
+        L.orc_rollout_ex.restype = C.c_double
         L.orc_rollout_batch.argtypes = [mp, C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_double, _dp,
                                         _dp, C.c_int]
+        L.orc_rollout_batch_ex.argtypes = [mp, C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                           _dp, _dp, C.c_int]
+        L.orc_spline_slopes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _dp]
+        L.orc_setpoints.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
         L.orc_predict_state.argtypes = [mp, _dp, _dp, C.c_int, C.c_int, C.c_int, C.c_double, _dp]
         L.orc_predict_state.restype = C.c_int
         L.orc_shift_knots.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp]
@@ -93,7 +101,7 @@ def lib():
         L.orc_average.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
         L.orc_solve.argtypes = [mp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                 C.c_int, _dp, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
-                                C.c_uint32, _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp]
+                                C.c_uint32, _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, C.c_int]
         L.orc_solve.restype = C.c_int
         _lib = L
     return _lib
@@ -266,26 +274,45 @@ def step(m, x, tau, dt) -> np.ndarray:
     return y
 
 
-def rollout(m, x0, knots, H, dt, traj=False):
+def rollout(m, x0, knots, H, dt, traj=False, spline=0):
     """Returns (cost, x_final[, traj [H+1, nx]])."""
     om = _om(m)
     kn = _d(knots)
     nk = kn.shape[0]
     xf = np.zeros(om.nx)
     tr = np.zeros((H + 1, om.nx)) if traj else None
-    S = lib().orc_rollout(om.ref, _ptr(_d(x0)), _ptr(kn), nk, H, dt, _ptr(xf), _ptr(tr))
+    S = lib().orc_rollout_ex(om.ref, _ptr(_d(x0)), _ptr(kn), nk, H, dt, spline, _ptr(xf), _ptr(tr))
     return (S, xf, tr) if traj else (S, xf)
 
 
-def rollout_batch(m, x0, knots, H, dt, finals=False, nthreads=None):
+def rollout_batch(m, x0, knots, H, dt, finals=False, nthreads=None, spline=0):
     om = _om(m)
     kn = _d(knots)
     N, nk = kn.shape[0], kn.shape[1]
     costs = np.zeros(N)
     fin = np.zeros((N, om.nx)) if finals else None
     nt = nthreads or os.cpu_count() or 1
-    lib().orc_rollout_batch(om.ref, N, _ptr(_d(x0)), _ptr(kn), nk, H, dt, _ptr(costs), _ptr(fin), nt)
+    lib().orc_rollout_batch_ex(om.ref, N, _ptr(_d(x0)), _ptr(kn), nk, H, dt, spline, _ptr(costs), _ptr(fin), nt)
     return (costs, fin) if finals else costs
+
+
+def setpoints(knots, H, dt, spline=0):
+    """The (q_ref, v_ref) [H, nu] a rollout tracks for knots [nk, 2, nu]."""
+    kn = _d(knots)
+    nk, _, nu = kn.shape
+    q = np.zeros((H, nu))
+    v = np.zeros((H, nu))
+    lib().orc_setpoints(spline, nu, nk, H, dt, _ptr(kn), _ptr(q), _ptr(v))
+    return q, v
+
+
+def spline_slopes(knots, H, dt, spline) -> np.ndarray:
+    """Sec. IV-D variants: the velocity knots replaced by the variant spline's node
+    derivatives of the position knots (knots [nk, 2, nu])."""
+    kn = _d(knots).copy()
+    nk, _, nu = kn.shape
+    lib().orc_spline_slopes(spline, nu, nk, H * dt / (nk - 1), _ptr(kn))
+    return kn
 
 
 def predict_state(m, x0, knots, H, nsteps, dt) -> np.ndarray:
@@ -330,7 +357,7 @@ def average(knots, w) -> np.ndarray:
 
 
 def solve(m, n, nk, H, iters, dt, lam, sigma, state, nominal, seed=1, iter_base=0, inst=0,
-          normalize=0, scale_q=1.0, scale_v=0.0, nthreads=None, keep=False):
+          normalize=0, scale_q=1.0, scale_v=0.0, nthreads=None, keep=False, spline=0):
     """Alg. 1 from `state` and `nominal`. Returns dict(mean, best, info[, knots, costs])."""
     om = _om(m)
     nu = om.nj
@@ -343,7 +370,7 @@ def solve(m, n, nk, H, iters, dt, lam, sigma, state, nominal, seed=1, iter_base=
     nt = nthreads or os.cpu_count() or 1
     st = lib().orc_solve(om.ref, n, nk, H, iters, dt, lam, normalize, _ptr(_d(sigma)), scale_q,
                          scale_v, seed, iter_base, inst, _ptr(_d(state)), _ptr(_d(nominal)),
-                         _ptr(mean), _ptr(best), _ptr(info), nt, _ptr(kn), _ptr(co))
+                         _ptr(mean), _ptr(best), _ptr(info), nt, _ptr(kn), _ptr(co), spline)
     out = dict(status=st, mean=mean.reshape(nk, 2, nu), best=best.reshape(nk, 2, nu),
                smin=info[0], smax=info[1], best_cost=info[2], best_index=int(info[3]),
                best_iter=int(info[4]), ess=info[5], n_finite=int(info[6]))

@@ -817,27 +817,155 @@ int orc_step(const orc_model* m, double* x, const double* tau, double dt) {
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Position-only spline variants of the ablation (Sec. IV-D, Tab. III)                    */
+/* ------------------------------------------------------------------------------------ */
+#define ORC_SPLINE_HERMITE 0
+#define ORC_SPLINE_CUBIC 1     /* natural cubic spline through the position nodes */
+#define ORC_SPLINE_QUADRATIC 2 /* C1 quadratic spline through the nodes, zero initial slope */
+
+/* Natural cubic spline on nodes y[0..K-1] with spacing h: the second derivatives M solve
+ * the full K x K system (rows 0 and K-1: M = 0; row k: M_{k-1} + 4 M_k + M_{k+1} =
+ * 6 (y_{k+1} - 2 y_k + y_{k-1}) / h^2), by dense Gaussian elimination with partial
+ * pivoting. */
+static void natural_cubic_moments(int K, double h, const double* y, double* M) {
+    double A[32][33];
+    for (int r = 0; r < K; ++r) {
+        for (int c = 0; c <= K; ++c) A[r][c] = 0;
+        if (r == 0 || r == K - 1) {
+            A[r][r] = 1;
+        } else {
+            A[r][r - 1] = 1;
+            A[r][r] = 4;
+            A[r][r + 1] = 1;
+            A[r][K] = 6.0 * (y[r + 1] - 2.0 * y[r] + y[r - 1]) / (h * h);
+        }
+    }
+    for (int c = 0; c < K; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < K; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k <= K; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+        for (int r = c + 1; r < K; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int k = c; k <= K; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    for (int r = K - 1; r >= 0; --r) {
+        double acc = A[r][K];
+        for (int k = r + 1; k < K; ++k) acc -= A[r][k] * M[k];
+        M[r] = acc / A[r][r];
+    }
+}
+
+/* C1 quadratic spline through y with zero slope at the first node: on segment k,
+ * q(s) = y_k + d_k h s + (y_{k+1} - y_k - d_k h) s^2, so d_{k+1} = q'(end) = 2 (y_{k+1} -
+ * y_k) / h - d_k. */
+static void quadratic_slopes(int K, double h, const double* y, double* d) {
+    d[0] = 0;
+    for (int k = 0; k + 1 < K; ++k) d[k + 1] = 2.0 * (y[k + 1] - y[k]) / h - d[k];
+}
+
+/* Value and time derivative of joint j's variant spline at segment k, local time s. */
+static void variant_eval(int spline, double h, const double* y, const double* aux, int k, double s,
+                         double* q, double* qd) {
+    if (spline == ORC_SPLINE_QUADRATIC) {
+        double a2 = y[k + 1] - y[k] - aux[k] * h;
+        *q = y[k] + aux[k] * h * s + a2 * s * s;
+        *qd = aux[k] + 2.0 * a2 * s / h;
+    } else { /* natural cubic in moment form */
+        double u = 1.0 - s;
+        *q = u * y[k] + s * y[k + 1] + h * h / 6.0 * ((u * u * u - u) * aux[k] + (s * s * s - s) * aux[k + 1]);
+        *qd = (y[k + 1] - y[k]) / h + h / 6.0 * (-(3.0 * u * u - 1.0) * aux[k] + (3.0 * s * s - 1.0) * aux[k + 1]);
+    }
+}
+
+/* The node derivatives of the variant spline of every joint's position knots, written
+ * into the velocity knots: knots [nk][2][nu], spacing dtk. */
+void orc_spline_slopes(int spline, int nu, int nk, double dtk, double* knots) {
+    if (spline == ORC_SPLINE_HERMITE) return;
+    double y[32], aux[32];
+    for (int j = 0; j < nu; ++j) {
+        for (int k = 0; k < nk; ++k) y[k] = knots[(k * 2 + 0) * nu + j];
+        if (spline == ORC_SPLINE_QUADRATIC) {
+            quadratic_slopes(nk, dtk, y, aux);
+            for (int k = 0; k < nk; ++k) knots[(k * 2 + 1) * nu + j] = aux[k];
+        } else {
+            natural_cubic_moments(nk, dtk, y, aux);
+            for (int k = 0; k < nk; ++k) {
+                double q, qd;
+                if (k + 1 < nk) variant_eval(spline, dtk, y, aux, k, 0.0, &q, &qd);
+                else variant_eval(spline, dtk, y, aux, nk - 2, 1.0, &q, &qd);
+                knots[(k * 2 + 1) * nu + j] = qd;
+            }
+        }
+    }
+}
+
+/* Per-joint data of the position-only variants: node positions ys [nj][nk] and the
+ * moments (cubic) or node slopes (quadratic) aux [nj][nk]. */
+static void variant_prepare(int spline, int nj, int nk, double dtk, const double* knots, double* ys,
+                            double* aux) {
+    for (int j = 0; j < nj; ++j) {
+        for (int k = 0; k < nk; ++k) ys[j * nk + k] = knots[(k * 2 + 0) * nj + j];
+        if (spline == ORC_SPLINE_QUADRATIC) quadratic_slopes(nk, dtk, ys + j * nk, aux + j * nk);
+        else natural_cubic_moments(nk, dtk, ys + j * nk, aux + j * nk);
+    }
+}
+
+/* Setpoints (q_ref, v_ref) of step h for every joint: the spline at t_h = h dt. */
+static void step_setpoints(int spline, int nj, int nk, int H, double dtk, const double* knots,
+                           const double* ys, const double* aux, int h, double* qref, double* vref) {
+    int k;
+    double s;
+    orc_segment(h, H, nk, &k, &s);
+    for (int j = 0; j < nj; ++j) {
+        if (spline == ORC_SPLINE_HERMITE)
+            orc_hermite(s, dtk, knots[(k * 2 + 0) * nj + j], knots[(k * 2 + 1) * nj + j],
+                        knots[((k + 1) * 2 + 0) * nj + j], knots[((k + 1) * 2 + 1) * nj + j], &qref[j],
+                        &vref[j]);
+        else
+            variant_eval(spline, dtk, ys + j * nk, aux + j * nk, k, s, &qref[j], &vref[j]);
+    }
+}
+
+/* The setpoints a rollout tracks: qref, vref [H][nu] for knots [nk][2][nu]. */
+void orc_setpoints(int spline, int nu, int nk, int H, double dt, const double* knots, double* qref,
+                   double* vref) {
+    const double dtk = knot_dt(nk, H, dt);
+    double* ys = (double*)malloc(sizeof(double) * (size_t)(nu > 0 ? nu : 1) * nk);
+    double* aux = (double*)malloc(sizeof(double) * (size_t)(nu > 0 ? nu : 1) * nk);
+    if (spline != ORC_SPLINE_HERMITE) variant_prepare(spline, nu, nk, dtk, knots, ys, aux);
+    for (int h = 0; h < H; ++h)
+        step_setpoints(spline, nu, nk, H, dtk, knots, ys, aux, h, qref + (size_t)h * nu, vref + (size_t)h * nu);
+    free(ys);
+    free(aux);
+}
+
 /* Rollout of one sample (Alg. 1 "simulate"): H steps from x0 tracking the Hermite
  * setpoints of knots [nk][2][nu]; returns S = sum_h c(x_h, u_h) + c_T(x_H) (Sec. IV-A).
  * x_final [nx] and traj [(H+1)][nx] are optional. */
-double orc_rollout(const orc_model* m, const double* x0, const double* knots, int nk, int H,
-                   double dt, double* x_final, double* traj) {
+double orc_rollout_ex(const orc_model* m, const double* x0, const double* knots, int nk, int H,
+                      double dt, int spline, double* x_final, double* traj) {
     const int nj = m->nb - 1, nq = 7 + nj, nx = nq + 6 + nj;
     double x[7 + ORC_MAXB + 6 + ORC_MAXB];
     double qref[ORC_MAXB], vref[ORC_MAXB], tau[ORC_MAXB], acc[ORC_MAXNV];
     orc_kin* K = (orc_kin*)malloc(sizeof(orc_kin));
     memcpy(x, x0, sizeof(double) * nx);
     const double dtk = knot_dt(nk, H, dt);
+    /* position-only variants: per-joint node positions and their spline data */
+    double* ys = (double*)malloc(sizeof(double) * (size_t)(nj > 0 ? nj : 1) * nk);
+    double* aux = (double*)malloc(sizeof(double) * (size_t)(nj > 0 ? nj : 1) * nk);
+    if (spline != ORC_SPLINE_HERMITE) variant_prepare(spline, nj, nk, dtk, knots, ys, aux);
     double S = 0;
     if (traj) memcpy(traj, x, sizeof(double) * nx);
     for (int h = 0; h < H; ++h) {
-        int k;
-        double s;
-        orc_segment(h, H, nk, &k, &s);
-        for (int j = 0; j < nj; ++j)
-            orc_hermite(s, dtk, knots[(k * 2 + 0) * nj + j], knots[(k * 2 + 1) * nj + j],
-                        knots[((k + 1) * 2 + 0) * nj + j], knots[((k + 1) * 2 + 1) * nj + j],
-                        &qref[j], &vref[j]);
+        step_setpoints(spline, nj, nk, H, dtk, knots, ys, aux, h, qref, vref);
         pd_torque(m, x, qref, vref, tau);
         if (aba(m, x, tau, K, acc) != 0) {
             S = NAN;
@@ -850,7 +978,14 @@ double orc_rollout(const orc_model* m, const double* x0, const double* knots, in
     if (H > 0 && isfinite(S)) S += terminal_cost(m, x0, x, H, dt);
     if (x_final) memcpy(x_final, x, sizeof(double) * nx);
     free(K);
+    free(ys);
+    free(aux);
     return S;
+}
+
+double orc_rollout(const orc_model* m, const double* x0, const double* knots, int nk, int H,
+                   double dt, double* x_final, double* traj) {
+    return orc_rollout_ex(m, x0, knots, nk, H, dt, ORC_SPLINE_HERMITE, x_final, traj);
 }
 
 /* Sec. III-E state prediction: simulate the first `nsteps` steps of the spline defined by
@@ -949,7 +1084,7 @@ typedef struct {
     const orc_model* m;
     const double* x0;
     const double* knots;
-    int N, nk, H, E, nx, tid, nthreads;
+    int N, nk, H, E, nx, tid, nthreads, spline;
     double dt;
     double* costs;
     double* finals;
@@ -958,27 +1093,32 @@ typedef struct {
 static void* rollout_worker(void* arg) {
     rollout_job* j = (rollout_job*)arg;
     for (int n = j->tid; n < j->N; n += j->nthreads)
-        j->costs[n] = orc_rollout(j->m, j->x0, j->knots + (size_t)n * j->E, j->nk, j->H, j->dt,
-                                  j->finals ? j->finals + (size_t)n * j->nx : NULL, NULL);
+        j->costs[n] = orc_rollout_ex(j->m, j->x0, j->knots + (size_t)n * j->E, j->nk, j->H, j->dt, j->spline,
+                                     j->finals ? j->finals + (size_t)n * j->nx : NULL, NULL);
     return NULL;
 }
 
 /* costs[N] (and finals[N][nx] if non-null) for knots [N][nk][2][nu]. */
-void orc_rollout_batch(const orc_model* m, int N, const double* x0, const double* knots, int nk,
-                       int H, double dt, double* costs, double* finals, int nthreads) {
+void orc_rollout_batch_ex(const orc_model* m, int N, const double* x0, const double* knots, int nk,
+                          int H, double dt, int spline, double* costs, double* finals, int nthreads) {
     const int nj = m->nb - 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     pthread_t th[256];
     rollout_job jobs[256];
     for (int t = 0; t < nthreads; ++t) {
-        jobs[t] = (rollout_job){m, x0, knots, N, nk, H, nk * 2 * nj, 7 + nj + 6 + nj, t, nthreads,
+        jobs[t] = (rollout_job){m, x0, knots, N, nk, H, nk * 2 * nj, 7 + nj + 6 + nj, t, nthreads, spline,
                                 dt, costs, finals};
         if (nthreads > 1) pthread_create(&th[t], NULL, rollout_worker, &jobs[t]);
     }
     if (nthreads == 1) rollout_worker(&jobs[0]);
     else
         for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+void orc_rollout_batch(const orc_model* m, int N, const double* x0, const double* knots, int nk,
+                       int H, double dt, double* costs, double* finals, int nthreads) {
+    orc_rollout_batch_ex(m, N, x0, knots, nk, H, dt, ORC_SPLINE_HERMITE, costs, finals, nthreads);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -988,12 +1128,14 @@ void orc_rollout_batch(const orc_model* m, int N, const double* x0, const double
  * costs_out (optional) [iters][N].
  * info[0..7] = S_min, S_max (last iteration), best cost over the solve, best sample
  * index, iteration of the best, ESS (last iteration), n_finite (last), status.
- * Iteration i draws noise with counter iter_base + i. Returns status (0 or -3). */
+ * Iteration i draws noise with counter iter_base + i. spline: ORC_SPLINE_* (the position-
+ * only variants track their own spline of the sampled position knots).
+ * Returns status (0 or -3). */
 int orc_solve(const orc_model* m, int N, int nk, int H, int iters, double dt, double lambda,
               int normalize, const double* sigma, double scale_q, double scale_v, uint64_t seed,
               uint32_t iter_base, uint32_t inst, const double* x0, const double* nominal_in,
               double* mean_out, double* best_out, double* info, int nthreads, double* knots_out,
-              double* costs_out) {
+              double* costs_out, int spline) {
     const int nj = m->nb - 1, E = nk * 2 * nj;
     double* knots = (double*)malloc(sizeof(double) * (size_t)N * E);
     double* costs = (double*)malloc(sizeof(double) * N);
@@ -1011,7 +1153,10 @@ int orc_solve(const orc_model* m, int N, int nk, int H, int iters, double dt, do
         orc_sample_knots(nj, nk, N, H, dt, nominal, sigma + (size_t)it * nk, scale_q, scale_v, seed,
                          iter_base + (uint32_t)it, inst, has_limits ? m->q_min : NULL,
                          has_limits ? m->q_max : NULL, knots);
-        orc_rollout_batch(m, N, x0, knots, nk, H, dt, costs, NULL, nthreads);
+        /* position-only variants: the velocity knots carry the variant spline's node slopes */
+        for (int n = 0; n < N && spline != ORC_SPLINE_HERMITE; ++n)
+            orc_spline_slopes(spline, nj, nk, knot_dt(nk, H, dt), knots + (size_t)n * E);
+        orc_rollout_batch_ex(m, N, x0, knots, nk, H, dt, spline, costs, NULL, nthreads);
         if (knots_out) memcpy(knots_out + (size_t)it * N * E, knots, sizeof(double) * (size_t)N * E);
         if (costs_out) memcpy(costs_out + (size_t)it * N, costs, sizeof(double) * N);
         int st = orc_weights(N, costs, lambda, normalize, w, winfo);

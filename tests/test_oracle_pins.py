@@ -794,3 +794,110 @@ def test_tab2_weights_and_standing_load():
     assert m.w_z == m.w_vx == m.w_tilt == m.w_tau == 0.0
     assert m.f0[2] * m.nc == pytest.approx(float(np.sum(m.mass)) * m.gravity)
     assert m.pdot_des == (0.5, 0.0, 0.0)
+
+
+# ------------------------------------------------------------------------------------
+# Spline variants of the ablation (Sec. IV-D): setpoints and node slopes
+# ------------------------------------------------------------------------------------
+def _variant_knots(rng, nk, nu):
+    kn = np.zeros((nk, 2, nu))
+    kn[:, 0] = rng.normal(size=(nk, nu))
+    kn[:, 1] = rng.normal(size=(nk, nu))     # ignored by the position-only variants
+    return kn
+
+
+@pytest.mark.parametrize("nk", [2, 3, 6, 16])
+def test_natural_cubic_variant_against_scipy(orc, nk):
+    from scipy.interpolate import CubicSpline
+    rng = np.random.default_rng(nk)
+    H, dt, nu = 200, 0.005, 3
+    kn = _variant_knots(rng, nk, nu)
+    tk = np.arange(nk) * H * dt / (nk - 1)
+    q, v = orc.setpoints(kn, H, dt, orc.SPLINE_CUBIC)
+    sl = orc.spline_slopes(kn, H, dt, orc.SPLINE_CUBIC)
+    th = np.arange(H) * dt
+    for j in range(nu):
+        cs = CubicSpline(tk, kn[:, 0, j], bc_type="natural")
+        np.testing.assert_allclose(q[:, j], cs(th), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(v[:, j], cs(th, 1), rtol=1e-11, atol=1e-11)
+        np.testing.assert_allclose(sl[:, 1, j], cs(tk, 1), rtol=1e-11, atol=1e-11)
+    np.testing.assert_array_equal(sl[:, 0], kn[:, 0])
+
+
+def test_hermite_setpoints_against_scipy(orc):
+    from scipy.interpolate import CubicHermiteSpline
+    rng = np.random.default_rng(3)
+    H, dt, nk, nu = 200, 0.005, 6, 2
+    kn = _variant_knots(rng, nk, nu)
+    tk = np.arange(nk) * H * dt / (nk - 1)
+    q, v = orc.setpoints(kn, H, dt, orc.SPLINE_HERMITE)
+    th = np.arange(H) * dt
+    for j in range(nu):
+        hs = CubicHermiteSpline(tk, kn[:, 0, j], kn[:, 1, j])
+        np.testing.assert_allclose(q[:, j], hs(th), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(v[:, j], hs(th, 1), rtol=1e-11, atol=1e-11)
+
+
+def test_quadratic_variant(orc):
+    rng = np.random.default_rng(5)
+    H, dt, nk, nu = 200, 0.005, 6, 2
+    T = H * dt
+    tk = np.arange(nk) * T / (nk - 1)
+    th = np.arange(H) * dt
+    # reproduces a quadratic that starts at rest: q(t) = a + c t^2
+    a, c = rng.normal(size=nu), rng.normal(size=nu)
+    kn = np.zeros((nk, 2, nu))
+    kn[:, 0] = a + np.outer(tk ** 2, c)
+    q, v = orc.setpoints(kn, H, dt, orc.SPLINE_QUADRATIC)
+    np.testing.assert_allclose(q, a + np.outer(th ** 2, c), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(v, np.outer(2 * th, c), rtol=1e-11, atol=1e-11)
+    # on random nodes: interpolates, is C1 at the nodes, piecewise quadratic, starts at rest
+    kn = _variant_knots(rng, nk, nu)
+    q, v = orc.setpoints(kn, H, dt, orc.SPLINE_QUADRATIC)
+    step = H // (nk - 1)
+    np.testing.assert_allclose(q[::step][:nk - 1], kn[:nk - 1, 0], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(v[0], 0.0, atol=1e-12)
+    sl = orc.spline_slopes(kn, H, dt, orc.SPLINE_QUADRATIC)
+    for k in range(nk - 1):
+        seg = slice(k * step, (k + 1) * step)
+        for j in range(nu):
+            # the exact quadratic through the segment's end values with its start slope
+            t0, h = tk[k], T / (nk - 1)
+            s = (th[seg] - t0) / h
+            a2 = kn[k + 1, 0, j] - kn[k, 0, j] - sl[k, 1, j] * h
+            np.testing.assert_allclose(q[seg, j], kn[k, 0, j] + sl[k, 1, j] * h * s + a2 * s ** 2, rtol=1e-12,
+                                       atol=1e-12)
+            # C1: the segment's end slope is the next node's slope
+            assert sl[k, 1, j] + 2 * a2 / h == pytest.approx(sl[k + 1, 1, j], rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("spline", [1, 2])
+def test_variant_equals_hermite_with_its_node_slopes(orc, spline):
+    # each segment of either variant is a polynomial of degree <= 3 with the variant's end
+    # values and slopes, so the Hermite interpolant of those nodes is the same curve
+    rng = np.random.default_rng(10 + spline)
+    H, dt, nk, nu = 200, 0.005, 6, 3
+    kn = _variant_knots(rng, nk, nu)
+    qv, vv = orc.setpoints(kn, H, dt, spline)
+    qh, vh = orc.setpoints(orc.spline_slopes(kn, H, dt, spline), H, dt, orc.SPLINE_HERMITE)
+    np.testing.assert_allclose(qh, qv, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(vh, vv, rtol=1e-11, atol=1e-11)
+
+
+def test_variant_solve_ignores_sampled_velocities(orc):
+    # under a position-only variant the sampled velocity knots do not matter: the rollout
+    # costs equal those of the same knots with zeroed velocity knots
+    p = S.scale_quadruped(n=16)
+    p.horizon = 60
+    kn = orc.sample_knots(p.model.nj, p.nk, p.n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=4)
+    kz = kn.copy()
+    kz[:, :, 1, :] = 0.0
+    for spline in (1, 2):
+        a = orc.rollout_batch(p.model, p.state, kn, p.horizon, p.dt, spline=spline)
+        b = orc.rollout_batch(p.model, p.state, kz, p.horizon, p.dt, spline=spline)
+        np.testing.assert_array_equal(a, b)
+    r = orc.solve(p.model, p.n, p.nk, p.horizon, 1, p.dt, p.lam, p.sigma[:1], p.state, p.nominal, seed=2,
+                  spline=2, keep=True)
+    for n in range(p.n):
+        np.testing.assert_allclose(r["knots"][0, n], orc.spline_slopes(r["knots"][0, n], p.horizon, p.dt, 2),
+                                   rtol=0, atol=0)
