@@ -408,6 +408,12 @@ mppi_status mppi_ctx_rollout_ms(mppi_ctx* ctx, float* h_ms);
  * [6] mapping, [7] block_size. */
 mppi_status mppi_ctx_info(const mppi_ctx* ctx, int32_t* h_out8);
 
+/* What the library derived from a model: h_out4 = (topology: 0 generic tree, 1 base + 4
+ * chains of <= 3, 2 base + 2 chains + a branch body with 2 chains; axis plan of the
+ * lanes-per-chain quadruped: 0 any axes, 1 every chain turns about +x, +y, +y; 1 when the
+ * modular cost of Sec. IV-A is on, else 0; the number of bodies). */
+mppi_status mppi_model_info(const mppi_model* model, int32_t* h_out4);
+
 /* Device bytes one solve of a context occupies (its buffers). */
 size_t mppi_ctx_device_bytes(const mppi_ctx* ctx);
 

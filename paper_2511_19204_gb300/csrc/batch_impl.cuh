@@ -242,12 +242,22 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 const int ne = min(n, last_n);
                 const float* kn = I.knots + (size_t)ne * I.E;
                 float c;
-                if (M->topology == TOPO_QUADRUPED)
-                    c = M->paper_cost ? lanes_rollout<3, false, true>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
-                                      : lanes_rollout<3, false, false>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
-                else
-                    c = M->paper_cost ? lanes_rollout<6, true, true>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
-                                      : lanes_rollout<6, true, false>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+                if (M->topology == TOPO_QUADRUPED) {
+                    if (M->axis_plan == AXP_XYY)
+                        c = M->paper_cost
+                                ? lanes_rollout<3, false, true, AXP_XYY>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
+                                : lanes_rollout<3, false, false, AXP_XYY>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk,
+                                                                          nullptr);
+                    else
+                        c = M->paper_cost ? lanes_rollout<3, false, true, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk, I.dt,
+                                                                                      I.dtk, nullptr)
+                                          : lanes_rollout<3, false, false, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk,
+                                                                                       I.dt, I.dtk, nullptr);
+                } else {
+                    c = M->paper_cost
+                            ? lanes_rollout<6, true, true, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
+                            : lanes_rollout<6, true, false, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+                }
                 if (n <= last_n && g == 0) I.costs[n] = c;
             } else if (I.mapping == MPPI_MAP_HALFWARP) {
                 const int gl = threadIdx.x & 15;

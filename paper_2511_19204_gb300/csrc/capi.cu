@@ -48,7 +48,14 @@ struct LanePlan {
     int topology = TOPO_GENERIC;
     int b0[4] = {0, 0, 0, 0}, len[4] = {0, 0, 0, 0};
     int branch = 0;
+    int axis_plan = AXP_GENERIC;
 };
+
+static bool axis_is(const mppi_model_desc& d, int b, int k) {
+    for (int i = 0; i < 3; ++i)
+        if (d.axis[3 * b + i] != (i == k ? 1.0 : 0.0)) return false;
+    return true;
+}
 
 static bool is_chain(const mppi_model_desc& d, int first, int len, int parent) {
     if (len < 1 || first + len > d.nb || d.parent[first] != parent) return false;
@@ -67,10 +74,14 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
         for (int l = 0; l < 4 && ok; ++l) ok = is_chain(d, 1 + l * L, L, 0);
         if (ok) {
             P.topology = TOPO_QUADRUPED;
+            bool xyy = L == 3;
             for (int l = 0; l < 4; ++l) {
                 P.b0[l] = 1 + l * L;
                 P.len[l] = L;
+                if (xyy)
+                    xyy = axis_is(d, P.b0[l], 0) && axis_is(d, P.b0[l] + 1, 1) && axis_is(d, P.b0[l] + 2, 1);
             }
+            if (xyy) P.axis_plan = AXP_XYY;
             return P;
         }
     }
@@ -152,6 +163,7 @@ static void fill_model(const mppi_model_desc& d, const std::vector<int>& level, 
         if (isfinite(d.q_min[j]) || isfinite(d.q_max[j])) lim = 1;
     M.has_limits = lim;
     M.topology = plan.topology;
+    M.axis_plan = plan.axis_plan;
     for (int l = 0; l < 4; ++l) {
         M.lane_b0[l] = plan.b0[l];
         M.lane_len[l] = plan.len[l];
@@ -364,7 +376,8 @@ cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knot
         case MPPI_MAP_WARP: return launch_rollout_warp_f32(a, 32, c->block, s);
         case MPPI_MAP_HALFWARP: return launch_rollout_warp_f32(a, 16, c->block, s);
         case MPPI_MAP_CHAIN:
-            return launch_rollout_chain_f32(a, c->model->topology, c->model->host_f.paper_cost != 0, c->block, s);
+            return launch_rollout_chain_f32(a, c->model->topology, c->model->host_f.paper_cost != 0,
+                                            c->model->host_f.axis_plan, c->block, s);
         case MPPI_MAP_THREAD: return launch_rollout_thread_f32(a, c->model->topology, c->block, s);
         default: return cudaErrorInvalidValue;
     }
@@ -1006,6 +1019,15 @@ mppi_status mppi_ctx_info(const mppi_ctx* c, int32_t* o) {
     o[5] = c->nx;
     o[6] = c->mapping;
     o[7] = c->block;
+    return MPPI_OK;
+}
+
+mppi_status mppi_model_info(const mppi_model* m, int32_t* o) {
+    if (!m || !o) return MPPI_ERR_INVALID_ARG;
+    o[0] = m->topology;
+    o[1] = m->host_f.axis_plan;
+    o[2] = m->host_f.paper_cost;
+    o[3] = m->nb;
     return MPPI_OK;
 }
 

@@ -4,7 +4,7 @@
 
 namespace mppi {
 
-template <int LMAX, bool BRANCH, bool PAPER>
+template <int LMAX, bool BRANCH, bool PAPER, int AXP>
 __global__ void __launch_bounds__(256) rollout_lanes_kernel(RolloutArgs<float> a) {
     __shared__ __align__(16) DevModel<float> Ms;
     __shared__ uint64_t mbar;
@@ -20,13 +20,13 @@ __global__ void __launch_bounds__(256) rollout_lanes_kernel(RolloutArgs<float> a
     const int E = a.nk * 2 * nj;
     const int nx = 13 + 2 * nj;
     double* xf = (active && a.finals) ? a.finals + (size_t)n * nx : nullptr;
-    const float c = lanes_rollout<LMAX, BRANCH, PAPER>(Ms, g, a.x0, a.knots + (size_t)ne * E, a.H, a.nk, a.dt, a.dtk, xf);
+    const float c = lanes_rollout<LMAX, BRANCH, PAPER, AXP>(Ms, g, a.x0, a.knots + (size_t)ne * E, a.H, a.nk, a.dt, a.dtk, xf);
     if (active && g == 0) a.costs[n] = c;
 }
 
 bool chain_mapping_supported(int topology) { return topology == TOPO_QUADRUPED || topology == TOPO_HUMANOID; }
 
-cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int block,
+cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
                                      cudaStream_t s) {
     if (!chain_mapping_supported(topology)) return cudaErrorNotSupported;
     if (block <= 0) block = 128;
@@ -35,11 +35,17 @@ cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, 
     const int grid = (a.N + spb - 1) / spb;
     if (grid == 0) return cudaSuccess;
     if (topology == TOPO_QUADRUPED) {
-        if (paper) rollout_lanes_kernel<3, false, true><<<grid, block, 0, s>>>(a);
-        else rollout_lanes_kernel<3, false, false><<<grid, block, 0, s>>>(a);
+        const bool xyy = axis_plan == AXP_XYY;
+        if (paper) {
+            if (xyy) rollout_lanes_kernel<3, false, true, AXP_XYY><<<grid, block, 0, s>>>(a);
+            else rollout_lanes_kernel<3, false, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
+        } else {
+            if (xyy) rollout_lanes_kernel<3, false, false, AXP_XYY><<<grid, block, 0, s>>>(a);
+            else rollout_lanes_kernel<3, false, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
+        }
     } else {
-        if (paper) rollout_lanes_kernel<6, true, true><<<grid, block, 0, s>>>(a);
-        else rollout_lanes_kernel<6, true, false><<<grid, block, 0, s>>>(a);
+        if (paper) rollout_lanes_kernel<6, true, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
+        else rollout_lanes_kernel<6, true, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -76,13 +76,21 @@ struct alignas(16) DevModel {
     T f0[4];
     T pdot_des[4];
     T Rdes[12];                         // R_des row-major (9 used)
-    int32_t paper_cost, pad3[3];
+    int32_t paper_cost;
+    int32_t axis_plan;                  // lanes-per-chain axis plan (AXP_*)
+    int32_t pad3[2];
 };
 
 // Tree shapes with a lanes-per-chain kernel.
 constexpr int TOPO_GENERIC = 0;
 constexpr int TOPO_QUADRUPED = 1;   // 4 chains of <= 3 bodies off the base
 constexpr int TOPO_HUMANOID = 2;    // 2 chains of <= 6 off the base + a branch body with 2 chains of <= 6
+
+// Axis plans of the lanes-per-chain quadruped: AXP_GENERIC, any unit axes; AXP_XYY, every
+// chain's joints turn about +x, +y, +y (hip abduction, hip and knee flexion of the usual
+// quadruped layout), which the passes exploit at compile time.
+constexpr int AXP_GENERIC = 0;
+constexpr int AXP_XYY = 1;
 
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64-bit
@@ -301,12 +309,9 @@ __device__ __forceinline__ void full_rotate(const M3<T>& R, const T* B, T* out) 
 // E = Rj^T (Rj = joint rotation child->parent) and r = joint position in the parent:
 // rotate (Rj M Rj^T), then shift the reference point by r:
 //   C' unchanged, B' += r^ C', A' += r^ B'^T - B'' r^  (B'' the shifted B).
+// The reference-point shift of the congruence for already rotated blocks A, B, C.
 template <typename T>
-__device__ __forceinline__ void art_to_parent(const Art<T>& Ia, const M3<T>& Rj, V3<T> r, Art<T>& out) {
-    T A[6], B[9], C[6];
-    sym_rotate(Rj, Ia.A, A);
-    full_rotate(Rj, Ia.B, B);
-    sym_rotate(Rj, Ia.C, C);
+__device__ __forceinline__ void art_shift(const T* A, const T* B, const T* C, V3<T> r, Art<T>& out) {
     // B2 = B + r^ C : column j of r^ C = r x C[:, j]
     const V3<T> c0 = v3(C[0], C[3], C[4]), c1 = v3(C[3], C[1], C[5]), c2 = v3(C[4], C[5], C[2]);
     const V3<T> x0 = cross(r, c0), x1 = cross(r, c1), x2 = cross(r, c2);
@@ -331,6 +336,15 @@ __device__ __forceinline__ void art_to_parent(const Art<T>& Ia, const M3<T>& Rj,
     for (int k = 0; k < 9; ++k) out.B[k] = B2[k];
 #pragma unroll
     for (int k = 0; k < 6; ++k) out.C[k] = C[k];
+}
+
+template <typename T>
+__device__ __forceinline__ void art_to_parent(const Art<T>& Ia, const M3<T>& Rj, V3<T> r, Art<T>& out) {
+    T A[6], B[9], C[6];
+    sym_rotate(Rj, Ia.A, A);
+    full_rotate(Rj, Ia.B, B);
+    sym_rotate(Rj, Ia.C, C);
+    art_shift(A, B, C, r, out);
 }
 
 // Solve the 6x6 SPD system [[A, B], [B^T, C]] x = b by Cholesky (in registers).

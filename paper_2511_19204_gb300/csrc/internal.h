@@ -64,7 +64,7 @@ cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int bloc
 cudaError_t launch_rollout_warp_f64(const RolloutArgs<double>& a, int G, int block, cudaStream_t s);
 cudaError_t launch_rollout_thread_f32(const RolloutArgs<float>& a, int topology, int block, cudaStream_t s);
 bool thread_mapping_supported(int topology);
-cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int block,
+cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
                                      cudaStream_t s);
 bool chain_mapping_supported(int topology);
 // state after the first nsteps steps of knots [nk][2][nj] from x0 (one warp, Sec. III-E)

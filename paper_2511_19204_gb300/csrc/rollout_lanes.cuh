@@ -12,12 +12,29 @@
 // articulated-body algorithm, Sec. III-A Hermite setpoints, Sec. III-C PD tracking,
 // semi-implicit Euler, Kahan-summed running cost.
 #pragma once
+#include <type_traits>
+
 #include "internal.h"
 #include "rollout_warp.cuh"
 
 namespace mppi {
 
 constexpr int LANES = 4;
+
+// Axis code of chain position J under an axis plan (AXP_* in common.cuh).
+template <int AXP, int J>
+__host__ __device__ constexpr int chain_axis() {
+    return AXP == AXP_XYY ? (J == 0 ? 0 : 1) : -1;
+}
+
+// f(std::integral_constant<int, J>) for J = B .. E - 1, unrolled at compile time.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
 
 __device__ __forceinline__ float lsum(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 1, LANES);
@@ -37,10 +54,148 @@ struct BodyMem {
     float uu;
 };
 
-template <bool KEEP>
-__device__ __forceinline__ M3<float> joint_rot(const DevModel<float>& M, int b, const BodyMem& m) {
-    if (KEEP) return m.R;
-    return axis_rotation(v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]), m.s, m.c);
+// ------------------------------------------------------------------------------------
+// Joint rotations Rj (child -> parent). AX = 0, 1, 2: about the coordinate axis x, y, z
+// (+1 direction), kept as (sin, cos), so applying one touches two components and costs 4
+// multiplies instead of 9. AX = -1: any unit axis, the full matrix. The axis-vector
+// operations below are written out per AX (a select, not a multiply by 0 or 1, which
+// IEEE arithmetic would not fold away).
+// ------------------------------------------------------------------------------------
+template <int AX>
+struct JRot {
+    float s, c;
+};
+template <>
+struct JRot<-1> {
+    M3<float> R;
+};
+
+template <int AX>
+__device__ __forceinline__ V3<float> jrot(const JRot<AX>& J, V3<float> v) {  // Rj v
+    if constexpr (AX == 0) return v3(v.x, J.c * v.y - J.s * v.z, J.s * v.y + J.c * v.z);
+    else if constexpr (AX == 1) return v3(J.c * v.x + J.s * v.z, v.y, J.c * v.z - J.s * v.x);
+    else if constexpr (AX == 2) return v3(J.c * v.x - J.s * v.y, J.s * v.x + J.c * v.y, v.z);
+    else return mul(J.R, v);
+}
+template <int AX>
+__device__ __forceinline__ V3<float> jrotT(const JRot<AX>& J, V3<float> v) {  // Rj^T v
+    if constexpr (AX == 0) return v3(v.x, J.c * v.y + J.s * v.z, J.c * v.z - J.s * v.y);
+    else if constexpr (AX == 1) return v3(J.c * v.x - J.s * v.z, v.y, J.s * v.x + J.c * v.z);
+    else if constexpr (AX == 2) return v3(J.c * v.x + J.s * v.y, J.c * v.y - J.s * v.x, v.z);
+    else return mulT(J.R, v);
+}
+// R Rj: row i of the product is Rj^T applied to row i of R
+template <int AX>
+__device__ __forceinline__ M3<float> jcompose(const M3<float>& R, const JRot<AX>& J) {
+    if constexpr (AX < 0) {
+        return mul(R, J.R);
+    } else {
+        M3<float> o;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const V3<float> w = jrotT(J, v3(R.m[3 * i], R.m[3 * i + 1], R.m[3 * i + 2]));
+            o.m[3 * i] = w.x;
+            o.m[3 * i + 1] = w.y;
+            o.m[3 * i + 2] = w.z;
+        }
+        return o;
+    }
+}
+// Rj S Rj^T: N = S Rj^T has rows Rj (row i of S); the result has columns Rj (column j of N)
+template <int AX>
+__device__ __forceinline__ void jsym_rotate(const JRot<AX>& J, const float* S, float* out) {
+    if constexpr (AX < 0) {
+        sym_rotate(J.R, S, out);
+    } else {
+        const V3<float> r0 = jrot(J, v3(S[0], S[3], S[4])), r1 = jrot(J, v3(S[3], S[1], S[5])),
+                        r2 = jrot(J, v3(S[4], S[5], S[2]));
+        const V3<float> c0 = jrot(J, v3(r0.x, r1.x, r2.x)), c1 = jrot(J, v3(r0.y, r1.y, r2.y)),
+                        c2 = jrot(J, v3(r0.z, r1.z, r2.z));
+        out[0] = c0.x;
+        out[1] = c1.y;
+        out[2] = c2.z;
+        out[3] = c1.x;
+        out[4] = c2.x;
+        out[5] = c2.y;
+    }
+}
+template <int AX>
+__device__ __forceinline__ void jfull_rotate(const JRot<AX>& J, const float* B, float* out) {
+    if constexpr (AX < 0) {
+        full_rotate(J.R, B, out);
+    } else {
+        const V3<float> r0 = jrot(J, v3(B[0], B[1], B[2])), r1 = jrot(J, v3(B[3], B[4], B[5])),
+                        r2 = jrot(J, v3(B[6], B[7], B[8]));
+        const V3<float> c0 = jrot(J, v3(r0.x, r1.x, r2.x)), c1 = jrot(J, v3(r0.y, r1.y, r2.y)),
+                        c2 = jrot(J, v3(r0.z, r1.z, r2.z));
+        out[0] = c0.x;
+        out[1] = c1.x;
+        out[2] = c2.x;
+        out[3] = c0.y;
+        out[4] = c1.y;
+        out[5] = c2.y;
+        out[6] = c0.z;
+        out[7] = c1.z;
+        out[8] = c2.z;
+    }
+}
+template <int AX>
+__device__ __forceinline__ void jart_to_parent(const Art<float>& Ia, const JRot<AX>& J, V3<float> r, Art<float>& out) {
+    float A[6], B[9], C[6];
+    jsym_rotate(J, Ia.A, A);
+    jfull_rotate(J, Ia.B, B);
+    jsym_rotate(J, Ia.C, C);
+    art_shift(A, B, C, r, out);
+}
+
+// Axis-vector operations with a = the joint axis (component AX for a coordinate axis).
+template <int AX>
+__device__ __forceinline__ V3<float> add_ax(const DevModel<float>& M, int b, V3<float> v, float x) {  // v + x a
+    if constexpr (AX == 0) return v3(v.x + x, v.y, v.z);
+    else if constexpr (AX == 1) return v3(v.x, v.y + x, v.z);
+    else if constexpr (AX == 2) return v3(v.x, v.y, v.z + x);
+    else return v + x * v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
+}
+template <int AX>
+__device__ __forceinline__ V3<float> cross_ax(const DevModel<float>& M, int b, V3<float> w, float x) {  // w x (x a)
+    if constexpr (AX == 0) return v3(0.f, w.z * x, -(w.y * x));
+    else if constexpr (AX == 1) return v3(-(w.z * x), 0.f, w.x * x);
+    else if constexpr (AX == 2) return v3(w.y * x, -(w.x * x), 0.f);
+    else return cross(w, x * v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]));
+}
+template <int AX>
+__device__ __forceinline__ float dot_ax(const DevModel<float>& M, int b, V3<float> v) {  // a . v
+    if constexpr (AX == 0) return v.x;
+    else if constexpr (AX == 1) return v.y;
+    else if constexpr (AX == 2) return v.z;
+    else return dot(v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]), v);
+}
+template <int AX>
+__device__ __forceinline__ V3<float> symcol_ax(const DevModel<float>& M, int b, const float* S) {  // S a
+    if constexpr (AX == 0) return v3(S[0], S[3], S[4]);
+    else if constexpr (AX == 1) return v3(S[3], S[1], S[5]);
+    else if constexpr (AX == 2) return v3(S[4], S[5], S[2]);
+    else return sym_mul(S, v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]));
+}
+template <int AX>
+__device__ __forceinline__ V3<float> btcol_ax(const DevModel<float>& M, int b, const float* B) {  // B^T a
+    if constexpr (AX >= 0) {
+        return v3(B[3 * AX], B[3 * AX + 1], B[3 * AX + 2]);
+    } else {
+        const V3<float> a = v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
+        return v3(B[0] * a.x + B[3] * a.y + B[6] * a.z, B[1] * a.x + B[4] * a.y + B[7] * a.z,
+                  B[2] * a.x + B[5] * a.y + B[8] * a.z);
+    }
+}
+
+template <bool KEEP, int AX>
+__device__ __forceinline__ JRot<AX> joint_rot(const DevModel<float>& M, int b, const BodyMem& m) {
+    if constexpr (AX >= 0) {
+        return JRot<AX>{m.s, m.c};
+    } else {
+        if (KEEP) return JRot<-1>{m.R};
+        return JRot<-1>{axis_rotation(v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]), m.s, m.c)};
+    }
 }
 
 struct Pose {
@@ -113,20 +268,25 @@ __device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Ar
 
 // Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
 // the bias (contact forces included).
-template <bool KEEP, bool PAPER>
+template <bool KEEP, bool PAPER, int AX>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, float q, float qd, const Pose& Pp,
                                            Pose& P, BodyMem& m, float& pcost, bool count) {
-    const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
+    const V3<float> r = jpos_of(M, b);
     sincosf(q, &m.s, &m.c);
-    const M3<float> Rj = axis_rotation(a, m.s, m.c);
-    if (KEEP) m.R = Rj;
-    P.R = mul(Pp.R, Rj);
+    JRot<AX> J;
+    if constexpr (AX >= 0) {
+        J.s = m.s;
+        J.c = m.c;
+    } else {
+        J.R = axis_rotation(axis_of(M, b), m.s, m.c);
+        if (KEEP) m.R = J.R;
+    }
+    P.R = jcompose(Pp.R, J);
     P.p = Pp.p + mul(Pp.R, r);
-    P.w = mulT(Rj, Pp.w) + qd * a;
-    P.v = mulT(Rj, Pp.v - cross(r, Pp.w));
-    const V3<float> sa = qd * a;
-    m.cw = cross(P.w, sa);
-    m.cv = cross(P.v, sa);
+    P.w = add_ax<AX>(M, b, jrotT(J, Pp.w), qd);
+    P.v = jrotT(J, Pp.v - cross(r, Pp.w));
+    m.cw = cross_ax<AX>(M, b, P.w, qd);
+    m.cv = cross_ax<AX>(M, b, P.v, qd);
     V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
     body_contacts<PAPER>(M, b, P, fen, fef, pcost, count);
     body_bias(M, b, P, fen, fef, m.x0, m.x1);
@@ -138,10 +298,10 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, floa
 
 // Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
 // then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D.
-template <bool KEEP>
+template <bool KEEP, int AX>
 __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, float tau, BodyMem& m, bool has_carry,
                                            Art<float>& carry, V3<float>& cpn, V3<float>& cpf) {
-    const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
+    const V3<float> r = jpos_of(M, b);
     Art<float> IA;
     body_inertia(M, b, IA);
     V3<float> pAn = m.x0, pAf = m.x1;
@@ -155,11 +315,10 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
         pAn = pAn + cpn;
         pAf = pAf + cpf;
     }
-    const V3<float> ua = sym_mul(IA.A, a);
-    const V3<float> ul = v3(IA.B[0] * a.x + IA.B[3] * a.y + IA.B[6] * a.z, IA.B[1] * a.x + IA.B[4] * a.y + IA.B[7] * a.z,
-                            IA.B[2] * a.x + IA.B[5] * a.y + IA.B[8] * a.z);
-    const float invD = 1.f / (dot(a, ua) + M.armature[b]);
-    const float u = tau - dot(a, pAn);
+    const V3<float> ua = symcol_ax<AX>(M, b, IA.A);
+    const V3<float> ul = btcol_ax<AX>(M, b, IA.B);
+    const float invD = 1.f / (dot_ax<AX>(M, b, ua) + M.armature[b]);
+    const float u = tau - dot_ax<AX>(M, b, pAn);
     const float U[6] = {ua.x, ua.y, ua.z, ul.x, ul.y, ul.z};
     Art<float> Ia;
     Ia.A[0] = IA.A[0] - U[0] * U[0] * invD;
@@ -182,10 +341,10 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
     const M3<float>& Bm = *reinterpret_cast<const M3<float>*>(Ia.B);
     const V3<float> pan = pAn + sym_mul(Ia.A, m.cw) + mul(Bm, m.cv) + ud * ua;
     const V3<float> paf = pAf + mulT(Bm, m.cw) + sym_mul(Ia.C, m.cv) + ud * ul;
-    const M3<float> Rj = joint_rot<KEEP>(M, b, m);
-    art_to_parent(Ia, Rj, r, carry);
-    cpf = mul(Rj, paf);
-    cpn = mul(Rj, pan) + cross(r, cpf);
+    const JRot<AX> J = joint_rot<KEEP, AX>(M, b, m);
+    jart_to_parent(Ia, J, r, carry);
+    cpf = jrot(J, paf);
+    cpn = jrot(J, pan) + cross(r, cpf);
     m.x0 = invD * ua;
     m.x1 = invD * ul;
     m.uu = ud;
@@ -193,15 +352,15 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
 
 // Pass 3 of body b: from the parent's acceleration (apw, apv, offset by gravity) to its
 // own, and its joint acceleration.
-template <bool KEEP>
+template <bool KEEP, int AX>
 __device__ __forceinline__ float body_pass3(const DevModel<float>& M, int b, const BodyMem& m, V3<float>& apw,
                                             V3<float>& apv) {
-    const V3<float> a = axis_of(M, b), r = jpos_of(M, b);
-    const M3<float> Rj = joint_rot<KEEP>(M, b, m);
-    const V3<float> a1w = mulT(Rj, apw) + m.cw;
-    const V3<float> a1v = mulT(Rj, apv - cross(r, apw)) + m.cv;
+    const V3<float> r = jpos_of(M, b);
+    const JRot<AX> J = joint_rot<KEEP, AX>(M, b, m);
+    const V3<float> a1w = jrotT(J, apw) + m.cw;
+    const V3<float> a1v = jrotT(J, apv - cross(r, apw)) + m.cv;
     const float qdd = m.uu - dot(m.x0, a1w) - dot(m.x1, a1v);
-    apw = a1w + qdd * a;
+    apw = add_ax<AX>(M, b, a1w, qdd);
     apv = a1v;
     return qdd;
 }
@@ -240,7 +399,7 @@ __device__ __forceinline__ void cost_terms(const DevModel<float>& M, const Pose&
 // The lane plan (first body and length of each lane's chain, the branch body and which
 // lanes carry it) is in the model: lane_b0, lane_len, branch. PAPER compiles the
 // modular cost of Sec. IV-A in (models with any of its weights non-zero).
-template <int LMAX, bool BRANCH, bool PAPER>
+template <int LMAX, bool BRANCH, bool PAPER, int AXP>
 __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, const double* __restrict__ x0,
                                             const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                             double* __restrict__ xf) {
@@ -312,21 +471,21 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         BodyMem mb;
         Pose PB;
         if (on_branch) {
-            body_pass1<KEEP, PAPER>(M, bb, qb, qdb, B, PB, mb, pcost, g == 2);
+            body_pass1<KEEP, PAPER, -1>(M, bb, qb, qdb, B, PB, mb, pcost, g == 2);
             if (cb == bb) cost_terms(M, PB, tz, tt);
         }
         BodyMem mem[LMAX];
         {
             Pose Pp = on_branch ? PB : B;
-#pragma unroll
-            for (int j = 0; j < LMAX; ++j) {
+            static_for<0, LMAX>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
                 if (j < len) {
                     Pose P;
-                    body_pass1<KEEP, PAPER>(M, b0 + j, q[j], qd[j], Pp, P, mem[j], pcost, true);
+                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>()>(M, b0 + j, q[j], qd[j], Pp, P, mem[j], pcost, true);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
-            }
+            });
         }
         if (cb != 0) {
             tz = __shfl_sync(0xffffffffu, tz, cowner, LANES);
@@ -335,9 +494,10 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         // ---- pass 2 ----
         Art<float> carry;
         V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
-#pragma unroll
-        for (int j = LMAX - 1; j >= 0; --j)
-            if (j < len) body_pass2<KEEP>(M, b0 + j, tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+        static_for<0, LMAX>([&](auto ic) {
+            constexpr int j = LMAX - 1 - decltype(ic)::value;
+            if (j < len) body_pass2<KEEP, chain_axis<AXP, j>()>(M, b0 + j, tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+        });
         if (BRANCH) {
             // arms meet at the branch body: own + partner (lanes 2 <-> 3), identical on both
             Art<float> sumc;
@@ -357,7 +517,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 carry = sumc;
                 cpn = sn;
                 cpf = sf;
-                body_pass2<KEEP>(M, bb, taub, mb, true, carry, cpn, cpf);
+                body_pass2<KEEP, -1>(M, bb, taub, mb, true, carry, cpn, cpf);
                 if (g == 3) {  // lane 2 alone hands the branch to the base
 #pragma unroll
                     for (int t = 0; t < 6; ++t) carry.A[t] = 0.f;
@@ -397,9 +557,11 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         float qdd[LMAX], qddb = 0.f;
         {
             V3<float> apw = aw, apv = av;
-            if (on_branch) qddb = body_pass3<KEEP>(M, bb, mb, apw, apv);
-#pragma unroll
-            for (int j = 0; j < LMAX; ++j) qdd[j] = j < len ? body_pass3<KEEP>(M, b0 + j, mem[j], apw, apv) : 0.f;
+            if (on_branch) qddb = body_pass3<KEEP, -1>(M, bb, mb, apw, apv);
+            static_for<0, LMAX>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                qdd[j] = j < len ? body_pass3<KEEP, chain_axis<AXP, j>()>(M, b0 + j, mem[j], apw, apv) : 0.f;
+            });
         }
         // ---- running cost on the pre-step state ----
         float te = 0.f;

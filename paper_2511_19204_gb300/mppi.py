@@ -112,6 +112,7 @@ SIGNATURES = [
     ("mppi_predict_state_device", C.c_int32, [_P, _P, C.c_int32, _P]),
     ("mppi_shift_warm_start", C.c_int32, [_P, C.c_int32]),
     ("mppi_get_warm_start", C.c_int32, [_P, _fp]),
+    ("mppi_model_info", C.c_int32, [_P, _ip]),
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
     ("mppi_average", C.c_int32, [C.c_int32, C.c_int32, _fp, _dp, _dp]),
@@ -232,6 +233,11 @@ class Model:
         h = _P()
         _check(L.mppi_model_create(C.byref(d), C.byref(h)))
         self.h = h
+
+    def info(self):
+        o = np.zeros(4, np.int32)
+        _check(load().mppi_model_info(self.h, o.ctypes.data_as(_ip)))
+        return dict(topology=int(o[0]), axis_plan=int(o[1]), paper_cost=int(o[2]), nb=int(o[3]))
 
     def forward_dynamics(self, states, tau, fp64=False):
         L = load()

@@ -216,6 +216,34 @@ def test_mappings_agree(M, orc, robot, n, block):
         assert np.max(np.abs(out[mapping] - out[0]) / np.abs(out[0])) < 1e-4
 
 
+@pytest.mark.parametrize("tilt", [0.0, 0.05, -1.0])
+def test_chain_axis_plans(M, orc, tilt):
+    # the quadruped's x, y, y joint axes select the axis-specialised chain kernel; a tilted
+    # or reversed hip axis the generic one; both agree with the oracle
+    p = S.scale_quadruped(n=256)
+    p.horizon = 120
+    m = p.model
+    if tilt:
+        axis = m.axis.copy()
+        for b in range(1, m.nb, 3):
+            a = np.array([1.0, 0.0, tilt]) if tilt > 0 else np.array([-1.0, 0.0, 0.0])
+            axis[b] = a / np.linalg.norm(a)
+        m = m.copy(axis=axis)
+        p.model = m
+    mod = M.Model(m)
+    assert mod.info()["topology"] == 1
+    assert mod.info()["axis_plan"] == (1 if tilt == 0.0 else 0)
+    kn = orc.sample_knots(m.nj, p.nk, p.n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed).astype(np.float32)
+    c = M.Controller.from_problem(mod, p, mapping=M.MPPI_MAP_CHAIN)
+    got, fin = c.rollout_explicit(p.state, kn, finals=True)
+    ref_c, ref_f = orc.rollout_batch(m, p.state, kn.astype(np.float64), p.horizon, p.dt, finals=True)
+    err = np.abs(got - ref_c) / np.abs(ref_c)
+    err_f = np.max(np.abs(fin - ref_f), axis=1) / np.max(np.abs(ref_f), axis=1)
+    print(f"axis plan {mod.info()['axis_plan']}: cost rel. error median {np.median(err):.2e} max {err.max():.2e}, "
+          f"final state max {err_f.max():.2e}")
+    assert err.max() < 1e-4 and err_f.max() < 1e-4
+
+
 # ------------------------------------------------------------------------------------
 # Weights and average
 # ------------------------------------------------------------------------------------
