@@ -262,9 +262,9 @@ def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1,
     ms.sort()
     host.sort()
     units = p.n * p.horizon * p.iters
-    fl = flops.flops_per_step(p.model) * p.n * p.horizon
-    achieved = fl / (statistics.mean(roll) * 1e-3) / 1e12
     info = ctrl.info()
+    fl_step = flops.flops_per_step(p.model, mapping_chain=info["mapping"] == mppi.MPPI_MAP_CHAIN)
+    achieved = fl_step * p.n * p.horizon / (statistics.mean(roll) * 1e-3) / 1e12
     return {"samples": p.n, "horizon": p.horizon, "knots": p.nk, "iters": p.iters, "dt": p.dt,
             "mapping": mppi.MAPPING_NAMES.get(info["mapping"]), "block": info["block"],
             "rollout_steps_per_s": units / (statistics.mean(ms) * 1e-3),
@@ -273,7 +273,7 @@ def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1,
             "host_latency_ms": {"p50": host[len(host) // 2], "p99": host[min(len(host) - 1, int(0.99 * len(host)))]},
             "rollout_launch_ms": statistics.mean(roll),
             "rollout_tflops": achieved, "rollout_frac_fp32_peak": achieved / flops.fp32_peak_tflops(),
-            "flops_per_step_sample": flops.flops_per_step(p.model)}
+            "flops_per_step_sample": fl_step}
 
 
 def other_configs(mppi, synth, torch, flops):
@@ -564,7 +564,7 @@ def run_ours(args, rank, world, local):
     if rank != 0:
         return 0
     # roofline of the dominant kernel (the rollout): FP32 ALU bound
-    fl_step = flops.flops_per_step(p.model)
+    fl_step = flops.flops_per_step(p.model, mapping_chain=info["mapping"] == mppi.MPPI_MAP_CHAIN)
     roll_ms = statistics.mean(rollout_ms)
     achieved = fl_step * p.n * p.horizon / (roll_ms * 1e-3) / 1e12
     peak = flops.fp32_peak_tflops()

@@ -29,6 +29,12 @@ With the modular cost of Sec. IV-A on (any of its weights non-zero), in addition
   per base: height term 3, R^T R_des 54, rotation angle (vee 3, norm 6, trace 3,
   arctangent 1), theta^2 term 2, reduction 3                                      75
   (the terminal term, ~15 flops per rollout, is not counted per step)
+Quadrupeds whose chains turn about +x, +y, +y run the axis-specialised kernel, which
+applies joint rotations to two components. Per joint body it evaluates 666 instead of
+961: joint rotation 1 (sincos only), pass 1 61 (composition 18, origin 18, angular
+velocity 7, linear velocity 18), velocity product 4, pass 2 390 (U, D, u 3, congruence
+210 with 108 for the rotations, force transform 24, the rest as above), pass 3 44
+(transform 30, joint acceleration 13, update 1); the other items as above.
 """
 from __future__ import annotations
 
@@ -39,13 +45,34 @@ MOD_JOINT = 4
 MOD_CONTACT = 5 + 8 + 4
 MOD_BASE = 3 + 54 + 3 + 6 + 3 + 1 + 2 + 3
 MOD_WEIGHTS = ("w_h", "w_orient", "w_q", "w_cvel", "w_cforce", "w_term")
+PER_JOINT_XYY = 55 + 1 + 61 + 4 + 78 + (3 + 63 + 66 + 24 + 210 + 24) + 27 + 44 + 4 + 2
 
 
-def flops_per_step(model, contacts_active=None) -> int:
+def axis_plan_xyy(model) -> bool:
+    """True when the model runs the axis-specialised chain kernel: a floating base with 4
+    chains of 3 bodies whose joint axes are exactly +x, +y, +y."""
+    import numpy as np
+    if model.fixed_base or model.nb != 13:
+        return False
+    ex, ey = np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])
+    for leg in range(4):
+        b0 = 1 + 3 * leg
+        if list(model.parent[b0:b0 + 3]) != [0, b0, b0 + 1]:
+            return False
+        if not (np.array_equal(model.axis[b0], ex) and np.array_equal(model.axis[b0 + 1], ey)
+                and np.array_equal(model.axis[b0 + 2], ey)):
+            return False
+    return True
+
+
+def flops_per_step(model, contacts_active=None, mapping_chain=True) -> int:
     """Flops of one step of one sample. ``contacts_active`` defaults to every contact
-    point (the standing / walking regime); pass a number for another regime."""
+    point (the standing / walking regime); pass a number for another regime.
+    ``mapping_chain``: the rollout runs the lanes-per-chain kernel (which specialises the
+    axes of x, y, y quadrupeds)."""
     nc = model.nc if contacts_active is None else contacts_active
-    f = PER_JOINT * model.nj + PER_CONTACT * nc + PER_BASE
+    per_joint = PER_JOINT_XYY if mapping_chain and axis_plan_xyy(model) else PER_JOINT
+    f = per_joint * model.nj + PER_CONTACT * nc + PER_BASE
     if any(getattr(model, w, 0.0) for w in MOD_WEIGHTS):
         f += MOD_JOINT * model.nj + MOD_CONTACT * model.nc + MOD_BASE
     return f
