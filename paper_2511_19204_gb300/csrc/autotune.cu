@@ -67,6 +67,7 @@ mppi_status autotune_ctx(mppi_ctx* c, int reps, TuneVal* out) {
     sa.scale_q = (float)c->scale_q;
     sa.scale_v = (float)c->scale_v;
     sa.dtk = (float)c->dtk;
+    sa.spline = c->spline;
     cudaError_t e = launch_sample_knots(sa, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "autotune: sample knots");
     cudaEvent_t e0, e1;
@@ -78,35 +79,40 @@ mppi_status autotune_ctx(mppi_ctx* c, int reps, TuneVal* out) {
     const int saved_m = c->mapping, saved_b = c->block;
     float best = 1e30f;
     int bm = saved_m, bb = saved_b;
-    for (int mi = 0; mi < 4; ++mi) {
-        for (int bi = 0; bi < 4; ++bi) {
-            out->ms[mi * 4 + bi] = -1.f;
-            const int m = kMappings[mi], b = kBlocks[bi];
-            if (!mapping_valid(c->model, m, b)) continue;
-            c->mapping = m;
-            c->block = b;
-            // one untimed launch, then reps timed ones
-            e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, c->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r)
+    for (int k = 0; k < 16; ++k) out->ms[k] = -1.f;
+    // two rounds over every candidate, keeping each one's faster round: the first round
+    // also absorbs the clock ramp of a GPU that was idle before the call
+    for (int round = 0; round < 2; ++round) {
+        for (int mi = 0; mi < 4; ++mi) {
+            for (int bi = 0; bi < 4; ++bi) {
+                const int m = kMappings[mi], b = kBlocks[bi];
+                if (!mapping_valid(c->model, m, b)) continue;
+                c->mapping = m;
+                c->block = b;
+                // one untimed launch, then reps timed ones
                 e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, c->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                c->mapping = saved_m;
-                c->block = saved_b;
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return cuda_fail(c, e, "autotune: timed rollout");
-            }
-            ms /= (float)reps;
-            out->ms[mi * 4 + bi] = ms;
-            if (ms < best) {
-                best = ms;
-                bm = m;
-                bb = b;
+                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                    e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    c->mapping = saved_m;
+                    c->block = saved_b;
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return cuda_fail(c, e, "autotune: timed rollout");
+                }
+                ms /= (float)reps;
+                float& slot = out->ms[mi * 4 + bi];
+                if (slot < 0.f || ms < slot) slot = ms;
+                if (ms < best) {
+                    best = ms;
+                    bm = m;
+                    bb = b;
+                }
             }
         }
     }

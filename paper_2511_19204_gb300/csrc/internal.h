@@ -43,7 +43,7 @@ struct SampleArgs {
     uint32_t seed_lo, seed_hi;
     int N, nk, nj, has_limits;
     float scale_q, scale_v, dtk;
-    int spline;              // MPPI_SPLINE_*
+    int spline = 0;          // MPPI_SPLINE_*
 };
 
 template <typename T>

@@ -18,7 +18,7 @@ struct NoiseParams {
     uint32_t it, inst, seed_lo, seed_hi;
     int N, nk, nj, has_limits;
     float scale_q, scale_v, dtk;
-    int spline;              // MPPI_SPLINE_*
+    int spline = 0;          // MPPI_SPLINE_*
 };
 
 // Node derivatives of the position-only spline variants of the ablation (Sec. IV-D):

@@ -148,53 +148,79 @@ __device__ __forceinline__ void jart_to_parent(const Art<float>& Ia, const JRot<
     art_shift(A, B, C, r, out);
 }
 
+// A body's constants, loaded once per rollout into registers (the step loop would
+// otherwise re-read them from shared memory every step).
+struct BodyConst {
+    V3<float> a, r, mc;   // joint axis, joint position in the parent, mass * com
+    float Ao[6];          // rotational inertia about the body origin
+    float m, arm, kp, kd, tmax, qinit;
+    int b;
+};
+
+__device__ __forceinline__ BodyConst load_body(const DevModel<float>& M, int b) {
+    BodyConst C;
+    C.a = v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
+    C.r = v3(M.jpos[0][b], M.jpos[1][b], M.jpos[2][b]);
+    C.mc = v3(M.mc[0][b], M.mc[1][b], M.mc[2][b]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) C.Ao[t] = M.Ao[t][b];
+    C.m = M.mass[b];
+    C.arm = M.armature[b];
+    C.kp = M.kp[b];
+    C.kd = M.kd[b];
+    C.tmax = M.tau_max[b];
+    C.qinit = M.q_init[b];
+    C.b = b;
+    return C;
+}
+
 // Axis-vector operations with a = the joint axis (component AX for a coordinate axis).
 template <int AX>
-__device__ __forceinline__ V3<float> add_ax(const DevModel<float>& M, int b, V3<float> v, float x) {  // v + x a
+__device__ __forceinline__ V3<float> add_ax(const BodyConst& C, V3<float> v, float x) {  // v + x a
     if constexpr (AX == 0) return v3(v.x + x, v.y, v.z);
     else if constexpr (AX == 1) return v3(v.x, v.y + x, v.z);
     else if constexpr (AX == 2) return v3(v.x, v.y, v.z + x);
-    else return v + x * v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
+    else return v + x * C.a;
 }
 template <int AX>
-__device__ __forceinline__ V3<float> cross_ax(const DevModel<float>& M, int b, V3<float> w, float x) {  // w x (x a)
+__device__ __forceinline__ V3<float> cross_ax(const BodyConst& C, V3<float> w, float x) {  // w x (x a)
     if constexpr (AX == 0) return v3(0.f, w.z * x, -(w.y * x));
     else if constexpr (AX == 1) return v3(-(w.z * x), 0.f, w.x * x);
     else if constexpr (AX == 2) return v3(w.y * x, -(w.x * x), 0.f);
-    else return cross(w, x * v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]));
+    else return cross(w, x * C.a);
 }
 template <int AX>
-__device__ __forceinline__ float dot_ax(const DevModel<float>& M, int b, V3<float> v) {  // a . v
+__device__ __forceinline__ float dot_ax(const BodyConst& C, V3<float> v) {  // a . v
     if constexpr (AX == 0) return v.x;
     else if constexpr (AX == 1) return v.y;
     else if constexpr (AX == 2) return v.z;
-    else return dot(v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]), v);
+    else return dot(C.a, v);
 }
 template <int AX>
-__device__ __forceinline__ V3<float> symcol_ax(const DevModel<float>& M, int b, const float* S) {  // S a
+__device__ __forceinline__ V3<float> symcol_ax(const BodyConst& C, const float* S) {  // S a
     if constexpr (AX == 0) return v3(S[0], S[3], S[4]);
     else if constexpr (AX == 1) return v3(S[3], S[1], S[5]);
     else if constexpr (AX == 2) return v3(S[4], S[5], S[2]);
-    else return sym_mul(S, v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]));
+    else return sym_mul(S, C.a);
 }
 template <int AX>
-__device__ __forceinline__ V3<float> btcol_ax(const DevModel<float>& M, int b, const float* B) {  // B^T a
+__device__ __forceinline__ V3<float> btcol_ax(const BodyConst& C, const float* B) {  // B^T a
     if constexpr (AX >= 0) {
         return v3(B[3 * AX], B[3 * AX + 1], B[3 * AX + 2]);
     } else {
-        const V3<float> a = v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
+        const V3<float> a = C.a;
         return v3(B[0] * a.x + B[3] * a.y + B[6] * a.z, B[1] * a.x + B[4] * a.y + B[7] * a.z,
                   B[2] * a.x + B[5] * a.y + B[8] * a.z);
     }
 }
 
 template <bool KEEP, int AX>
-__device__ __forceinline__ JRot<AX> joint_rot(const DevModel<float>& M, int b, const BodyMem& m) {
+__device__ __forceinline__ JRot<AX> joint_rot(const BodyConst& C, const BodyMem& m) {
     if constexpr (AX >= 0) {
         return JRot<AX>{m.s, m.c};
     } else {
         if (KEEP) return JRot<-1>{m.R};
-        return JRot<-1>{axis_rotation(v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]), m.s, m.c)};
+        return JRot<-1>{axis_rotation(C.a, m.s, m.c)};
     }
 }
 
@@ -203,12 +229,6 @@ struct Pose {
     V3<float> p, w, v;
 };
 
-__device__ __forceinline__ V3<float> axis_of(const DevModel<float>& M, int b) {
-    return v3(M.axis[0][b], M.axis[1][b], M.axis[2][b]);
-}
-__device__ __forceinline__ V3<float> jpos_of(const DevModel<float>& M, int b) {
-    return v3(M.jpos[0][b], M.jpos[1][b], M.jpos[2][b]);
-}
 
 // Contact forces of body b's points; with the modular cost (PAPER), `count` lanes also
 // add the points' running-cost terms to pcost (a replicated body counts on one lane).
@@ -238,21 +258,21 @@ __device__ __forceinline__ void body_contacts(const DevModel<float>& M, int b, c
 }
 
 // v x* (I v) - f_ext for body b (see the warp kernel for the exact-cancellation form).
-__device__ __forceinline__ void body_bias(const DevModel<float>& M, int b, const Pose& P, V3<float> fen, V3<float> fef,
+__device__ __forceinline__ void body_bias(const BodyConst& C, const Pose& P, V3<float> fen, V3<float> fef,
                                           V3<float>& pn, V3<float>& pf) {
-    const float Ao[6] = {M.Ao[0][b], M.Ao[1][b], M.Ao[2][b], M.Ao[3][b], M.Ao[4][b], M.Ao[5][b]};
-    const V3<float> mc = v3(M.mc[0][b], M.mc[1][b], M.mc[2][b]);
+    const float* Ao = C.Ao;
+    const V3<float> mc = C.mc;
     const V3<float> mcw = cross(mc, P.w);
     const V3<float> hn = sym_mul(Ao, P.w) + cross(mc, P.v);
-    const V3<float> hf = M.mass[b] * P.v - mcw;
+    const V3<float> hf = C.m * P.v - mcw;
     pn = cross(P.w, hn) - cross(P.v, mcw) - fen;
     pf = cross(P.w, hf) - fef;
 }
 
-__device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Art<float>& IA) {
-    const V3<float> mc = v3(M.mc[0][b], M.mc[1][b], M.mc[2][b]);
+__device__ __forceinline__ void body_inertia(const BodyConst& C, Art<float>& IA) {
+    const V3<float> mc = C.mc;
 #pragma unroll
-    for (int t = 0; t < 6; ++t) IA.A[t] = M.Ao[t][b];
+    for (int t = 0; t < 6; ++t) IA.A[t] = C.Ao[t];
     IA.B[0] = 0.f;
     IA.B[1] = -mc.z;
     IA.B[2] = mc.y;
@@ -262,36 +282,36 @@ __device__ __forceinline__ void body_inertia(const DevModel<float>& M, int b, Ar
     IA.B[6] = -mc.y;
     IA.B[7] = mc.x;
     IA.B[8] = 0.f;
-    IA.C[0] = IA.C[1] = IA.C[2] = M.mass[b];
+    IA.C[0] = IA.C[1] = IA.C[2] = C.m;
     IA.C[3] = IA.C[4] = IA.C[5] = 0.f;
 }
 
 // Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
 // the bias (contact forces included).
 template <bool KEEP, bool PAPER, int AX>
-__device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, float q, float qd, const Pose& Pp,
-                                           Pose& P, BodyMem& m, float& pcost, bool count) {
-    const V3<float> r = jpos_of(M, b);
+__device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyConst& C, float q, float qd,
+                                           const Pose& Pp, Pose& P, BodyMem& m, float& pcost, bool count) {
+    const V3<float> r = C.r;
     sincosf(q, &m.s, &m.c);
     JRot<AX> J;
     if constexpr (AX >= 0) {
         J.s = m.s;
         J.c = m.c;
     } else {
-        J.R = axis_rotation(axis_of(M, b), m.s, m.c);
+        J.R = axis_rotation(C.a, m.s, m.c);
         if (KEEP) m.R = J.R;
     }
     P.R = jcompose(Pp.R, J);
     P.p = Pp.p + mul(Pp.R, r);
-    P.w = add_ax<AX>(M, b, jrotT(J, Pp.w), qd);
+    P.w = add_ax<AX>(C, jrotT(J, Pp.w), qd);
     P.v = jrotT(J, Pp.v - cross(r, Pp.w));
-    m.cw = cross_ax<AX>(M, b, P.w, qd);
-    m.cv = cross_ax<AX>(M, b, P.v, qd);
+    m.cw = cross_ax<AX>(C, P.w, qd);
+    m.cv = cross_ax<AX>(C, P.v, qd);
     V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-    body_contacts<PAPER>(M, b, P, fen, fef, pcost, count);
-    body_bias(M, b, P, fen, fef, m.x0, m.x1);
+    body_contacts<PAPER>(M, C.b, P, fen, fef, pcost, count);
+    body_bias(C, P, fen, fef, m.x0, m.x1);
     if (PAPER && count) {
-        const float dq = q - M.q_init[b];
+        const float dq = q - C.qinit;
         pcost += M.w_q * dq * dq;
     }
 }
@@ -299,11 +319,11 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, int b, floa
 // Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
 // then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D.
 template <bool KEEP, int AX>
-__device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, float tau, BodyMem& m, bool has_carry,
+__device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMem& m, bool has_carry,
                                            Art<float>& carry, V3<float>& cpn, V3<float>& cpf) {
-    const V3<float> r = jpos_of(M, b);
+    const V3<float> r = C.r;
     Art<float> IA;
-    body_inertia(M, b, IA);
+    body_inertia(C, IA);
     V3<float> pAn = m.x0, pAf = m.x1;
     if (has_carry) {
 #pragma unroll
@@ -315,10 +335,10 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
         pAn = pAn + cpn;
         pAf = pAf + cpf;
     }
-    const V3<float> ua = symcol_ax<AX>(M, b, IA.A);
-    const V3<float> ul = btcol_ax<AX>(M, b, IA.B);
-    const float invD = 1.f / (dot_ax<AX>(M, b, ua) + M.armature[b]);
-    const float u = tau - dot_ax<AX>(M, b, pAn);
+    const V3<float> ua = symcol_ax<AX>(C, IA.A);
+    const V3<float> ul = btcol_ax<AX>(C, IA.B);
+    const float invD = 1.f / (dot_ax<AX>(C, ua) + C.arm);
+    const float u = tau - dot_ax<AX>(C, pAn);
     const float U[6] = {ua.x, ua.y, ua.z, ul.x, ul.y, ul.z};
     Art<float> Ia;
     Ia.A[0] = IA.A[0] - U[0] * U[0] * invD;
@@ -341,7 +361,7 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
     const M3<float>& Bm = *reinterpret_cast<const M3<float>*>(Ia.B);
     const V3<float> pan = pAn + sym_mul(Ia.A, m.cw) + mul(Bm, m.cv) + ud * ua;
     const V3<float> paf = pAf + mulT(Bm, m.cw) + sym_mul(Ia.C, m.cv) + ud * ul;
-    const JRot<AX> J = joint_rot<KEEP, AX>(M, b, m);
+    const JRot<AX> J = joint_rot<KEEP, AX>(C, m);
     jart_to_parent(Ia, J, r, carry);
     cpf = jrot(J, paf);
     cpn = jrot(J, pan) + cross(r, cpf);
@@ -353,14 +373,13 @@ __device__ __forceinline__ void body_pass2(const DevModel<float>& M, int b, floa
 // Pass 3 of body b: from the parent's acceleration (apw, apv, offset by gravity) to its
 // own, and its joint acceleration.
 template <bool KEEP, int AX>
-__device__ __forceinline__ float body_pass3(const DevModel<float>& M, int b, const BodyMem& m, V3<float>& apw,
-                                            V3<float>& apv) {
-    const V3<float> r = jpos_of(M, b);
-    const JRot<AX> J = joint_rot<KEEP, AX>(M, b, m);
+__device__ __forceinline__ float body_pass3(const BodyConst& C, const BodyMem& m, V3<float>& apw, V3<float>& apv) {
+    const V3<float> r = C.r;
+    const JRot<AX> J = joint_rot<KEEP, AX>(C, m);
     const V3<float> a1w = jrotT(J, apw) + m.cw;
     const V3<float> a1v = jrotT(J, apv - cross(r, apw)) + m.cv;
     const float qdd = m.uu - dot(m.x0, a1w) - dot(m.x1, a1v);
-    apw = add_ax<AX>(M, b, a1w, qdd);
+    apw = add_ax<AX>(C, a1w, qdd);
     apv = a1v;
     return qdd;
 }
@@ -375,7 +394,7 @@ __device__ __forceinline__ SegKnots seg_knots(const float* __restrict__ knots, i
                     knots[((k + 1) * 2 + 1) * nj + j]};
 }
 
-__device__ __forceinline__ float hermite_pd(const DevModel<float>& M, int b, const SegKnots& K, float s, float dtk,
+__device__ __forceinline__ float hermite_pd(const BodyConst& C, const SegKnots& K, float s, float dtk,
                                             float inv_dtk, float q, float qd) {
     const float q0 = K.q0, v0 = K.v0, q1 = K.q1, v1 = K.v1;
     const float s2 = s * s, s3 = s2 * s;
@@ -385,7 +404,7 @@ __device__ __forceinline__ float hermite_pd(const DevModel<float>& M, int b, con
     const float d01 = -6.f * s2 + 6.f * s, d11 = 3.f * s2 - 2.f * s;
     const float qref = h00 * q0 + h10 * dtk * v0 + h01 * q1 + h11 * dtk * v1;
     const float vref = (d00 * q0 + d01 * q1) * inv_dtk + d10 * v0 + d11 * v1;
-    return sc_clamp(M.kp[b] * (qref - q) + M.kd[b] * (vref - qd), -M.tau_max[b], M.tau_max[b]);
+    return sc_clamp(C.kp * (qref - q) + C.kd * (vref - qd), -C.tmax, C.tmax);
 }
 
 __device__ __forceinline__ void cost_terms(const DevModel<float>& M, const Pose& P, float& tz, float& tt) {
@@ -434,6 +453,17 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         if (cb >= M.lane_b0[l] && cb < M.lane_b0[l] + M.lane_len[l]) cowner = l;
     if (BRANCH && cb == bb) cowner = 2;
     SegKnots kc[KEEP ? LMAX : 1];
+    // short chains keep their bodies' constants (and the base's) in registers; long chains
+    // re-read them from shared memory where they are used
+    BodyConst bc[KEEP ? LMAX : 1];
+    BodyConst bc0;
+    if (KEEP) {
+#pragma unroll
+        for (int j = 0; j < LMAX; ++j) bc[j] = load_body(M, j < len ? b0 + j : b0);
+        bc0 = load_body(M, 0);
+    }
+    auto body = [&](int j) -> BodyConst { return KEEP ? bc[KEEP ? j : 0] : load_body(M, b0 + j); };
+    auto base = [&]() -> BodyConst { return KEEP ? bc0 : load_body(M, 0); };
     int kcur = -1;
     for (int h = 0; h < H; ++h) {
         const int r = h * (nk - 1);
@@ -449,10 +479,10 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         float tau[LMAX], taub = 0.f;
 #pragma unroll
         for (int j = 0; j < LMAX; ++j)
-            tau[j] = j < len ? hermite_pd(M, b0 + j, KEEP ? kc[KEEP ? j : 0] : seg_knots(knots, nj, k, b0 + j), s, dtk,
+            tau[j] = j < len ? hermite_pd(body(j), KEEP ? kc[KEEP ? j : 0] : seg_knots(knots, nj, k, b0 + j), s, dtk,
                                           inv_dtk, q[j], qd[j])
                              : 0.f;
-        if (on_branch) taub = hermite_pd(M, bb, seg_knots(knots, nj, k, bb), s, dtk, inv_dtk, qb, qdb);
+        if (on_branch) taub = hermite_pd(load_body(M, bb), seg_knots(knots, nj, k, bb), s, dtk, inv_dtk, qb, qdb);
         // ---- pass 1 ----
         B.R = quat_to_R(qw, qx, qy, qz);
         B.p = p;
@@ -463,7 +493,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         {
             V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
             body_contacts<PAPER>(M, 0, B, fen, fef, pcost, g == 0);
-            body_bias(M, 0, B, fen, fef, p0n, p0f);
+            body_bias(base(), B, fen, fef, p0n, p0f);
         }
         if (PAPER && g == 0) pcost += base_cost(M, B.R, B.p);
         float tz = 0.f, tt = 0.f;
@@ -471,7 +501,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         BodyMem mb;
         Pose PB;
         if (on_branch) {
-            body_pass1<KEEP, PAPER, -1>(M, bb, qb, qdb, B, PB, mb, pcost, g == 2);
+            body_pass1<KEEP, PAPER, -1>(M, load_body(M, bb), qb, qdb, B, PB, mb, pcost, g == 2);
             if (cb == bb) cost_terms(M, PB, tz, tt);
         }
         BodyMem mem[LMAX];
@@ -481,7 +511,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 constexpr int j = decltype(jc)::value;
                 if (j < len) {
                     Pose P;
-                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>()>(M, b0 + j, q[j], qd[j], Pp, P, mem[j], pcost, true);
+                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>()>(M, body(j), q[j], qd[j], Pp, P, mem[j], pcost, true);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
@@ -496,7 +526,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
         static_for<0, LMAX>([&](auto ic) {
             constexpr int j = LMAX - 1 - decltype(ic)::value;
-            if (j < len) body_pass2<KEEP, chain_axis<AXP, j>()>(M, b0 + j, tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+            if (j < len) body_pass2<KEEP, chain_axis<AXP, j>()>(body(j), tau[j], mem[j], j < len - 1, carry, cpn, cpf);
         });
         if (BRANCH) {
             // arms meet at the branch body: own + partner (lanes 2 <-> 3), identical on both
@@ -517,7 +547,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 carry = sumc;
                 cpn = sn;
                 cpf = sf;
-                body_pass2<KEEP, -1>(M, bb, taub, mb, true, carry, cpn, cpf);
+                body_pass2<KEEP, -1>(load_body(M, bb), taub, mb, true, carry, cpn, cpf);
                 if (g == 3) {  // lane 2 alone hands the branch to the base
 #pragma unroll
                     for (int t = 0; t < 6; ++t) carry.A[t] = 0.f;
@@ -532,7 +562,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         }
         // ---- base: every lane's contribution (butterfly), solve ----
         Art<float> IA0;
-        body_inertia(M, 0, IA0);
+        body_inertia(base(), IA0);
 #pragma unroll
         for (int t = 0; t < 6; ++t) IA0.A[t] += lsum(carry.A[t]);
 #pragma unroll
@@ -557,10 +587,10 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         float qdd[LMAX], qddb = 0.f;
         {
             V3<float> apw = aw, apv = av;
-            if (on_branch) qddb = body_pass3<KEEP, -1>(M, bb, mb, apw, apv);
+            if (on_branch) qddb = body_pass3<KEEP, -1>(load_body(M, bb), mb, apw, apv);
             static_for<0, LMAX>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
-                qdd[j] = j < len ? body_pass3<KEEP, chain_axis<AXP, j>()>(M, b0 + j, mem[j], apw, apv) : 0.f;
+                qdd[j] = j < len ? body_pass3<KEEP, chain_axis<AXP, j>()>(body(j), mem[j], apw, apv) : 0.f;
             });
         }
         // ---- running cost on the pre-step state ----
