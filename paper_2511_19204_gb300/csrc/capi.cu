@@ -57,6 +57,13 @@ static bool axis_is(const mppi_model_desc& d, int b, int k) {
     return true;
 }
 
+// the joint offset of body b lies on coordinate axis k (its other components are zero)
+static bool offset_along(const mppi_model_desc& d, int b, int k) {
+    for (int i = 0; i < 3; ++i)
+        if (i != k && d.jpos[3 * b + i] != 0.0) return false;
+    return true;
+}
+
 static bool is_chain(const mppi_model_desc& d, int first, int len, int parent) {
     if (len < 1 || first + len > d.nb || d.parent[first] != parent) return false;
     for (int j = 1; j < len; ++j)
@@ -79,7 +86,8 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
                 P.b0[l] = 1 + l * L;
                 P.len[l] = L;
                 if (xyy)
-                    xyy = axis_is(d, P.b0[l], 0) && axis_is(d, P.b0[l] + 1, 1) && axis_is(d, P.b0[l] + 2, 1);
+                    xyy = axis_is(d, P.b0[l], 0) && axis_is(d, P.b0[l] + 1, 1) && axis_is(d, P.b0[l] + 2, 1) &&
+                          offset_along(d, P.b0[l] + 1, 1) && offset_along(d, P.b0[l] + 2, 2);
             }
             if (xyy) P.axis_plan = AXP_XYY;
             return P;

@@ -86,9 +86,10 @@ constexpr int TOPO_GENERIC = 0;
 constexpr int TOPO_QUADRUPED = 1;   // 4 chains of <= 3 bodies off the base
 constexpr int TOPO_HUMANOID = 2;    // 2 chains of <= 6 off the base + a branch body with 2 chains of <= 6
 
-// Axis plans of the lanes-per-chain quadruped: AXP_GENERIC, any unit axes; AXP_XYY, every
-// chain's joints turn about +x, +y, +y (hip abduction, hip and knee flexion of the usual
-// quadruped layout), which the passes exploit at compile time.
+// Axis plans of the lanes-per-chain quadruped: AXP_GENERIC, any unit axes; AXP_XYY, the
+// usual leg layout: every chain's joints turn about +x, +y, +y (hip abduction, hip and
+// knee flexion), the thigh joint sits along y from the hip and the knee along z from the
+// thigh, which the passes exploit at compile time.
 constexpr int AXP_GENERIC = 0;
 constexpr int AXP_XYY = 1;
 

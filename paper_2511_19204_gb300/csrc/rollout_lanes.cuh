@@ -21,10 +21,14 @@ namespace mppi {
 
 constexpr int LANES = 4;
 
-// Axis code of chain position J under an axis plan (AXP_* in common.cuh).
+// Axis code and offset code of chain position J under an axis plan (AXP_* in common.cuh).
 template <int AXP, int J>
 __host__ __device__ constexpr int chain_axis() {
     return AXP == AXP_XYY ? (J == 0 ? 0 : 1) : -1;
+}
+template <int AXP, int J>
+__host__ __device__ constexpr int chain_offset() {
+    return AXP == AXP_XYY ? (J == 0 ? -1 : (J == 1 ? 1 : 2)) : -1;
 }
 
 // f(std::integral_constant<int, J>) for J = B .. E - 1, unrolled at compile time.
@@ -139,13 +143,88 @@ __device__ __forceinline__ void jfull_rotate(const JRot<AX>& J, const float* B, 
         out[8] = c2.z;
     }
 }
-template <int AX>
+// ------------------------------------------------------------------------------------
+// Joint offsets r along one coordinate axis (OF = 0, 1, 2: r = rho e_OF; OF = -1: any r).
+// (e_k x u)_i = eps_{i k p} u_p with p the third index: xk_src gives p (or -1 for i = k)
+// and xk_sgn the sign, so the products by zero components are never formed.
+// ------------------------------------------------------------------------------------
+__host__ __device__ constexpr int xk_src(int k, int i) { return i == k ? -1 : 3 - i - k; }
+__host__ __device__ constexpr float xk_sgn(int k, int i) {
+    return i == k ? 0.f : (((i - k + 3) % 3) == 2 ? 1.f : -1.f);
+}
+__device__ __forceinline__ float comp(V3<float> v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+
+template <int OF>
+__device__ __forceinline__ float rlen(V3<float> r) {
+    return OF == 0 ? r.x : (OF == 1 ? r.y : r.z);
+}
+// v + s (r x u), s = +1 or -1
+template <int OF>
+__device__ __forceinline__ V3<float> add_rcross(V3<float> v, V3<float> r, V3<float> u, float sgn) {
+    if constexpr (OF < 0) {
+        return sgn > 0.f ? v + cross(r, u) : v - cross(r, u);
+    } else {
+        const float rho = sgn * rlen<OF>(r);
+        float o[3] = {v.x, v.y, v.z};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i != OF) o[i] += (xk_sgn(OF, i) * rho) * comp(u, xk_src(OF, i));
+        return v3(o[0], o[1], o[2]);
+    }
+}
+// R r
+template <int OF>
+__device__ __forceinline__ V3<float> rot_r(const M3<float>& R, V3<float> r) {
+    if constexpr (OF < 0) {
+        return mul(R, r);
+    } else {
+        const float rho = rlen<OF>(r);
+        return v3(R.m[OF] * rho, R.m[3 + OF] * rho, R.m[6 + OF] * rho);
+    }
+}
+// The reference-point shift of the congruence (art_shift) for r = rho e_OF:
+// B2 = B + r^ C, A' = A + r^ B^T - B2 r^, written per component.
+template <int OF>
+__device__ __forceinline__ void art_shift_r(const float* A, const float* B, const float* C, V3<float> r,
+                                            Art<float>& out) {
+    if constexpr (OF < 0) {
+        art_shift(A, B, C, r, out);
+    } else {
+        const float rho = rlen<OF>(r);
+        auto Cs = [&](int i, int j) -> float {
+            return i == j ? C[i] : C[(i + j == 1) ? 3 : ((i + j == 2) ? 4 : 5)];
+        };
+        float B2[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                B2[3 * i + j] = i == OF ? B[3 * i + j] : B[3 * i + j] + (xk_sgn(OF, i) * rho) * Cs(xk_src(OF, i), j);
+        // A'(i, j) = A(i, j) + (r x B_row_j)_i - (B2_row_i x r)_j
+        //          = A(i, j) + [i != OF] s_i rho B(j, p_i) + [j != OF] s_j rho B2(i, p_j)
+        const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const int i = ii[t], j = jj[t];
+            float a = A[t];
+            if (i != OF) a += (xk_sgn(OF, i) * rho) * B[3 * j + xk_src(OF, i)];
+            if (j != OF) a += (xk_sgn(OF, j) * rho) * B2[3 * i + xk_src(OF, j)];
+            out.A[t] = a;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out.B[k] = B2[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out.C[k] = C[k];
+    }
+}
+
+template <int AX, int OF>
 __device__ __forceinline__ void jart_to_parent(const Art<float>& Ia, const JRot<AX>& J, V3<float> r, Art<float>& out) {
     float A[6], B[9], C[6];
     jsym_rotate(J, Ia.A, A);
     jfull_rotate(J, Ia.B, B);
     jsym_rotate(J, Ia.C, C);
-    art_shift(A, B, C, r, out);
+    art_shift_r<OF>(A, B, C, r, out);
 }
 
 // A body's constants, loaded once per rollout into registers (the step loop would
@@ -288,7 +367,7 @@ __device__ __forceinline__ void body_inertia(const BodyConst& C, Art<float>& IA)
 
 // Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
 // the bias (contact forces included).
-template <bool KEEP, bool PAPER, int AX>
+template <bool KEEP, bool PAPER, int AX, int OF>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyConst& C, float q, float qd,
                                            const Pose& Pp, Pose& P, BodyMem& m, float& pcost, bool count) {
     const V3<float> r = C.r;
@@ -302,9 +381,9 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyC
         if (KEEP) m.R = J.R;
     }
     P.R = jcompose(Pp.R, J);
-    P.p = Pp.p + mul(Pp.R, r);
+    P.p = Pp.p + rot_r<OF>(Pp.R, r);
     P.w = add_ax<AX>(C, jrotT(J, Pp.w), qd);
-    P.v = jrotT(J, Pp.v - cross(r, Pp.w));
+    P.v = jrotT(J, add_rcross<OF>(Pp.v, r, Pp.w, -1.f));
     m.cw = cross_ax<AX>(C, P.w, qd);
     m.cv = cross_ax<AX>(C, P.v, qd);
     V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
@@ -318,7 +397,7 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyC
 
 // Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
 // then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D.
-template <bool KEEP, int AX>
+template <bool KEEP, int AX, int OF>
 __device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMem& m, bool has_carry,
                                            Art<float>& carry, V3<float>& cpn, V3<float>& cpf) {
     const V3<float> r = C.r;
@@ -362,9 +441,9 @@ __device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMe
     const V3<float> pan = pAn + sym_mul(Ia.A, m.cw) + mul(Bm, m.cv) + ud * ua;
     const V3<float> paf = pAf + mulT(Bm, m.cw) + sym_mul(Ia.C, m.cv) + ud * ul;
     const JRot<AX> J = joint_rot<KEEP, AX>(C, m);
-    jart_to_parent(Ia, J, r, carry);
+    jart_to_parent<AX, OF>(Ia, J, r, carry);
     cpf = jrot(J, paf);
-    cpn = jrot(J, pan) + cross(r, cpf);
+    cpn = add_rcross<OF>(jrot(J, pan), r, cpf, 1.f);
     m.x0 = invD * ua;
     m.x1 = invD * ul;
     m.uu = ud;
@@ -372,12 +451,12 @@ __device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMe
 
 // Pass 3 of body b: from the parent's acceleration (apw, apv, offset by gravity) to its
 // own, and its joint acceleration.
-template <bool KEEP, int AX>
+template <bool KEEP, int AX, int OF>
 __device__ __forceinline__ float body_pass3(const BodyConst& C, const BodyMem& m, V3<float>& apw, V3<float>& apv) {
     const V3<float> r = C.r;
     const JRot<AX> J = joint_rot<KEEP, AX>(C, m);
     const V3<float> a1w = jrotT(J, apw) + m.cw;
-    const V3<float> a1v = jrotT(J, apv - cross(r, apw)) + m.cv;
+    const V3<float> a1v = jrotT(J, add_rcross<OF>(apv, r, apw, -1.f)) + m.cv;
     const float qdd = m.uu - dot(m.x0, a1w) - dot(m.x1, a1v);
     apw = add_ax<AX>(C, a1w, qdd);
     apv = a1v;
@@ -501,7 +580,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         BodyMem mb;
         Pose PB;
         if (on_branch) {
-            body_pass1<KEEP, PAPER, -1>(M, load_body(M, bb), qb, qdb, B, PB, mb, pcost, g == 2);
+            body_pass1<KEEP, PAPER, -1, -1>(M, load_body(M, bb), qb, qdb, B, PB, mb, pcost, g == 2);
             if (cb == bb) cost_terms(M, PB, tz, tt);
         }
         BodyMem mem[LMAX];
@@ -511,7 +590,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 constexpr int j = decltype(jc)::value;
                 if (j < len) {
                     Pose P;
-                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>()>(M, body(j), q[j], qd[j], Pp, P, mem[j], pcost, true);
+                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>(), chain_offset<AXP, j>()>(M, body(j), q[j], qd[j], Pp, P, mem[j], pcost, true);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
@@ -526,7 +605,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
         static_for<0, LMAX>([&](auto ic) {
             constexpr int j = LMAX - 1 - decltype(ic)::value;
-            if (j < len) body_pass2<KEEP, chain_axis<AXP, j>()>(body(j), tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+            if (j < len) body_pass2<KEEP, chain_axis<AXP, j>(), chain_offset<AXP, j>()>(body(j), tau[j], mem[j], j < len - 1, carry, cpn, cpf);
         });
         if (BRANCH) {
             // arms meet at the branch body: own + partner (lanes 2 <-> 3), identical on both
@@ -547,7 +626,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 carry = sumc;
                 cpn = sn;
                 cpf = sf;
-                body_pass2<KEEP, -1>(load_body(M, bb), taub, mb, true, carry, cpn, cpf);
+                body_pass2<KEEP, -1, -1>(load_body(M, bb), taub, mb, true, carry, cpn, cpf);
                 if (g == 3) {  // lane 2 alone hands the branch to the base
 #pragma unroll
                     for (int t = 0; t < 6; ++t) carry.A[t] = 0.f;
@@ -587,10 +666,10 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         float qdd[LMAX], qddb = 0.f;
         {
             V3<float> apw = aw, apv = av;
-            if (on_branch) qddb = body_pass3<KEEP, -1>(load_body(M, bb), mb, apw, apv);
+            if (on_branch) qddb = body_pass3<KEEP, -1, -1>(load_body(M, bb), mb, apw, apv);
             static_for<0, LMAX>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
-                qdd[j] = j < len ? body_pass3<KEEP, chain_axis<AXP, j>()>(body(j), mem[j], apw, apv) : 0.f;
+                qdd[j] = j < len ? body_pass3<KEEP, chain_axis<AXP, j>(), chain_offset<AXP, j>()>(body(j), mem[j], apw, apv) : 0.f;
             });
         }
         // ---- running cost on the pre-step state ----

@@ -34,7 +34,11 @@ applies joint rotations to two components. Per joint body it evaluates 666 inste
 961: joint rotation 1 (sincos only), pass 1 61 (composition 18, origin 18, angular
 velocity 7, linear velocity 18), velocity product 4, pass 2 390 (U, D, u 3, congruence
 210 with 108 for the rotations, force transform 24, the rest as above), pass 3 44
-(transform 30, joint acceleration 13, update 1); the other items as above.
+(transform 30, joint acceleration 13, update 1); the other items as above. The thigh and
+calf joints of that layout also sit on one coordinate axis of their parent (r = rho e_k),
+so products with r touch two components: 106 fewer per body (origin 6, linear velocity
+10, reference-point shift of the congruence 32, force transform 16, acceleration
+transform 22), 560 per body.
 """
 from __future__ import annotations
 
@@ -46,11 +50,13 @@ MOD_CONTACT = 5 + 8 + 4
 MOD_BASE = 3 + 54 + 3 + 6 + 3 + 1 + 2 + 3
 MOD_WEIGHTS = ("w_h", "w_orient", "w_q", "w_cvel", "w_cforce", "w_term")
 PER_JOINT_XYY = 55 + 1 + 61 + 4 + 78 + (3 + 63 + 66 + 24 + 210 + 24) + 27 + 44 + 4 + 2
+PER_JOINT_XYY_AXIAL = PER_JOINT_XYY - (12 + 8 + 70 + 8 + 8)
 
 
 def axis_plan_xyy(model) -> bool:
     """True when the model runs the axis-specialised chain kernel: a floating base with 4
-    chains of 3 bodies whose joint axes are exactly +x, +y, +y."""
+    chains of 3 bodies whose joint axes are exactly +x, +y, +y, with the thigh joint along
+    y from the hip and the knee along z from the thigh."""
     import numpy as np
     if model.fixed_base or model.nb != 13:
         return False
@@ -62,6 +68,10 @@ def axis_plan_xyy(model) -> bool:
         if not (np.array_equal(model.axis[b0], ex) and np.array_equal(model.axis[b0 + 1], ey)
                 and np.array_equal(model.axis[b0 + 2], ey)):
             return False
+        if model.jpos[b0 + 1][0] != 0.0 or model.jpos[b0 + 1][2] != 0.0:
+            return False
+        if model.jpos[b0 + 2][0] != 0.0 or model.jpos[b0 + 2][1] != 0.0:
+            return False
     return True
 
 
@@ -71,8 +81,11 @@ def flops_per_step(model, contacts_active=None, mapping_chain=True) -> int:
     ``mapping_chain``: the rollout runs the lanes-per-chain kernel (which specialises the
     axes of x, y, y quadrupeds)."""
     nc = model.nc if contacts_active is None else contacts_active
-    per_joint = PER_JOINT_XYY if mapping_chain and axis_plan_xyy(model) else PER_JOINT
-    f = per_joint * model.nj + PER_CONTACT * nc + PER_BASE
+    if mapping_chain and axis_plan_xyy(model):
+        joints = 4 * PER_JOINT_XYY + 8 * PER_JOINT_XYY_AXIAL
+    else:
+        joints = PER_JOINT * model.nj
+    f = joints + PER_CONTACT * nc + PER_BASE
     if any(getattr(model, w, 0.0) for w in MOD_WEIGHTS):
         f += MOD_JOINT * model.nj + MOD_CONTACT * model.nc + MOD_BASE
     return f
