@@ -37,7 +37,7 @@ WORKLOAD = ("single-instance scale: quadruped (floating base + 12 revolute joint
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=8192)
@@ -232,12 +232,15 @@ def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1,
     stream = torch.cuda.Stream()
     ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream, mapping=mapping,
                                         spline=spline)
-    if mapping == -1:
-        ctrl.autotune()
     ctrl.profile(True)
     x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
     out = torch.zeros(ctrl.E, dtype=torch.float32, device="cuda")
     w = torch.tensor(p.nominal.reshape(-1), dtype=torch.float32, device="cuda")
+    if mapping == -1:
+        # tune on the workload's own state: one solve uploads it first
+        ctrl.solve_device(x.data_ptr(), out.data_ptr(), d_warm=w.data_ptr())
+        ctrl.sync()
+        ctrl.autotune()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(warmup):
         ctrl.solve_device(x.data_ptr(), out.data_ptr(), d_warm=w.data_ptr())
@@ -512,6 +515,8 @@ def run_ours(args, rank, world, local):
     tuned = None
     if args.mapping == -1:
         try:
+            # tune on the workload's own state: one solve uploads it first
+            ctrl.solve(p.state)
             m, b, ms = ctrl.autotune()
             tuned = {"mapping": mppi.MAPPING_NAMES.get(m, m), "block": b,
                      "ms_per_rollout": {mppi.MAPPING_NAMES[k]: [round(float(v), 4) if v > 0 else None for v in ms[k]]
