@@ -127,10 +127,13 @@ cudaError_t launch_average_reduce(const double* partial, int nchunks, int E, dou
 // ------------------------------------------------------------------------------------
 // Iteration bookkeeping.
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs a) { finalize_iteration(a); }
+// One block; the element sums are spread over 1024 threads (each (sub-sum, element) task
+// sums its chunks in the same order whatever the block size, so the persistent kernel's
+// 256-thread finalize gives the same bits).
+__global__ void __launch_bounds__(1024) finalize_kernel(FinalizeArgs a) { finalize_iteration(a); }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-    finalize_kernel<<<1, 256, 0, s>>>(a);
+    finalize_kernel<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
 

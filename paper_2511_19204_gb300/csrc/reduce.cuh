@@ -31,8 +31,7 @@ __device__ __forceinline__ MinMax block_minmax(const float* __restrict__ costs, 
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
     float mn = INFINITY, mx = -INFINITY;
     int arg = 0x7fffffff, cnt = 0;
-    for (int n = t; n < N; n += blockDim.x) {
-        const float c = costs[n];
+    auto take = [&](float c, int n) {
         if (isfinite(c)) {
             ++cnt;
             if (c < mn) {
@@ -41,7 +40,26 @@ __device__ __forceinline__ MinMax block_minmax(const float* __restrict__ costs, 
             }
             mx = fmaxf(mx, c);
         }
+    };
+    // 16-byte loads, unrolled so a thread's loads (from L2) are in flight together. The
+    // result does not depend on how indices are spread over threads: min and max are
+    // exact and ties go to the lowest index.
+    int head = 0;
+    if ((reinterpret_cast<uintptr_t>(costs) & 15) == 0) {
+        const float4* c4 = reinterpret_cast<const float4*>(costs);
+        const int n4 = N >> 2;
+#pragma unroll 4
+        for (int i = t; i < n4; i += blockDim.x) {
+            const float4 v = c4[i];
+            take(v.x, 4 * i);
+            take(v.y, 4 * i + 1);
+            take(v.z, 4 * i + 2);
+            take(v.w, 4 * i + 3);
+        }
+        head = n4 << 2;
     }
+#pragma unroll 4
+    for (int n = head + t; n < N; n += blockDim.x) take(costs[n], n);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const float omn = __shfl_xor_sync(0xffffffffu, mn, off);
@@ -106,6 +124,7 @@ __device__ __noinline__ void chunk_weights_average(const float* __restrict__ cos
     const int el = ey * blockDim.x + threadIdx.x;
     if (el < E) {
         double acc = 0.0;
+#pragma unroll 16
         for (int i = 0; i < cn; ++i) acc = fma(s_e[i], (double)knots[(size_t)(n0 + i) * E + el], acc);
         partial[(size_t)c * E + el] = acc;
     }
@@ -141,6 +160,7 @@ __device__ __forceinline__ void block_total_zq(const double* __restrict__ zq, in
     if (t < 2 * FIN_SPLIT) {
         const int sidx = t % FIN_SPLIT, which = t / FIN_SPLIT;
         double acc = 0.0;
+#pragma unroll 8
         for (int c = sidx; c < nchunks; c += FIN_SPLIT) acc += zq[2 * c + which];
         s_part[t] = acc;
     }
@@ -208,8 +228,10 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
             for (int task = t; task < FIN_SPLIT * FIN_TILE; task += blockDim.x) {
                 const int sidx = task / FIN_TILE, el = task - sidx * FIN_TILE, e = e0 + el;
                 double acc = 0.0;
-                if (e < a.E)
+                if (e < a.E) {
+#pragma unroll 8
                     for (int c = sidx; c < a.nchunks; c += FIN_SPLIT) acc += a.partial[(size_t)c * a.E + e];
+                }
                 s_sub[task] = acc;
             }
         __syncthreads();
