@@ -909,6 +909,21 @@ mppi_status mppi_get_warm_start(const mppi_ctx* c, float* h_out) {
     return MPPI_OK;
 }
 
+mppi_status mppi_selftest_sincos(int32_t n, const float* h_x, float* h_sc) {
+    if (n < 0 || (n > 0 && (!h_x || !h_sc))) return MPPI_ERR_INVALID_ARG;
+    if (n == 0) return MPPI_OK;
+    float *d_x = nullptr, *d_sc = nullptr;
+    cudaError_t e = cudaMalloc(&d_x, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_sc, sizeof(float) * 2 * n);
+    if (e == cudaSuccess) e = cudaMemcpy(d_x, h_x, sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_fast_sincos(n, d_x, d_sc, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(h_sc, d_sc, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost);
+    if (d_x) cudaFree(d_x);
+    if (d_sc) cudaFree(d_sc);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest_sincos");
+    return MPPI_OK;
+}
+
 mppi_status mppi_philox_words(int32_t n, const uint32_t* h_ctr, const uint32_t* h_key, uint32_t* h_out) {
     if (n < 0 || (n > 0 && (!h_ctr || !h_key || !h_out))) return MPPI_ERR_INVALID_ARG;
     if (n == 0) return MPPI_OK;

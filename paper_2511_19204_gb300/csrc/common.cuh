@@ -35,6 +35,38 @@ __device__ __forceinline__ float sc_min(float a, float b) { return fminf(a, b); 
 __device__ __forceinline__ double sc_min(double a, double b) { return fmin(a, b); }
 template <typename T>
 __device__ __forceinline__ T sc_clamp(T x, T lo, T hi) { return sc_min(sc_max(x, lo), hi); }
+// Reciprocal and reciprocal square root: FP32 takes the hardware approximations (within
+// a couple of ulp, no slow path), FP64 (the check build) the correctly rounded forms.
+__device__ __forceinline__ float sc_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double sc_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sc_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sc_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// sin and cos of an FP32 angle of moderate size (joint angles, |x| up to ~1e4): Cody and
+// Waite's reduction by pi/2 with the constant split in two floats, then the Taylor
+// polynomials of sin (to x^9) and cos (to x^10) on [-pi/4, pi/4], whose truncation errors
+// (< 2e-9 and < 2e-10) lie below half an FP32 ulp of the results; the quadrant picks and
+// signs the pair.
+__device__ __forceinline__ void fast_sincos(float x, float* s, float* c) {
+    const float k = rintf(x * 0.636619772367581343f);       // x / (pi / 2), rounded
+    float r = fmaf(-k, 1.57079637050628662109375f, x);      // float(pi / 2)
+    r = fmaf(-k, -4.37113900018624283e-8f, r);              // pi / 2 - float(pi / 2)
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);  // 1/9!, -1/7!
+    ps = fmaf(r2, ps, 8.33333333e-3f);                      // 1/5!
+    ps = fmaf(r2, ps, -1.66666667e-1f);                     // -1/3!
+    const float sn = fmaf(r * r2, ps, r);
+    float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);  // -1/10!, 1/8!
+    pc = fmaf(r2, pc, -1.38888889e-3f);                     // -1/6!
+    pc = fmaf(r2, pc, 4.16666667e-2f);                      // 1/4!
+    pc = fmaf(r2, pc, -0.5f);
+    const float cs = fmaf(r2, pc, 1.0f);
+    const int q = (int)k & 3;
+    const float a = (q & 1) ? cs : sn;   // sin: sn, cs, -sn, -cs
+    const float b = (q & 1) ? sn : cs;   // cos: cs, -sn, -cs, sn
+    *s = (q & 2) ? -a : a;
+    *c = ((q + 1) & 2) ? -b : b;
+}
 
 // ------------------------------------------------------------------------------------
 // Model constants. Per-body arrays are structure-of-arrays over MAXB so that lane b of
@@ -370,9 +402,7 @@ __device__ __forceinline__ void art_solve(const Art<T>& I, const T* b, T* x) {
 #pragma unroll
             for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
             if (i == j) {
-                const T d = sc_sqrt(s);
-                L[i][i] = d;
-                inv[i] = T(1) / d;
+                inv[i] = sc_rsqrt(s);  // 1 / L[i][i]
             } else {
                 L[i][j] = s * inv[j];
             }

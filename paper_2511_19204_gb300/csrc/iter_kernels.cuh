@@ -195,6 +195,24 @@ cudaError_t launch_shift_knots(float* knots, int nj, int nk, int H, int steps, d
 }
 
 // ------------------------------------------------------------------------------------
+// The rollout's FP32 sine/cosine (fast_sincos) on a list of angles, for accuracy checks.
+// ------------------------------------------------------------------------------------
+__global__ void fast_sincos_kernel(int n, const float* __restrict__ x, float* __restrict__ sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s, c;
+    fast_sincos(x[i], &s, &c);
+    sc[2 * i] = s;
+    sc[2 * i + 1] = c;
+}
+
+cudaError_t launch_fast_sincos(int n, const float* x, float* sc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    fast_sincos_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, sc);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
 // Philox words for a list of counters (bit-exactness checks).
 // ------------------------------------------------------------------------------------
 __global__ void philox_words_kernel(int n, const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,

@@ -324,7 +324,7 @@ __device__ __forceinline__ void body_contacts(const DevModel<float>& M, int b, c
         if (depth > 0.f) {
             const V3<float> vw = mul(P.R, P.v + cross(P.w, rc));
             const float fn = fmaxf(M.contact_k * depth - M.contact_c * vw.z, 0.f);
-            const float sc = -M.mu * fn / sqrtf(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
+            const float sc = -M.mu * fn * rsqrtf(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
             const V3<float> F = v3(sc * vw.x, sc * vw.y, fn);
             const V3<float> fb = mulT(P.R, F);
             fef = fef + fb;
@@ -371,7 +371,7 @@ template <bool KEEP, bool PAPER, int AX, int OF>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyConst& C, float q, float qd,
                                            const Pose& Pp, Pose& P, BodyMem& m, float& pcost, bool count) {
     const V3<float> r = C.r;
-    sincosf(q, &m.s, &m.c);
+    fast_sincos(q, &m.s, &m.c);
     JRot<AX> J;
     if constexpr (AX >= 0) {
         J.s = m.s;
@@ -416,7 +416,7 @@ __device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMe
     }
     const V3<float> ua = symcol_ax<AX>(C, IA.A);
     const V3<float> ul = btcol_ax<AX>(C, IA.B);
-    const float invD = 1.f / (dot_ax<AX>(C, ua) + C.arm);
+    const float invD = sc_rcp(dot_ax<AX>(C, ua) + C.arm);
     const float u = tau - dot_ax<AX>(C, pAn);
     const float U[6] = {ua.x, ua.y, ua.z, ul.x, ul.y, ul.z};
     Art<float> Ia;
@@ -710,16 +710,16 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 dqs = 0.5f * dt;
             } else {
                 float sh, ch;
-                sincosf(0.5f * wn * dt, &sh, &ch);
+                fast_sincos(0.5f * wn * dt, &sh, &ch);
                 dq0 = ch;
-                dqs = sh / wn;
+                dqs = __fdividef(sh, wn);
             }
             const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
             const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
             const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
             const float ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
             const float nz = qw * dz + qx * dy - qy * dx + qz * dq0;
-            const float inv = 1.f / sqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
+            const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
             qw = nw * inv;
             qx = nx * inv;
             qy = ny * inv;
