@@ -275,10 +275,11 @@ mppi_status mppi_get_warm_start(const mppi_ctx* ctx, float* h_out);
 /* Kernel-level entry points (each runs one kernel of the path on host buffers)         */
 /* ---------------------------------------------------------------------------------- */
 
-/* The rollout's FP32 sine and cosine (a reduction by pi/2 and Taylor polynomials; no
- * counterpart in the paper, which leaves the arithmetic to its simulator) on n angles:
- * h_sc [n][2] = (sin, cos). For accuracy checks. */
-mppi_status mppi_selftest_sincos(int32_t n, const float* h_x, float* h_sc);
+/* The rollout's own FP32 elementary functions (no counterpart in the paper, which leaves
+ * the arithmetic to its simulator): sine and cosine (a reduction by pi/2 and Taylor
+ * polynomials) and the arctangent of the tilt cost (atan2 for y >= 0) on n argument
+ * pairs: h_out [n][3] = (sin x, cos x, atan2(y, x)). For accuracy checks. */
+mppi_status mppi_selftest_math(int32_t n, const float* h_x, const float* h_y, float* h_out);
 
 /* Philox4x32-10 (Salmon et al., SC'11) words for n counters: h_ctr [n][4], key [2],
  * h_out [n][4]. */

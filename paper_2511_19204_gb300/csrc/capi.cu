@@ -909,18 +909,21 @@ mppi_status mppi_get_warm_start(const mppi_ctx* c, float* h_out) {
     return MPPI_OK;
 }
 
-mppi_status mppi_selftest_sincos(int32_t n, const float* h_x, float* h_sc) {
-    if (n < 0 || (n > 0 && (!h_x || !h_sc))) return MPPI_ERR_INVALID_ARG;
+mppi_status mppi_selftest_math(int32_t n, const float* h_x, const float* h_y, float* h_out) {
+    if (n < 0 || (n > 0 && (!h_x || !h_y || !h_out))) return MPPI_ERR_INVALID_ARG;
     if (n == 0) return MPPI_OK;
-    float *d_x = nullptr, *d_sc = nullptr;
+    float *d_x = nullptr, *d_y = nullptr, *d_o = nullptr;
     cudaError_t e = cudaMalloc(&d_x, sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_sc, sizeof(float) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_y, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_o, sizeof(float) * 3 * n);
     if (e == cudaSuccess) e = cudaMemcpy(d_x, h_x, sizeof(float) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_fast_sincos(n, d_x, d_sc, 0);
-    if (e == cudaSuccess) e = cudaMemcpy(h_sc, d_sc, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(d_y, h_y, sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_fast_math(n, d_x, d_y, d_o, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(h_out, d_o, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost);
     if (d_x) cudaFree(d_x);
-    if (d_sc) cudaFree(d_sc);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest_sincos");
+    if (d_y) cudaFree(d_y);
+    if (d_o) cudaFree(d_o);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest_math");
     return MPPI_OK;
 }
 

@@ -42,6 +42,32 @@ __device__ __forceinline__ double sc_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float sc_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sc_rsqrt(double x) { return 1.0 / sqrt(x); }
 
+// atan2(y, x) for y >= 0 (an angle in [0, pi]) in FP32 without a division slow path:
+// t = min / max in [0, 1]; above tan(pi/8) the identity atan t = pi/4 + atan((t-1)/(t+1))
+// brings the argument into [-tan(pi/8), tan(pi/8)], where the Taylor series of atan to
+// u^17 has truncation error < 3e-9; then atan y/x = pi/2 - atan x/y for y > |x| and
+// pi - that for x < 0.
+__device__ __forceinline__ float fast_atan2_pos(float y, float x) {
+    const float ax = fabsf(x);
+    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
+    if (!(mx > 0.f)) return x < 0.f ? 3.14159265358979f : 0.f;
+    const float t = __fdividef(mn, mx);
+    const bool red = t > 0.414213562373095f;
+    const float u = red ? __fdividef(t - 1.f, t + 1.f) : t;
+    const float u2 = u * u;
+    float p = fmaf(u2, 1.f / 17.f, -1.f / 15.f);
+    p = fmaf(u2, p, 1.f / 13.f);
+    p = fmaf(u2, p, -1.f / 11.f);
+    p = fmaf(u2, p, 1.f / 9.f);
+    p = fmaf(u2, p, -1.f / 7.f);
+    p = fmaf(u2, p, 1.f / 5.f);
+    p = fmaf(u2, p, -1.f / 3.f);
+    float a = fmaf(u * u2, p, u);
+    if (red) a += 0.785398163397448f;           // pi / 4
+    if (y > ax) a = 1.57079632679490f - a;      // pi / 2
+    return x < 0.f ? 3.14159265358979f - a : a;
+}
+
 // sin and cos of an FP32 angle of moderate size (joint angles, |x| up to ~1e4): Cody and
 // Waite's reduction by pi/2 with the constant split in two floats, then the Taylor
 // polynomials of sin (to x^9) and cos (to x^10) on [-pi/4, pi/4], whose truncation errors
@@ -67,6 +93,13 @@ __device__ __forceinline__ void fast_sincos(float x, float* s, float* c) {
     *s = (q & 2) ? -a : a;
     *c = ((q + 1) & 2) ? -b : b;
 }
+
+// The rollout's elementary functions per precision: the FP32 path uses the own versions
+// above and the hardware approximations, the FP64 check build the library's exact ones.
+__device__ __forceinline__ void sc_sincos_r(float x, float* s, float* c) { fast_sincos(x, s, c); }
+__device__ __forceinline__ void sc_sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float sc_atan2_pos(float y, float x) { return fast_atan2_pos(y, x); }
+__device__ __forceinline__ double sc_atan2_pos(double y, double x) { return atan2(y, x); }
 
 // ------------------------------------------------------------------------------------
 // Model constants. Per-body arrays are structure-of-arrays over MAXB so that lane b of
@@ -275,7 +308,7 @@ __device__ __forceinline__ T base_cost(const DevModel<T>& M, const M3<T>& R, V3<
         for (int b = 0; b < 3; ++b)
             Q[3 * a + b] = R.m[a] * M.Rdes[b] + R.m[3 + a] * M.Rdes[3 + b] + R.m[6 + a] * M.Rdes[6 + b];
     const T vx = Q[7] - Q[5], vy = Q[2] - Q[6], vz = Q[3] - Q[1];
-    const T th = sc_atan2(sc_sqrt(vx * vx + vy * vy + vz * vz), Q[0] + Q[4] + Q[8] - T(1));
+    const T th = sc_atan2_pos(sc_sqrt(vx * vx + vy * vy + vz * vz), Q[0] + Q[4] + Q[8] - T(1));
     return M.w_h * sc_abs(p.z - M.z_des) + M.w_orient * th * th;
 }
 

@@ -102,7 +102,7 @@ struct FinalizeArgs {
 };
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* best_out, int E, cudaStream_t s);
-cudaError_t launch_fast_sincos(int n, const float* x, float* sc, cudaStream_t s);
+cudaError_t launch_fast_math(int n, const float* x, const float* y, float* out, cudaStream_t s);
 cudaError_t launch_philox_words(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s);
 cudaError_t launch_dynamics_f32(const DevModel<float>* m, int n, const double* x, const double* tau, double* acc,
                                 cudaStream_t s);

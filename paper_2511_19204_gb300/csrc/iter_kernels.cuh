@@ -195,20 +195,23 @@ cudaError_t launch_shift_knots(float* knots, int nj, int nk, int H, int steps, d
 }
 
 // ------------------------------------------------------------------------------------
-// The rollout's FP32 sine/cosine (fast_sincos) on a list of angles, for accuracy checks.
+// The rollout's FP32 sine/cosine (fast_sincos) and tilt arctangent (fast_atan2_pos) on a
+// list of arguments, for accuracy checks: out[i] = (sin x, cos x, atan2(y, x)).
 // ------------------------------------------------------------------------------------
-__global__ void fast_sincos_kernel(int n, const float* __restrict__ x, float* __restrict__ sc) {
+__global__ void fast_math_kernel(int n, const float* __restrict__ x, const float* __restrict__ y,
+                                 float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s, c;
     fast_sincos(x[i], &s, &c);
-    sc[2 * i] = s;
-    sc[2 * i + 1] = c;
+    out[3 * i] = s;
+    out[3 * i + 1] = c;
+    out[3 * i + 2] = fast_atan2_pos(y[i], x[i]);
 }
 
-cudaError_t launch_fast_sincos(int n, const float* x, float* sc, cudaStream_t s) {
+cudaError_t launch_fast_math(int n, const float* x, const float* y, float* out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    fast_sincos_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, sc);
+    fast_math_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, y, out);
     return cudaGetLastError();
 }
 

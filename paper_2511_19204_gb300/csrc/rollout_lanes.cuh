@@ -488,7 +488,7 @@ __device__ __forceinline__ float hermite_pd(const BodyConst& C, const SegKnots& 
 
 __device__ __forceinline__ void cost_terms(const DevModel<float>& M, const Pose& P, float& tz, float& tt) {
     const float dz = P.p.z - M.z_des;
-    const float tilt = atan2f(sqrtf(P.R.m[2] * P.R.m[2] + P.R.m[5] * P.R.m[5]), P.R.m[8]);
+    const float tilt = fast_atan2_pos(sqrtf(P.R.m[2] * P.R.m[2] + P.R.m[5] * P.R.m[5]), P.R.m[8]);
     tz = M.w_z * dz * dz;
     tt = M.w_tilt * tilt * tilt;
 }
@@ -544,11 +544,17 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
     auto body = [&](int j) -> BodyConst { return KEEP ? bc[KEEP ? j : 0] : load_body(M, b0 + j); };
     auto base = [&]() -> BodyConst { return KEEP ? bc0 : load_body(M, 0); };
     int kcur = -1;
+    // segment k = floor(h (nk - 1) / H) and its remainder rem = h (nk - 1) - k H, advanced
+    // by integer steps instead of a division per step; s = rem / H
+    const float inv_H = 1.0f / (float)H;
+    int k = 0, rem = -(nk - 1);
     for (int h = 0; h < H; ++h) {
-        const int r = h * (nk - 1);
-        int k = r / H;
-        if (k > nk - 2) k = nk - 2;
-        const float s = (float)(r - k * H) / (float)H;
+        rem += nk - 1;
+        while (rem >= H) {
+            rem -= H;
+            ++k;
+        }
+        const float s = (float)rem * inv_H;
         if (KEEP && k != kcur) {
             kcur = k;
 #pragma unroll

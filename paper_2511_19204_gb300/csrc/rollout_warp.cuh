@@ -82,7 +82,7 @@ __device__ __forceinline__ void warp_dynamics(const DevModel<T>& M, const LaneCo
     M3<T> Rj;
     {
         T sq, cq;
-        sc_sincos(L.joint ? S.q : T(0), &sq, &cq);
+        sc_sincos_r(L.joint ? S.q : T(0), &sq, &cq);
         Rj = axis_rotation(L.a, sq, cq);
     }
     M3<T> R;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void warp_dynamics(const DevModel<T>& M, const LaneCo
         if (depth > T(0)) {
             const V3<T> vw = mul(R, vl + cross(w, rc));
             const T fn = sc_max(M.contact_k * depth - M.contact_c * vw.z, T(0));
-            const T sc = -M.mu * fn / sc_sqrt(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
+            const T sc = -M.mu * fn * sc_rsqrt(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
             const V3<T> F = v3(sc * vw.x, sc * vw.y, fn);
             const V3<T> fb = mulT(R, F);
             fe_f = fe_f + fb;
@@ -186,7 +186,7 @@ __device__ __forceinline__ void warp_dynamics(const DevModel<T>& M, const LaneCo
         T tz = T(0), tt = T(0);
         if (gl == M.cost_body) {
             const T dz = p.z - M.z_des;
-            const T tilt = sc_atan2(sc_sqrt(R.m[2] * R.m[2] + R.m[5] * R.m[5]), R.m[8]);
+            const T tilt = sc_atan2_pos(sc_sqrt(R.m[2] * R.m[2] + R.m[5] * R.m[5]), R.m[8]);
             tz = M.w_z * dz * dz;
             tt = M.w_tilt * tilt * tilt;
         }
@@ -204,7 +204,7 @@ __device__ __forceinline__ void warp_dynamics(const DevModel<T>& M, const LaneCo
                     IA.B[1] * L.a.x + IA.B[4] * L.a.y + IA.B[7] * L.a.z,
                     IA.B[2] * L.a.x + IA.B[5] * L.a.y + IA.B[8] * L.a.z);
             const T D = dot(L.a, Ua) + L.arm;
-            invD = T(1) / D;
+            invD = sc_rcp(D);
             uu = tau - dot(L.a, pAn);
             Art<T> Ia;
             const T U[6] = {Ua.x, Ua.y, Ua.z, Ul.x, Ul.y, Ul.z};
@@ -315,7 +315,7 @@ __device__ __forceinline__ void integrate_lane(const DevModel<T>& M, const LaneC
             dqs = T(0.5) * dt;
         } else {
             T sh, ch;
-            sc_sincos(T(0.5) * wn * dt, &sh, &ch);
+            sc_sincos_r(T(0.5) * wn * dt, &sh, &ch);
             dq0 = ch;
             dqs = sh / wn;
         }
@@ -324,7 +324,7 @@ __device__ __forceinline__ void integrate_lane(const DevModel<T>& M, const LaneC
         const T nx = S.qw * dx + S.qx * dq0 + S.qy * dz - S.qz * dy;
         const T ny = S.qw * dy - S.qx * dz + S.qy * dq0 + S.qz * dx;
         const T nz = S.qw * dz + S.qx * dy - S.qy * dx + S.qz * dq0;
-        const T inv = T(1) / sc_sqrt(nw * nw + nx * nx + ny * ny + nz * nz);
+        const T inv = sc_rsqrt(nw * nw + nx * nx + ny * ny + nz * nz);
         S.qw = nw * inv;
         S.qx = nx * inv;
         S.qy = ny * inv;

@@ -113,7 +113,7 @@ SIGNATURES = [
     ("mppi_shift_warm_start", C.c_int32, [_P, C.c_int32]),
     ("mppi_get_warm_start", C.c_int32, [_P, _fp]),
     ("mppi_model_info", C.c_int32, [_P, _ip]),
-    ("mppi_selftest_sincos", C.c_int32, [C.c_int32, _fp, _fp]),
+    ("mppi_selftest_math", C.c_int32, [C.c_int32, _fp, _fp, _fp]),
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
     ("mppi_average", C.c_int32, [C.c_int32, C.c_int32, _fp, _dp, _dp]),
@@ -526,9 +526,10 @@ class Server:
             pass
 
 
-def selftest_sincos(x):
-    """The rollout's FP32 (sin, cos) of angles x, shape [n, 2]."""
+def selftest_math(x, y):
+    """The rollout's FP32 (sin x, cos x, atan2(y, x)) for y >= 0, shape [n, 3]."""
     xs = _f(x).reshape(-1).copy()
-    out = np.zeros((xs.shape[0], 2), np.float32)
-    _check(load().mppi_selftest_sincos(xs.shape[0], _pf(xs), _pf(out)))
+    ys = _f(y).reshape(-1).copy()
+    out = np.zeros((xs.shape[0], 3), np.float32)
+    _check(load().mppi_selftest_math(xs.shape[0], _pf(xs), _pf(ys), _pf(out)))
     return out

@@ -284,14 +284,20 @@ def test_average_matches_oracle(M, orc, n, E):
     np.testing.assert_array_equal(M.average(kn2, np.array([0.25, 0.75])), 0.25 * kn2[0] + 0.75 * kn2[1])
 
 
-def test_rollout_sincos_accuracy(M):
-    # the rollout's own sine/cosine against numpy's FP64 values of the same FP32 angles
+def test_rollout_elementary_functions(M):
+    # the rollout's own sine/cosine and tilt arctangent against numpy's FP64 values of the
+    # same FP32 arguments
     rng = np.random.default_rng(12)
     x = np.concatenate([np.linspace(-4 * np.pi, 4 * np.pi, 100001), rng.uniform(-100, 100, 100000),
                         [0.0, -0.0, np.pi / 4, np.pi / 2, np.pi, 1e-30, -1e-8]]).astype(np.float32)
-    sc = M.selftest_sincos(x).astype(np.float64)
-    xd = x.astype(np.float64)
-    err = np.maximum(np.abs(sc[:, 0] - np.sin(xd)), np.abs(sc[:, 1] - np.cos(xd)))
-    print(f"fast_sincos: max abs error {err.max():.2e} over |x| <= 100")
-    assert err.max() < 2.5e-7
-    assert sc[-2, 0] == np.float32(1e-30).astype(np.float64) or abs(sc[-2, 0] - 1e-30) < 1e-37
+    y = np.abs(rng.normal(size=x.shape)).astype(np.float32)
+    y[::7] *= np.float32(1e-4)
+    y[-7:] = [0.0, 0.0, 1.0, 0.0, 1e-20, 2.0, 0.0]
+    out = M.selftest_math(x, y).astype(np.float64)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    err_sc = np.maximum(np.abs(out[:, 0] - np.sin(xd)), np.abs(out[:, 1] - np.cos(xd)))
+    err_at = np.abs(out[:, 2] - np.arctan2(yd, xd))
+    print(f"fast_sincos: max abs error {err_sc.max():.2e} over |x| <= 100; "
+          f"fast_atan2_pos: max abs error {err_at.max():.2e}")
+    assert err_sc.max() < 2.5e-7
+    assert err_at.max() < 5e-7
