@@ -50,7 +50,7 @@ __device__ __forceinline__ double sc_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float fast_atan2_pos(float y, float x) {
     const float ax = fabsf(x);
     const float mx = fmaxf(y, ax), mn = fminf(y, ax);
-    if (!(mx > 0.f)) return x < 0.f ? 3.14159265358979f : 0.f;
+    if (!(mx > 0.f)) return signbit(x) ? 3.14159265358979f : 0.f;  // atan2(0, -0) = pi
     const float t = __fdividef(mn, mx);
     const bool red = t > 0.414213562373095f;
     const float u = red ? __fdividef(t - 1.f, t + 1.f) : t;
