@@ -293,6 +293,35 @@ __device__ __forceinline__ V3<float> btcol_ax(const BodyConst& C, const float* B
     }
 }
 
+// S v, B v and B^T v for a vector v whose component AX is zero (AX < 0: any v).
+template <int AX>
+__device__ __forceinline__ V3<float> sym_mul_z(const float* S, V3<float> v) {
+    if constexpr (AX == 0) return v3(S[3] * v.y + S[4] * v.z, S[1] * v.y + S[5] * v.z, S[5] * v.y + S[2] * v.z);
+    else if constexpr (AX == 1) return v3(S[0] * v.x + S[4] * v.z, S[3] * v.x + S[5] * v.z, S[4] * v.x + S[2] * v.z);
+    else if constexpr (AX == 2) return v3(S[0] * v.x + S[3] * v.y, S[3] * v.x + S[1] * v.y, S[4] * v.x + S[5] * v.y);
+    else return sym_mul(S, v);
+}
+template <int AX>
+__device__ __forceinline__ V3<float> mul_z(const M3<float>& B, V3<float> v) {
+    if constexpr (AX == 0)
+        return v3(B.m[1] * v.y + B.m[2] * v.z, B.m[4] * v.y + B.m[5] * v.z, B.m[7] * v.y + B.m[8] * v.z);
+    else if constexpr (AX == 1)
+        return v3(B.m[0] * v.x + B.m[2] * v.z, B.m[3] * v.x + B.m[5] * v.z, B.m[6] * v.x + B.m[8] * v.z);
+    else if constexpr (AX == 2)
+        return v3(B.m[0] * v.x + B.m[1] * v.y, B.m[3] * v.x + B.m[4] * v.y, B.m[6] * v.x + B.m[7] * v.y);
+    else return mul(B, v);
+}
+template <int AX>
+__device__ __forceinline__ V3<float> mulT_z(const M3<float>& B, V3<float> v) {
+    if constexpr (AX == 0)
+        return v3(B.m[3] * v.y + B.m[6] * v.z, B.m[4] * v.y + B.m[7] * v.z, B.m[5] * v.y + B.m[8] * v.z);
+    else if constexpr (AX == 1)
+        return v3(B.m[0] * v.x + B.m[6] * v.z, B.m[1] * v.x + B.m[7] * v.z, B.m[2] * v.x + B.m[8] * v.z);
+    else if constexpr (AX == 2)
+        return v3(B.m[0] * v.x + B.m[3] * v.y, B.m[1] * v.x + B.m[4] * v.y, B.m[2] * v.x + B.m[5] * v.y);
+    else return mulT(B, v);
+}
+
 template <bool KEEP, int AX>
 __device__ __forceinline__ JRot<AX> joint_rot(const BodyConst& C, const BodyMem& m) {
     if constexpr (AX >= 0) {
@@ -395,57 +424,92 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyC
     }
 }
 
-// Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
-// then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D.
-template <bool KEEP, int AX, int OF>
-__device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMem& m, bool has_carry,
-                                           Art<float>& carry, V3<float>& cpn, V3<float>& cpf) {
-    const V3<float> r = C.r;
-    Art<float> IA;
-    body_inertia(C, IA);
-    V3<float> pAn = m.x0, pAf = m.x1;
-    if (has_carry) {
-#pragma unroll
-        for (int t = 0; t < 6; ++t) IA.A[t] += carry.A[t];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) IA.B[t] += carry.B[t];
-#pragma unroll
-        for (int t = 0; t < 6; ++t) IA.C[t] += carry.C[t];
-        pAn = pAn + cpn;
-        pAf = pAf + cpf;
-    }
-    const V3<float> ua = symcol_ax<AX>(C, IA.A);
-    const V3<float> ul = btcol_ax<AX>(C, IA.B);
-    const float invD = sc_rcp(dot_ax<AX>(C, ua) + C.arm);
-    const float u = tau - dot_ax<AX>(C, pAn);
-    const float U[6] = {ua.x, ua.y, ua.z, ul.x, ul.y, ul.z};
+// The joint projection of an articulated inertia IA of a body (Featherstone's U = IA S,
+// D = S^T U + armature, Ia = IA - U U^T / D). For a body without children it depends on the
+// model only, so a rollout computes it once for the chain leaves.
+struct ArtProj {
     Art<float> Ia;
-    Ia.A[0] = IA.A[0] - U[0] * U[0] * invD;
-    Ia.A[1] = IA.A[1] - U[1] * U[1] * invD;
-    Ia.A[2] = IA.A[2] - U[2] * U[2] * invD;
-    Ia.A[3] = IA.A[3] - U[0] * U[1] * invD;
-    Ia.A[4] = IA.A[4] - U[0] * U[2] * invD;
-    Ia.A[5] = IA.A[5] - U[1] * U[2] * invD;
+    V3<float> ua, ul, x0, x1;  // U (angular, linear) and U / D
+    float invD;
+};
+
+template <int AX>
+__device__ __forceinline__ void art_project(const BodyConst& C, const Art<float>& IA, ArtProj& P) {
+    P.ua = symcol_ax<AX>(C, IA.A);
+    P.ul = btcol_ax<AX>(C, IA.B);
+    P.invD = sc_rcp(dot_ax<AX>(C, P.ua) + C.arm);
+    // x = U / D; Ia = IA - U x^T
+    P.x0 = P.invD * P.ua;
+    P.x1 = P.invD * P.ul;
+    const V3<float> ua = P.ua, ul = P.ul, x0 = P.x0, x1 = P.x1;
+    P.Ia.A[0] = IA.A[0] - ua.x * x0.x;
+    P.Ia.A[1] = IA.A[1] - ua.y * x0.y;
+    P.Ia.A[2] = IA.A[2] - ua.z * x0.z;
+    P.Ia.A[3] = IA.A[3] - ua.x * x0.y;
+    P.Ia.A[4] = IA.A[4] - ua.x * x0.z;
+    P.Ia.A[5] = IA.A[5] - ua.y * x0.z;
+    const float U[3] = {ua.x, ua.y, ua.z}, X1[3] = {x1.x, x1.y, x1.z};
 #pragma unroll
     for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
-        for (int j2 = 0; j2 < 3; ++j2) Ia.B[3 * i2 + j2] = IA.B[3 * i2 + j2] - U[i2] * U[3 + j2] * invD;
-    Ia.C[0] = IA.C[0] - U[3] * U[3] * invD;
-    Ia.C[1] = IA.C[1] - U[4] * U[4] * invD;
-    Ia.C[2] = IA.C[2] - U[5] * U[5] * invD;
-    Ia.C[3] = IA.C[3] - U[3] * U[4] * invD;
-    Ia.C[4] = IA.C[4] - U[3] * U[5] * invD;
-    Ia.C[5] = IA.C[5] - U[4] * U[5] * invD;
-    const float ud = u * invD;
+        for (int j2 = 0; j2 < 3; ++j2) P.Ia.B[3 * i2 + j2] = IA.B[3 * i2 + j2] - U[i2] * X1[j2];
+    P.Ia.C[0] = IA.C[0] - ul.x * x1.x;
+    P.Ia.C[1] = IA.C[1] - ul.y * x1.y;
+    P.Ia.C[2] = IA.C[2] - ul.z * x1.z;
+    P.Ia.C[3] = IA.C[3] - ul.x * x1.y;
+    P.Ia.C[4] = IA.C[4] - ul.x * x1.z;
+    P.Ia.C[5] = IA.C[5] - ul.y * x1.z;
+}
+
+template <int AX>
+__device__ __forceinline__ ArtProj leaf_projection(const BodyConst& C) {
+    Art<float> IA;
+    body_inertia(C, IA);
+    ArtProj P;
+    art_project<AX>(C, IA, P);
+    return P;
+}
+
+// Pass 2 of body b: its articulated inertia (own + `carry` from its child when has_carry),
+// then the carry to its parent; m.x0/x1/uu become U_ang/D, U_lin/D, u/D. LEAF: the body
+// has no child and `leaf` holds its projection.
+template <bool KEEP, int AX, int OF, bool LEAF = false>
+__device__ __forceinline__ void body_pass2(const BodyConst& C, float tau, BodyMem& m, bool has_carry,
+                                           Art<float>& carry, V3<float>& cpn, V3<float>& cpf,
+                                           const ArtProj* leaf = nullptr) {
+    const V3<float> r = C.r;
+    V3<float> pAn = m.x0, pAf = m.x1;
+    ArtProj Pj;
+    if constexpr (LEAF) {
+        Pj = *leaf;
+    } else {
+        Art<float> IA;
+        body_inertia(C, IA);
+        if (has_carry) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t) IA.A[t] += carry.A[t];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) IA.B[t] += carry.B[t];
+#pragma unroll
+            for (int t = 0; t < 6; ++t) IA.C[t] += carry.C[t];
+            pAn = pAn + cpn;
+            pAf = pAf + cpf;
+        }
+        art_project<AX>(C, IA, Pj);
+    }
+    const Art<float>& Ia = Pj.Ia;
+    const float u = tau - dot_ax<AX>(C, pAn);
+    const float ud = u * Pj.invD;
     const M3<float>& Bm = *reinterpret_cast<const M3<float>*>(Ia.B);
-    const V3<float> pan = pAn + sym_mul(Ia.A, m.cw) + mul(Bm, m.cv) + ud * ua;
-    const V3<float> paf = pAf + mulT(Bm, m.cw) + sym_mul(Ia.C, m.cv) + ud * ul;
+    // c = (cw, cv) has a zero component AX (it is a cross product with the joint axis)
+    const V3<float> pan = pAn + sym_mul_z<AX>(Ia.A, m.cw) + mul_z<AX>(Bm, m.cv) + ud * Pj.ua;
+    const V3<float> paf = pAf + mulT_z<AX>(Bm, m.cw) + sym_mul_z<AX>(Ia.C, m.cv) + ud * Pj.ul;
     const JRot<AX> J = joint_rot<KEEP, AX>(C, m);
     jart_to_parent<AX, OF>(Ia, J, r, carry);
     cpf = jrot(J, paf);
     cpn = add_rcross<OF>(jrot(J, pan), r, cpf, 1.f);
-    m.x0 = invD * ua;
-    m.x1 = invD * ul;
+    m.x0 = Pj.x0;
+    m.x1 = Pj.x1;
     m.uu = ud;
 }
 
@@ -542,6 +606,9 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         bc0 = load_body(M, 0);
     }
     auto body = [&](int j) -> BodyConst { return KEEP ? bc[KEEP ? j : 0] : load_body(M, b0 + j); };
+    // under the x, y, y plan every chain has 3 bodies: the calf is the leaf
+    ArtProj leafp;
+    if constexpr (AXP == AXP_XYY) leafp = leaf_projection<chain_axis<AXP, 2>()>(bc[2]);
     auto base = [&]() -> BodyConst { return KEEP ? bc0 : load_body(M, 0); };
     int kcur = -1;
     // segment k = floor(h (nk - 1) / H) and its remainder rem = h (nk - 1) - k H, advanced
@@ -611,7 +678,12 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
         static_for<0, LMAX>([&](auto ic) {
             constexpr int j = LMAX - 1 - decltype(ic)::value;
-            if (j < len) body_pass2<KEEP, chain_axis<AXP, j>(), chain_offset<AXP, j>()>(body(j), tau[j], mem[j], j < len - 1, carry, cpn, cpf);
+            if constexpr (AXP == AXP_XYY && j == 2)
+                body_pass2<KEEP, chain_axis<AXP, j>(), chain_offset<AXP, j>(), true>(body(j), tau[j], mem[j], false,
+                                                                                    carry, cpn, cpf, &leafp);
+            else if (j < len)
+                body_pass2<KEEP, chain_axis<AXP, j>(), chain_offset<AXP, j>()>(body(j), tau[j], mem[j], j < len - 1,
+                                                                              carry, cpn, cpf);
         });
         if (BRANCH) {
             // arms meet at the branch body: own + partner (lanes 2 <-> 3), identical on both
