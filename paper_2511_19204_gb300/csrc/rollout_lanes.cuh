@@ -253,6 +253,28 @@ __device__ __forceinline__ BodyConst load_body(const DevModel<float>& M, int b) 
     return C;
 }
 
+// Pins a loop-invariant value to a register: the empty asm makes it opaque, so the
+// compiler keeps it instead of recomputing or reloading it inside the step loop.
+__device__ __forceinline__ void pin(float& x) { asm volatile("" : "+f"(x)); }
+__device__ __forceinline__ void pin(V3<float>& v) {
+    pin(v.x);
+    pin(v.y);
+    pin(v.z);
+}
+__device__ __forceinline__ void pin(BodyConst& C) {
+    pin(C.a);
+    pin(C.r);
+    pin(C.mc);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) pin(C.Ao[t]);
+    pin(C.m);
+    pin(C.arm);
+    pin(C.kp);
+    pin(C.kd);
+    pin(C.tmax);
+    pin(C.qinit);
+}
+
 // Axis-vector operations with a = the joint axis (component AX for a coordinate axis).
 template <int AX>
 __device__ __forceinline__ V3<float> add_ax(const BodyConst& C, V3<float> v, float x) {  // v + x a
@@ -467,6 +489,17 @@ __device__ __forceinline__ ArtProj leaf_projection(const BodyConst& C) {
     body_inertia(C, IA);
     ArtProj P;
     art_project<AX>(C, IA, P);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) pin(P.Ia.A[t]);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) pin(P.Ia.B[t]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) pin(P.Ia.C[t]);
+    pin(P.ua);
+    pin(P.ul);
+    pin(P.x0);
+    pin(P.x1);
+    pin(P.invD);
     return P;
 }
 
@@ -602,8 +635,12 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
     BodyConst bc0;
     if (KEEP) {
 #pragma unroll
-        for (int j = 0; j < LMAX; ++j) bc[j] = load_body(M, j < len ? b0 + j : b0);
+        for (int j = 0; j < LMAX; ++j) {
+            bc[j] = load_body(M, j < len ? b0 + j : b0);
+            pin(bc[j]);
+        }
         bc0 = load_body(M, 0);
+        pin(bc0);
     }
     auto body = [&](int j) -> BodyConst { return KEEP ? bc[KEEP ? j : 0] : load_body(M, b0 + j); };
     // under the x, y, y plan every chain has 3 bodies: the calf is the leaf

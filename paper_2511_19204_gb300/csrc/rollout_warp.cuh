@@ -30,6 +30,30 @@ struct LaneConst {
     bool body, joint;
 };
 
+// Pins a loop-invariant value to a register (an opaque empty asm), so the compiler keeps
+// it across the step loop instead of reloading or recomputing it each step.
+__device__ __forceinline__ void pin_r(float& x) { asm volatile("" : "+f"(x)); }
+__device__ __forceinline__ void pin_r(double& x) { asm volatile("" : "+d"(x)); }
+template <typename T>
+__device__ __forceinline__ void pin_lane_const(LaneConst<T>& L) {
+    pin_r(L.a.x);
+    pin_r(L.a.y);
+    pin_r(L.a.z);
+    pin_r(L.r.x);
+    pin_r(L.r.y);
+    pin_r(L.r.z);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pin_r(L.Ao[k]);
+    pin_r(L.mc.x);
+    pin_r(L.mc.y);
+    pin_r(L.mc.z);
+    pin_r(L.m);
+    pin_r(L.arm);
+    pin_r(L.kp);
+    pin_r(L.kd);
+    pin_r(L.tmax);
+}
+
 template <typename T>
 __device__ __forceinline__ void load_lane_const(const DevModel<T>& M, int b, LaneConst<T>& L) {
     L.body = b < M.nb;
@@ -376,11 +400,13 @@ __device__ __forceinline__ void store_lane_state(const DevModel<T>& M, const Lan
 // sum on every lane. x0: initial state [nx] (global, FP32 or FP64). xf: optional state
 // after the last step simulated.
 template <typename T, int G, typename XT>
-__device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>& L, int gl,
+__device__ __noinline__ T warp_rollout(const DevModel<T>& M, const LaneConst<T>& Lin, int gl,
                                           const XT* __restrict__ x0, const float* __restrict__ knots, int H,
                                           int nsteps, int nk, T dt, T dtk, T* __restrict__ contrib,
                                           XT* __restrict__ xf) {
     const int nj = M.nb - 1;
+    LaneConst<T> L = Lin;
+    pin_lane_const(L);
     LaneState<T> S;
     load_lane_state(M, L, gl, x0, S);
     const V3<T> p_start = S.p;

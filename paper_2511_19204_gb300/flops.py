@@ -29,16 +29,20 @@ With the modular cost of Sec. IV-A on (any of its weights non-zero), in addition
   per base: height term 3, R^T R_des 54, rotation angle (vee 3, norm 6, trace 3,
   arctangent 1), theta^2 term 2, reduction 3                                      75
   (the terminal term, ~15 flops per rollout, is not counted per step)
-Quadrupeds whose chains turn about +x, +y, +y run the axis-specialised kernel, which
-applies joint rotations to two components. Per joint body it evaluates 666 instead of
-961: joint rotation 1 (sincos only), pass 1 61 (composition 18, origin 18, angular
-velocity 7, linear velocity 18), velocity product 4, pass 2 390 (U, D, u 3, congruence
-210 with 108 for the rotations, force transform 24, the rest as above), pass 3 44
-(transform 30, joint acceleration 13, update 1); the other items as above. The thigh and
-calf joints of that layout also sit on one coordinate axis of their parent (r = rho e_k),
-so products with r touch two components: 106 fewer per body (origin 6, linear velocity
-10, reference-point shift of the congruence 32, force transform 16, acceleration
-transform 22), 560 per body.
+Quadrupeds whose chains turn about +x, +y, +y (thigh joint along y from the hip, knee
+along z from the thigh) run the specialised chain kernel, which applies joint rotations
+to two components, shifts reference points along one axis, skips the zero component of
+the velocity product, reuses U / D in the projection and computes the leaf's projection
+once per rollout. Per step:
+  hip   (x axis, any offset, has a child): Hermite + PD 55, sincos 1, pass 1 61
+        (composition 18, origin 18, angular velocity 7, linear velocity 18), velocity
+        product 4, bias 78, child accumulation 27, pass 2 346 (D and u 3, projection 48,
+        bias products and update 61, congruence 210 = rotations 108 + shift 102, force
+        transform 24), pass 3 44, Euler 4, effort 2                                    622
+  thigh (y axis, offset along y, has a child): as the hip but pass 1 41 (origin 6,
+        linear velocity 10), shift 32, force transform 16, pass 3 36                  516
+  calf  (y axis, offset along z, leaf): as the thigh without the child accumulation,
+        D and the projection (u 1 instead of 3 + 48)                                  439
 """
 from __future__ import annotations
 
@@ -49,8 +53,9 @@ MOD_JOINT = 4
 MOD_CONTACT = 5 + 8 + 4
 MOD_BASE = 3 + 54 + 3 + 6 + 3 + 1 + 2 + 3
 MOD_WEIGHTS = ("w_h", "w_orient", "w_q", "w_cvel", "w_cforce", "w_term")
-PER_JOINT_XYY = 55 + 1 + 61 + 4 + 78 + (3 + 63 + 66 + 24 + 210 + 24) + 27 + 44 + 4 + 2
-PER_JOINT_XYY_AXIAL = PER_JOINT_XYY - (12 + 8 + 70 + 8 + 8)
+PER_JOINT_XYY_HIP = 55 + 1 + 61 + 4 + 78 + 27 + (3 + 48 + 61 + 210 + 24) + 44 + 4 + 2
+PER_JOINT_XYY_THIGH = 55 + 1 + 41 + 4 + 78 + 27 + (3 + 48 + 61 + 140 + 16) + 36 + 4 + 2
+PER_JOINT_XYY_CALF = 55 + 1 + 41 + 4 + 78 + 0 + (1 + 0 + 61 + 140 + 16) + 36 + 4 + 2
 
 
 def axis_plan_xyy(model) -> bool:
@@ -82,7 +87,7 @@ def flops_per_step(model, contacts_active=None, mapping_chain=True) -> int:
     axes of x, y, y quadrupeds)."""
     nc = model.nc if contacts_active is None else contacts_active
     if mapping_chain and axis_plan_xyy(model):
-        joints = 4 * PER_JOINT_XYY + 8 * PER_JOINT_XYY_AXIAL
+        joints = 4 * (PER_JOINT_XYY_HIP + PER_JOINT_XYY_THIGH + PER_JOINT_XYY_CALF)
     else:
         joints = PER_JOINT * model.nj
     f = joints + PER_CONTACT * nc + PER_BASE
