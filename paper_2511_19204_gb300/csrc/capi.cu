@@ -416,9 +416,6 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it], s, cudaEventRecordExternal);
     if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it + 1], s, cudaEventRecordExternal);
-    if (e == cudaSuccess)
-        e = launch_weights_average(c->d_costs, c->d_knots, c->N, c->E, c->lambda, c->normalize, nullptr, c->d_zq,
-                                   c->d_partial, c->d_info, s);
     if (e == cudaSuccess) {
         FinalizeArgs f;
         f.partial = c->d_partial;
@@ -436,7 +433,7 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
         f.mean_out = c->d_mean;
         f.best_out = c->d_best;
         f.result = c->d_result;
-        e = launch_finalize(f, s);
+        e = launch_weights_finalize(f, c->d_zq, c->d_partial, c->N, c->lambda, c->normalize, s);
     }
     return e;
 }
@@ -1059,7 +1056,7 @@ mppi_status mppi_model_info(const mppi_model* m, int32_t* o) {
 
 size_t mppi_ctx_device_bytes(const mppi_ctx* c) { return c ? c->dev_bytes : 0; }
 
-int32_t mppi_ctx_kernels_per_solve(const mppi_ctx* c) { return c ? 1 + 4 * c->iters : 0; }
+int32_t mppi_ctx_kernels_per_solve(const mppi_ctx* c) { return c ? 1 + 3 * c->iters : 0; }
 
 mppi_status mppi_ctx_set_fp64_check(mppi_ctx* c, int32_t on) {
     if (!c) return MPPI_ERR_INVALID_ARG;

@@ -26,7 +26,7 @@ struct DevSolve {
     double best_cost;
     int32_t best_index, best_iter, status, pad;
     uint32_t iter_counter;   // Philox counter word 2 of the solve's first iteration
-    uint32_t pad2;
+    uint32_t blocks_done;    // blocks of the running weights launch that finished (last resets)
     uint32_t dev_error;      // DEV_ERR_* bits from bounded device waits
     uint32_t pad3;
 };
@@ -101,6 +101,10 @@ struct FinalizeArgs {
     mppi_result* result;
 };
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+// chunk weights + partial sums with the finalize run by the last block to finish (one
+// launch per iteration); zq and partial as in launch_weights_average
+cudaError_t launch_weights_finalize(const FinalizeArgs& a, double* zq, double* partial, int N, double lambda,
+                                    int normalize, cudaStream_t s);
 cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* best_out, int E, cudaStream_t s);
 cudaError_t launch_fast_math(int n, const float* x, const float* y, float* out, cudaStream_t s);
 cudaError_t launch_philox_words(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s);

@@ -137,6 +137,38 @@ cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Weights and chunk partial sums, then the iteration's finalize in the block that
+// finishes last (each block fences its writes and counts itself in DevSolve::blocks_done;
+// the last one resets the counter): one launch per iteration instead of two, the same
+// sums in the same order.
+constexpr int WF_THREADS = 256;
+
+__global__ void __launch_bounds__(WF_THREADS) weights_finalize_kernel(FinalizeArgs f, double* zq, double* partial,
+                                                                       int N, double lambda, int normalize) {
+    __shared__ int s_last;
+    chunk_weights_average(f.costs, f.knots, N, f.E, lambda, normalize, blockIdx.x, blockIdx.y, nullptr, zq, partial,
+                          f.info);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y;
+        s_last = atomicAdd(&f.solve->blocks_done, 1u) == total - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    finalize_iteration(f);
+    if (threadIdx.x == 0) f.solve->blocks_done = 0;
+}
+
+cudaError_t launch_weights_finalize(const FinalizeArgs& a, double* zq, double* partial, int N, double lambda,
+                                    int normalize, cudaStream_t s) {
+    const dim3 grid(num_chunks(N), (a.E + WF_THREADS - 1) / WF_THREADS);
+    if (grid.x == 0) return cudaSuccess;
+    weights_finalize_kernel<<<grid, WF_THREADS, 0, s>>>(a, zq, partial, N, lambda, normalize);
+    return cudaGetLastError();
+}
+
 __global__ void solve_begin_kernel(DevSolve* solve, const float* nominal, float* best_out, int E) {
     if (threadIdx.x == 0) {
         solve->best_cost = INFINITY;
