@@ -188,9 +188,41 @@ def cpu_baseline(n_samples: int):
     oracle.solve_problem(p, nthreads=cores)
     dt = time.perf_counter() - t0
     units = p.n * p.horizon * p.iters
+    # the same oracle on one thread, on an eighth of the sample
+    p1 = synth.scale_quadruped(n=max(n_samples // 8, 1))
+    t1 = time.perf_counter()
+    oracle.solve_problem(p1, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{p.n} of 8192 samples, all {p.iters} iterations x {p.horizon} steps, one solve "
-                      f"({dt:.2f} s wall, FP64 C oracle, {cores} threads)"}
+                      f"({dt:.2f} s wall, FP64 C oracle, {cores} threads)",
+            "single_thread_value": p1.n * p1.horizon * p1.iters / dt1,
+            "single_thread_sample": f"{p1.n} samples, one solve, one thread ({dt1:.2f} s wall)"}
+
+
+def oracle_parity(mppi, synth, mapping, block):
+    """Error of one full-size solve of the headline workload against the FP64 oracle on
+    the same inputs (fresh controller, the problem's nominal as warm start, counter 0):
+    the largest relative error over the updated control points, the best cost's relative
+    error and whether the best sample agrees. Not timed."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    p = synth.scale_quadruped()
+    c = mppi.Controller.from_problem(mppi.Model(p.model), p, mapping=mapping, block=block)
+    nom32 = p.nominal.astype(np.float32)
+    mean, best, info = c.solve(p.state, warm=nom32)
+    t0 = time.perf_counter()
+    ref = oracle.solve(p.model, p.n, p.nk, p.horizon, p.iters, p.dt, p.lam, p.sigma, p.state,
+                       nom32.astype(np.float64), seed=p.seed)
+    dt = time.perf_counter() - t0
+    err = float(np.max(np.abs(mean - ref["mean"]) / np.maximum(1.0, np.abs(ref["mean"]))))
+    return {"workload": "the headline workload, one solve at full size", "oracle_s": dt,
+            "mean_knots_max_rel_err": err,
+            "best_cost_rel_err": abs(info["best_cost"] - ref["best_cost"]) / abs(ref["best_cost"]),
+            "best_index_equal": bool(info["best_index"] == ref["best_index"]
+                                     and info["best_iter"] == ref["best_iter"]),
+            "tolerance": 1e-3}
 
 
 def run_reference(args, rank, world):
@@ -621,6 +653,10 @@ def run_ours(args, rank, world, local):
             line["serving"] = {"error": repr(exc)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_samples)
+        try:
+            line["oracle_parity"] = oracle_parity(mppi, synth, info["mapping"], info["block"])
+        except Exception as exc:  # reported, never silently dropped
+            line["oracle_parity"] = {"error": repr(exc)}
     print(json.dumps(line), flush=True)
     del np
     return 0

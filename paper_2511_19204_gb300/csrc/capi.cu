@@ -87,7 +87,8 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
                 P.len[l] = L;
                 if (xyy)
                     xyy = axis_is(d, P.b0[l], 0) && axis_is(d, P.b0[l] + 1, 1) && axis_is(d, P.b0[l] + 2, 1) &&
-                          offset_along(d, P.b0[l] + 1, 1) && offset_along(d, P.b0[l] + 2, 2);
+                          d.jpos[3 * P.b0[l] + 2] == 0.0 && offset_along(d, P.b0[l] + 1, 1) &&
+                          offset_along(d, P.b0[l] + 2, 2);
             }
             if (xyy) P.axis_plan = AXP_XYY;
             return P;

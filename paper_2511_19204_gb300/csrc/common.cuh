@@ -153,8 +153,8 @@ constexpr int TOPO_HUMANOID = 2;    // 2 chains of <= 6 off the base + a branch 
 
 // Axis plans of the lanes-per-chain quadruped: AXP_GENERIC, any unit axes; AXP_XYY, the
 // usual leg layout: every chain's joints turn about +x, +y, +y (hip abduction, hip and
-// knee flexion), the thigh joint sits along y from the hip and the knee along z from the
-// thigh, which the passes exploit at compile time.
+// knee flexion), the hip sits in the base's xy-plane, the thigh joint along y from the
+// hip and the knee along z from the thigh, which the passes exploit at compile time.
 constexpr int AXP_GENERIC = 0;
 constexpr int AXP_XYY = 1;
 

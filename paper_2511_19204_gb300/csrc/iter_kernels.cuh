@@ -141,7 +141,7 @@ cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
 // finishes last (each block fences its writes and counts itself in DevSolve::blocks_done;
 // the last one resets the counter): one launch per iteration instead of two, the same
 // sums in the same order.
-constexpr int WF_THREADS = 256;
+constexpr int WF_THREADS = 1024;
 
 __global__ void __launch_bounds__(WF_THREADS) weights_finalize_kernel(FinalizeArgs f, double* zq, double* partial,
                                                                        int N, double lambda, int normalize) {

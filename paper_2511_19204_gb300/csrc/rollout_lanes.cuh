@@ -28,7 +28,7 @@ __host__ __device__ constexpr int chain_axis() {
 }
 template <int AXP, int J>
 __host__ __device__ constexpr int chain_offset() {
-    return AXP == AXP_XYY ? (J == 0 ? -1 : (J == 1 ? 1 : 2)) : -1;
+    return AXP == AXP_XYY ? (J == 0 ? 3 : (J == 1 ? 1 : 2)) : -1;  // 3: the hip offset lies in the xy-plane
 }
 
 // f(std::integral_constant<int, J>) for J = B .. E - 1, unrolled at compile time.
@@ -158,11 +158,17 @@ template <int OF>
 __device__ __forceinline__ float rlen(V3<float> r) {
     return OF == 0 ? r.x : (OF == 1 ? r.y : r.z);
 }
+// r x u for r in the xy-plane (OF == 3: r.z == 0), the products with r.z left out
+__device__ __forceinline__ V3<float> cross_rxy(V3<float> r, V3<float> u) {
+    return v3(r.y * u.z, -(r.x * u.z), r.x * u.y - r.y * u.x);
+}
 // v + s (r x u), s = +1 or -1
 template <int OF>
 __device__ __forceinline__ V3<float> add_rcross(V3<float> v, V3<float> r, V3<float> u, float sgn) {
     if constexpr (OF < 0) {
         return sgn > 0.f ? v + cross(r, u) : v - cross(r, u);
+    } else if constexpr (OF == 3) {
+        return sgn > 0.f ? v + cross_rxy(r, u) : v - cross_rxy(r, u);
     } else {
         const float rho = sgn * rlen<OF>(r);
         float o[3] = {v.x, v.y, v.z};
@@ -177,6 +183,8 @@ template <int OF>
 __device__ __forceinline__ V3<float> rot_r(const M3<float>& R, V3<float> r) {
     if constexpr (OF < 0) {
         return mul(R, r);
+    } else if constexpr (OF == 3) {
+        return v3(R.m[0] * r.x + R.m[1] * r.y, R.m[3] * r.x + R.m[4] * r.y, R.m[6] * r.x + R.m[7] * r.y);
     } else {
         const float rho = rlen<OF>(r);
         return v3(R.m[OF] * rho, R.m[3 + OF] * rho, R.m[6 + OF] * rho);
@@ -189,6 +197,29 @@ __device__ __forceinline__ void art_shift_r(const float* A, const float* B, cons
                                             Art<float>& out) {
     if constexpr (OF < 0) {
         art_shift(A, B, C, r, out);
+    } else if constexpr (OF == 3) {
+        // as art_shift with every r x (.) and (.) x r formed without r.z
+        const V3<float> x0 = cross_rxy(r, v3(C[0], C[3], C[4])), x1 = cross_rxy(r, v3(C[3], C[1], C[5])),
+                        x2 = cross_rxy(r, v3(C[4], C[5], C[2]));
+        const float B2[9] = {B[0] + x0.x, B[1] + x1.x, B[2] + x2.x, B[3] + x0.y, B[4] + x1.y,
+                             B[5] + x2.y, B[6] + x0.z, B[7] + x1.z, B[8] + x2.z};
+        const V3<float> d0 = cross_rxy(r, v3(B[0], B[1], B[2]));
+        const V3<float> d1 = cross_rxy(r, v3(B[3], B[4], B[5]));
+        const V3<float> d2 = cross_rxy(r, v3(B[6], B[7], B[8]));
+        // f_i = (row i of B2) x r = -(r x row i)
+        const V3<float> f0 = cross_rxy(r, v3(B2[0], B2[1], B2[2]));
+        const V3<float> f1 = cross_rxy(r, v3(B2[3], B2[4], B2[5]));
+        const V3<float> f2 = cross_rxy(r, v3(B2[6], B2[7], B2[8]));
+        out.A[0] = A[0] + d0.x + f0.x;
+        out.A[1] = A[1] + d1.y + f1.y;
+        out.A[2] = A[2] + d2.z + f2.z;
+        out.A[3] = A[3] + d1.x + f0.y;
+        out.A[4] = A[4] + d2.x + f0.z;
+        out.A[5] = A[5] + d2.y + f1.z;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out.B[k] = B2[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out.C[k] = C[k];
     } else {
         const float rho = rlen<OF>(r);
         auto Cs = [&](int i, int j) -> float {
@@ -570,6 +601,26 @@ __device__ __forceinline__ SegKnots seg_knots(const float* __restrict__ knots, i
                     knots[((k + 1) * 2 + 1) * nj + j]};
 }
 
+// Power-basis form of one joint's Hermite segment (Eq. hermite_segment expanded in s, with
+// m = dtk v): q(s) = ((c3 s + c2) s + c1) s + c0, c0 = q0, c1 = m0,
+// c2 = 3 (q1 - q0) - 2 m0 - m1, c3 = -2 (q1 - q0) + m0 + m1; dq/dt = dq/ds / dtk. Formed
+// once per segment, evaluated in 5 fused multiply-adds per step.
+struct SegPoly {
+    float c0, c1, c2, c3;
+};
+
+__device__ __forceinline__ SegPoly seg_poly(const SegKnots& K, float dtk) {
+    const float m0 = dtk * K.v0, m1 = dtk * K.v1, dq = K.q1 - K.q0;
+    return SegPoly{K.q0, m0, fmaf(3.f, dq, -fmaf(2.f, m0, m1)), fmaf(-2.f, dq, m0 + m1)};
+}
+
+__device__ __forceinline__ float poly_pd(const BodyConst& C, const SegPoly& P, float s, float inv_dtk, float q,
+                                         float qd) {
+    const float qref = fmaf(fmaf(fmaf(P.c3, s, P.c2), s, P.c1), s, P.c0);
+    const float vref = fmaf(fmaf(3.f * P.c3, s, 2.f * P.c2), s, P.c1) * inv_dtk;
+    return sc_clamp(C.kp * (qref - q) + C.kd * (vref - qd), -C.tmax, C.tmax);
+}
+
 __device__ __forceinline__ float hermite_pd(const BodyConst& C, const SegKnots& K, float s, float dtk,
                                             float inv_dtk, float q, float qd) {
     const float q0 = K.q0, v0 = K.v0, q1 = K.q1, v1 = K.v1;
@@ -628,7 +679,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
     for (int l = 0; l < LANES; ++l)
         if (cb >= M.lane_b0[l] && cb < M.lane_b0[l] + M.lane_len[l]) cowner = l;
     if (BRANCH && cb == bb) cowner = 2;
-    SegKnots kc[KEEP ? LMAX : 1];
+    SegPoly kc[KEEP ? LMAX : 1];
     // short chains keep their bodies' constants (and the base's) in registers; long chains
     // re-read them from shared memory where they are used
     BodyConst bc[KEEP ? LMAX : 1];
@@ -663,14 +714,17 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             kcur = k;
 #pragma unroll
             for (int j = 0; j < (KEEP ? LMAX : 1); ++j)
-                if (j < len) kc[j] = seg_knots(knots, nj, k, b0 + j);
+                if (j < len) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
         }
         float tau[LMAX], taub = 0.f;
 #pragma unroll
-        for (int j = 0; j < LMAX; ++j)
-            tau[j] = j < len ? hermite_pd(body(j), KEEP ? kc[KEEP ? j : 0] : seg_knots(knots, nj, k, b0 + j), s, dtk,
-                                          inv_dtk, q[j], qd[j])
-                             : 0.f;
+        for (int j = 0; j < LMAX; ++j) {
+            if (KEEP)
+                tau[j] = j < len ? poly_pd(body(j), kc[KEEP ? j : 0], s, inv_dtk, q[j], qd[j]) : 0.f;
+            else
+                tau[j] = j < len ? hermite_pd(body(j), seg_knots(knots, nj, k, b0 + j), s, dtk, inv_dtk, q[j], qd[j])
+                                 : 0.f;
+        }
         if (on_branch) taub = hermite_pd(load_body(M, bb), seg_knots(knots, nj, k, bb), s, dtk, inv_dtk, qb, qdb);
         // ---- pass 1 ----
         B.R = quat_to_R(qw, qx, qy, qz);

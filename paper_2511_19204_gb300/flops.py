@@ -29,20 +29,22 @@ With the modular cost of Sec. IV-A on (any of its weights non-zero), in addition
   per base: height term 3, R^T R_des 54, rotation angle (vee 3, norm 6, trace 3,
   arctangent 1), theta^2 term 2, reduction 3                                      75
   (the terminal term, ~15 flops per rollout, is not counted per step)
-Quadrupeds whose chains turn about +x, +y, +y (thigh joint along y from the hip, knee
-along z from the thigh) run the specialised chain kernel, which applies joint rotations
-to two components, shifts reference points along one axis, skips the zero component of
-the velocity product, reuses U / D in the projection and computes the leaf's projection
-once per rollout. Per step:
-  hip   (x axis, any offset, has a child): Hermite + PD 55, sincos 1, pass 1 61
-        (composition 18, origin 18, angular velocity 7, linear velocity 18), velocity
-        product 4, bias 78, child accumulation 27, pass 2 346 (D and u 3, projection 48,
-        bias products and update 61, congruence 210 = rotations 108 + shift 102, force
-        transform 24), pass 3 44, Euler 4, effort 2                                    622
-  thigh (y axis, offset along y, has a child): as the hip but pass 1 41 (origin 6,
-        linear velocity 10), shift 32, force transform 16, pass 3 36                  516
+Quadrupeds whose chains turn about +x, +y, +y (hip in the base's xy-plane, thigh joint
+along y from the hip, knee along z from the thigh) run the specialised chain kernel, which
+applies joint rotations to two components, forms products with the offsets from their
+non-zero components only, skips the zero component of the velocity product, reuses U / D
+in the projection, computes the leaf's projection once per rollout and evaluates each
+setpoint from a power-basis form of its segment (formed once per segment). Per step:
+  hip   (x axis, offset in the xy-plane, has a child): setpoint + PD 20 (qref 6, vref 5,
+        PD 5, clamp 2, segment form amortised ~0), sincos 1, pass 1 51 (composition 18,
+        origin 12, angular velocity 7, linear velocity 14), velocity product 4, bias 78,
+        child accumulation 27, pass 2 306 (D and u 3, projection 48, bias products and
+        update 61, congruence 174 = rotations 108 + shift 66, force transform 20), pass 3
+        40, Euler 4, effort 2                                                        533
+  thigh (y axis, offset along y, has a child): pass 1 41 (origin 6, linear velocity
+        10), shift 32, force transform 16, pass 3 36, the rest as the hip               481
   calf  (y axis, offset along z, leaf): as the thigh without the child accumulation,
-        D and the projection (u 1 instead of 3 + 48)                                  439
+        D and the projection (u 1 instead of 3 + 48)                                  404
 """
 from __future__ import annotations
 
@@ -53,15 +55,15 @@ MOD_JOINT = 4
 MOD_CONTACT = 5 + 8 + 4
 MOD_BASE = 3 + 54 + 3 + 6 + 3 + 1 + 2 + 3
 MOD_WEIGHTS = ("w_h", "w_orient", "w_q", "w_cvel", "w_cforce", "w_term")
-PER_JOINT_XYY_HIP = 55 + 1 + 61 + 4 + 78 + 27 + (3 + 48 + 61 + 210 + 24) + 44 + 4 + 2
-PER_JOINT_XYY_THIGH = 55 + 1 + 41 + 4 + 78 + 27 + (3 + 48 + 61 + 140 + 16) + 36 + 4 + 2
-PER_JOINT_XYY_CALF = 55 + 1 + 41 + 4 + 78 + 0 + (1 + 0 + 61 + 140 + 16) + 36 + 4 + 2
+PER_JOINT_XYY_HIP = 20 + 1 + 51 + 4 + 78 + 27 + (3 + 48 + 61 + 174 + 20) + 40 + 4 + 2
+PER_JOINT_XYY_THIGH = 20 + 1 + 41 + 4 + 78 + 27 + (3 + 48 + 61 + 140 + 16) + 36 + 4 + 2
+PER_JOINT_XYY_CALF = 20 + 1 + 41 + 4 + 78 + 0 + (1 + 0 + 61 + 140 + 16) + 36 + 4 + 2
 
 
 def axis_plan_xyy(model) -> bool:
     """True when the model runs the axis-specialised chain kernel: a floating base with 4
-    chains of 3 bodies whose joint axes are exactly +x, +y, +y, with the thigh joint along
-    y from the hip and the knee along z from the thigh."""
+    chains of 3 bodies whose joint axes are exactly +x, +y, +y, with the hip in the base's
+    xy-plane, the thigh joint along y from the hip and the knee along z from the thigh."""
     import numpy as np
     if model.fixed_base or model.nb != 13:
         return False
@@ -72,6 +74,8 @@ def axis_plan_xyy(model) -> bool:
             return False
         if not (np.array_equal(model.axis[b0], ex) and np.array_equal(model.axis[b0 + 1], ey)
                 and np.array_equal(model.axis[b0 + 2], ey)):
+            return False
+        if model.jpos[b0][2] != 0.0:
             return False
         if model.jpos[b0 + 1][0] != 0.0 or model.jpos[b0 + 1][2] != 0.0:
             return False
