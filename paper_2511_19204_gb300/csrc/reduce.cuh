@@ -7,11 +7,12 @@
 //      number of finite costs (cheap; every block does it redundantly),
 //   2. forms the unnormalised weights e_n = exp(-S_hat_n / lambda) of its own samples in
 //      FP64 (every e_n <= 1 and the argmin's e is exactly 1, so nothing overflows),
-//   3. writes P_c[e] = sum_{n in c} e_n theta_{n,e} (FP64, increasing n) and, from the
-//      first element tile, z_c = sum e_n and q_c = sum e_n^2.
+//   3. writes P_c[e] = sum_{n in c} e_n theta_{n,e} (FP64) and, from the first element
+//      tile, z_c = sum e_n and q_c = sum e_n^2.
 // The iteration's finalize then forms z = sum_c z_c, lse = log z, ESS = z^2 / sum q_c and
-// the mean sum_c P_c[e] / z. Each sum runs in a fixed order, so results depend only on
-// AVG_CHUNK, never on the grid or on scheduling.
+// the mean sum_c P_c[e] / z. Each sum runs in a fixed order (interleaved accumulators and
+// balanced trees, since a long chain of dependent FP64 operations is slow on this part),
+// so results depend only on AVG_CHUNK, never on the block size, the grid or scheduling.
 #pragma once
 #include "internal.h"
 
@@ -115,64 +116,74 @@ __device__ __noinline__ void chunk_weights_average(const float* __restrict__ cos
     const MinMax mm = block_minmax(costs, N);
     const int n0 = c * AVG_CHUNK;
     const int cn = min(AVG_CHUNK, N - n0);
-    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-        const double e = mm.nfinite > 0 ? unnorm_weight(costs[n0 + i], mm, lambda, normalize) : 0.0;
-        s_e[i] = e;
-        if (e_out && ey == 0) e_out[n0 + i] = e;
+    for (int i = threadIdx.x; i < AVG_CHUNK; i += blockDim.x) {
+        const double e = (i < cn && mm.nfinite > 0) ? unnorm_weight(costs[n0 + i], mm, lambda, normalize) : 0.0;
+        s_e[i] = e;  // zero past the chunk's end
+        if (e_out && ey == 0 && i < cn) e_out[n0 + i] = e;
     }
     __syncthreads();
+    // FP64 latency is long on this part, so no sum is one long dependent chain: the knot
+    // partials use 8 accumulators (sample i into i mod 8, increasing i) combined as a
+    // balanced tree, and z, q a fixed pairwise tree over the 64 weights
     const int el = ey * blockDim.x + threadIdx.x;
     if (el < E) {
-        double acc = 0.0;
-#pragma unroll 16
-        for (int i = 0; i < cn; ++i) acc = fma(s_e[i], (double)knots[(size_t)(n0 + i) * E + el], acc);
-        partial[(size_t)c * E + el] = acc;
-    }
-    if (ey == 0 && threadIdx.x == 0) {
-        double z = 0.0, q = 0.0;
-        for (int i = 0; i < cn; ++i) {
-            z += s_e[i];
-            q = fma(s_e[i], s_e[i], q);
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i0 = 0; i0 < cn; i0 += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < cn) a[u] = fma(s_e[i0 + u], (double)knots[(size_t)(n0 + i0 + u) * E + el], a[u]);
         }
-        zq[2 * c] = z;
-        zq[2 * c + 1] = q;
-        if (c == 0) {
-            info->smin = mm.nfinite ? (double)mm.smin : NAN;
-            info->smax = mm.nfinite ? (double)mm.smax : NAN;
-            info->best = mm.best;
-            info->nfinite = mm.nfinite;
-            info->status = mm.nfinite ? MPPI_OK : MPPI_ERR_ALL_COSTS_NONFINITE;
+        partial[(size_t)c * E + el] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
+    if (ey == 0 && threadIdx.x < 32) {
+        const int t = threadIdx.x;
+        const double e0 = s_e[t], e1 = s_e[t + 32];
+        double z = e0 + e1, q = fma(e0, e0, e1 * e1);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            z += __shfl_down_sync(0xffffffffu, z, off);
+            q += __shfl_down_sync(0xffffffffu, q, off);
+        }
+        if (t == 0) {
+            zq[2 * c] = z;
+            zq[2 * c + 1] = q;
+            if (c == 0) {
+                info->smin = mm.nfinite ? (double)mm.smin : NAN;
+                info->smax = mm.nfinite ? (double)mm.smax : NAN;
+                info->best = mm.best;
+                info->nfinite = mm.nfinite;
+                info->status = mm.nfinite ? MPPI_OK : MPPI_ERR_ALL_COSTS_NONFINITE;
+            }
         }
     }
     __syncthreads();
 }
 
-constexpr int FIN_SPLIT = 8;   // interleaved sub-sums per total in the finalize
-constexpr int FIN_TILE = 128;  // elements per finalize tile
+constexpr int FIN_SPLIT = 16;  // interleaved sub-sums per element total in the finalize
+constexpr int FIN_TILE = 128;   // elements per finalize tile
 
-// Block-wide: z = sum_c z_c and q = sum_c q_c as FIN_SPLIT interleaved sub-sums (chunks
-// s, s + FIN_SPLIT, ... in increasing order) combined in sub-sum order; every thread
-// receives the totals. Needs blockDim.x >= 2 * FIN_SPLIT.
+// sum of 16 values in a fixed balanced tree
+__device__ __forceinline__ double tree16(const double* v, int stride) {
+    double l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l[i] = v[(2 * i) * stride] + v[(2 * i + 1) * stride];
+    return ((l[0] + l[1]) + (l[2] + l[3])) + ((l[4] + l[5]) + (l[6] + l[7]));
+}
+
+// Block-wide: z = sum_c z_c and q = sum_c q_c. One warp per total: lane l sums chunks
+// c = l, l + 32, ... in increasing order, then a fixed shuffle tree. Every thread receives
+// the totals. Needs blockDim.x >= 64.
 __device__ __forceinline__ void block_total_zq(const double* __restrict__ zq, int nchunks, double* z, double* q) {
-    __shared__ double s_part[2 * FIN_SPLIT];
     __shared__ double s_tot[2];
     const int t = threadIdx.x;
-    if (t < 2 * FIN_SPLIT) {
-        const int sidx = t % FIN_SPLIT, which = t / FIN_SPLIT;
+    if (t < 64) {
+        const int lane = t & 31, which = t >> 5;
         double acc = 0.0;
-#pragma unroll 8
-        for (int c = sidx; c < nchunks; c += FIN_SPLIT) acc += zq[2 * c + which];
-        s_part[t] = acc;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double a = 0.0, b = 0.0;
-        for (int sidx = 0; sidx < FIN_SPLIT; ++sidx) {
-            a += s_part[sidx];
-            b += s_part[FIN_SPLIT + sidx];
-        }
-        s_tot[0] = a;
-        s_tot[1] = b;
+#pragma unroll 4
+        for (int c = lane; c < nchunks; c += 32) acc += zq[2 * c + which];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) s_tot[which] = acc;
     }
     __syncthreads();
     *z = s_tot[0];
@@ -221,7 +232,7 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
     z = s_z;
     const bool last = a.iter == a.iters - 1;
     // chunk totals: FIN_SPLIT interleaved sub-sums per element (chunks c = s, s + FIN_SPLIT,
-    // ... in increasing order) spread over the block, then combined in sub-sum order
+    // ... in increasing order) spread over the block, then combined by a balanced tree
     __shared__ double s_sub[FIN_SPLIT * FIN_TILE];
     for (int e0 = 0; e0 < a.E; e0 += FIN_TILE) {
         if (ok)
@@ -229,7 +240,7 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
                 const int sidx = task / FIN_TILE, el = task - sidx * FIN_TILE, e = e0 + el;
                 double acc = 0.0;
                 if (e < a.E) {
-#pragma unroll 8
+#pragma unroll 4
                     for (int c = sidx; c < a.nchunks; c += FIN_SPLIT) acc += a.partial[(size_t)c * a.E + e];
                 }
                 s_sub[task] = acc;
@@ -238,11 +249,7 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
         for (int el = t; el < FIN_TILE && e0 + el < a.E; el += blockDim.x) {
             const int e = e0 + el;
             float m = a.nominal[e];
-            if (ok) {
-                double tot = 0.0;
-                for (int sidx = 0; sidx < FIN_SPLIT; ++sidx) tot += s_sub[sidx * FIN_TILE + el];
-                m = (float)(tot / z);
-            }
+            if (ok) m = (float)(tree16(s_sub + el, FIN_TILE) / z);
             if (s_update) a.best_out[e] = a.knots[(size_t)inf.best * a.E + e];
             if (last) a.mean_out[e] = m;
             a.nominal[e] = m;
