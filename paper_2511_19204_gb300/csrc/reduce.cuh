@@ -127,11 +127,18 @@ __device__ __noinline__ void chunk_weights_average(const float* __restrict__ cos
     // balanced tree, and z, q a fixed pairwise tree over the 64 weights
     const int el = ey * blockDim.x + threadIdx.x;
     if (el < E) {
+        // all AVG_CHUNK loads are independent and issued together; past the chunk's end
+        // (the last, ragged chunk) the index is clamped and the weight is 0, so the term
+        // adds nothing
+        const float* kp = knots + (size_t)n0 * E + el;
         double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int i0 = 0; i0 < cn; i0 += 8) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (i0 + u < cn) a[u] = fma(s_e[i0 + u], (double)knots[(size_t)(n0 + i0 + u) * E + el], a[u]);
+        for (int i0 = 0; i0 < AVG_CHUNK; i0 += 8) {
+            float kv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) kv[u] = kp[(size_t)min(i0 + u, cn - 1) * E];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = fma(s_e[i0 + u], (double)kv[u], a[u]);
         }
         partial[(size_t)c * E + el] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
@@ -202,18 +209,14 @@ __device__ __forceinline__ double chunk_total(const double* __restrict__ partial
 // iteration the outputs, the resident warm start and the noise counter.
 __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
     __shared__ int s_update;
-    __shared__ double s_z;
     const int t = threadIdx.x;
     DevIterInfo inf = *a.info;
     const bool ok = inf.status == MPPI_OK;
     double z = 0.0, q = 0.0;
     block_total_zq(a.zq, a.nchunks, &z, &q);
+    // the mean multiplies by 1 / z; lse and ESS are formed at the end, off the element path
+    const double inv_z = 1.0 / z;
     if (t == 0) {
-        s_z = z;
-        inf.lse = ok ? log(z) : NAN;
-        inf.ess = ok ? z * z / q : 0.0;
-        a.info->lse = inf.lse;
-        a.info->ess = inf.ess;
         int upd = 0;
         if (ok) {
             const double cb = (double)a.costs[inf.best];
@@ -229,7 +232,6 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
         s_update = upd;
     }
     __syncthreads();
-    z = s_z;
     const bool last = a.iter == a.iters - 1;
     // chunk totals: FIN_SPLIT interleaved sub-sums per element (chunks c = s, s + FIN_SPLIT,
     // ... in increasing order) spread over the block, then combined by a balanced tree
@@ -240,7 +242,7 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
                 const int sidx = task / FIN_TILE, el = task - sidx * FIN_TILE, e = e0 + el;
                 double acc = 0.0;
                 if (e < a.E) {
-#pragma unroll 4
+#pragma unroll 8
                     for (int c = sidx; c < a.nchunks; c += FIN_SPLIT) acc += a.partial[(size_t)c * a.E + e];
                 }
                 s_sub[task] = acc;
@@ -249,12 +251,18 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
         for (int el = t; el < FIN_TILE && e0 + el < a.E; el += blockDim.x) {
             const int e = e0 + el;
             float m = a.nominal[e];
-            if (ok) m = (float)(tree16(s_sub + el, FIN_TILE) / z);
+            if (ok) m = (float)(tree16(s_sub + el, FIN_TILE) * inv_z);
             if (s_update) a.best_out[e] = a.knots[(size_t)inf.best * a.E + e];
             if (last) a.mean_out[e] = m;
             a.nominal[e] = m;
         }
         __syncthreads();
+    }
+    if (t == 0) {
+        inf.lse = ok ? log(z) : NAN;
+        inf.ess = ok ? z * z / q : 0.0;
+        a.info->lse = inf.lse;
+        a.info->ess = inf.ess;
     }
     if (last) {
         if (a.warm_from == MPPI_WARM_BEST && a.solve->best_index >= 0)
