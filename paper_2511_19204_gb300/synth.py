@@ -334,6 +334,30 @@ def chain2(seed: int = 11) -> RobotModel:
     return _finish("chain2", bodies, [], fixed_base=True, w_tau=0.0)
 
 
+def random_tree(nb: int = 32, nc: int = 32, seed: int = 17, fixed_base: bool = False) -> RobotModel:
+    """A floating (or fixed) base with nb - 1 revolute bodies on a random tree (each body's
+    parent drawn among the earlier ones), skewed unit axes, random offsets, masses and
+    inertias, and nc contact points on random bodies: the largest model the library
+    accepts at nb = nc = 32."""
+    rng = np.random.default_rng(seed)
+    bodies = [dict(parent=-1, mass=float(rng.uniform(2.0, 6.0)), com=tuple(rng.normal(scale=0.02, size=3)),
+                   inertia=_box_inertia(4.0, 0.3, 0.2, 0.1))]
+    for b in range(1, nb):
+        a = rng.normal(size=3)
+        ms = float(rng.uniform(0.2, 1.5))
+        bodies.append(dict(parent=int(rng.integers(0, b)), axis=tuple(a / np.linalg.norm(a)),
+                           jpos=tuple(rng.normal(scale=0.08, size=3)), mass=ms,
+                           com=tuple(rng.normal(scale=0.04, size=3)),
+                           inertia=_sphere_inertia(ms, float(rng.uniform(0.03, 0.08))),
+                           armature=0.05, kp=20.0, kd=0.8, tau_max=30.0))
+    contacts = [(int(rng.integers(0, nb)), tuple(rng.normal(scale=0.05, size=3))) for _ in range(nc)]
+    m = _finish(f"random_tree_{nb}", bodies, contacts, fixed_base=fixed_base, contact_k=2.0e4, contact_c=200.0,
+                mu=0.8, eps_f=1.5, z_des=0.5, vx_des=0.0, w_z=1.0, w_vx=0.5, w_tilt=0.5, w_tau=1e-3)
+    m.q_stand = np.zeros(nb - 1)
+    m.base_z0 = 0.5
+    return m
+
+
 def free_body(m: float = 2.5) -> RobotModel:
     """A single floating rigid body with an asymmetric inertia and an offset centre of mass."""
     bodies = [dict(parent=-1, mass=m, com=(0.03, -0.02, 0.05),
@@ -395,7 +419,7 @@ def with_paper_cost(m: RobotModel, task: str, pdot_des=(0.0, 0.0, 0.0), z_des: f
 
 
 MODELS = {"quadruped": quadruped, "humanoid": humanoid, "pendulum": pendulum, "chain2": chain2,
-          "free_body": free_body, "branch3": branch3, "point_mass": point_mass}
+          "free_body": free_body, "branch3": branch3, "point_mass": point_mass, "random_tree": random_tree}
 
 
 # --------------------------------------------------------------------------------------
