@@ -368,7 +368,7 @@ size_t ctx_layout(mppi_ctx* c, bool assign) {
 }
 
 cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knots, int N, float* d_costs,
-                            double* d_finals, cudaStream_t s, const SampleArgs* noise) {
+                            double* d_finals, cudaStream_t s) {
     RolloutArgs<float> a;
     a.model = (const DevModel<float>*)c->model->d_f;
     a.x0 = d_x0;
@@ -381,11 +381,6 @@ cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knot
     a.nk = c->nk;
     a.dt = (float)c->dt;
     a.dtk = (float)c->dtk;
-    if (noise) {  // the lanes-per-chain kernel draws its knots itself
-        if (c->mapping != MPPI_MAP_CHAIN) return cudaErrorInvalidValue;
-        a.fuse_noise = 1;
-        a.noise = *noise;
-    }
     switch (c->mapping) {
         case MPPI_MAP_WARP: return launch_rollout_warp_f32(a, 32, c->block, s);
         case MPPI_MAP_HALFWARP: return launch_rollout_warp_f32(a, 16, c->block, s);
@@ -418,11 +413,9 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
     sa.scale_v = (float)c->scale_v;
     sa.dtk = (float)c->dtk;
     sa.spline = c->spline;
-    // the lanes-per-chain kernel draws its own knots; the other mappings get the noise kernel
-    const bool fuse = c->mapping == MPPI_MAP_CHAIN;
-    cudaError_t e = fuse ? cudaSuccess : launch_sample_knots(sa, s);
+    cudaError_t e = launch_sample_knots(sa, s);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it], s, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s, fuse ? &sa : nullptr);
+    if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it + 1], s, cudaEventRecordExternal);
     if (e == cudaSuccess) {
         FinalizeArgs f;
@@ -1064,10 +1057,7 @@ mppi_status mppi_model_info(const mppi_model* m, int32_t* o) {
 
 size_t mppi_ctx_device_bytes(const mppi_ctx* c) { return c ? c->dev_bytes : 0; }
 
-int32_t mppi_ctx_kernels_per_solve(const mppi_ctx* c) {
-    if (!c) return 0;
-    return 1 + (c->mapping == MPPI_MAP_CHAIN ? 2 : 3) * c->iters;
-}
+int32_t mppi_ctx_kernels_per_solve(const mppi_ctx* c) { return c ? 1 + 3 * c->iters : 0; }
 
 mppi_status mppi_ctx_set_fp64_check(mppi_ctx* c, int32_t on) {
     if (!c) return MPPI_ERR_INVALID_ARG;

@@ -1,6 +1,5 @@
 // Lanes-per-chain rollout kernels (see rollout_lanes.cuh).
 #pragma once
-#include "noise.cuh"
 #include "rollout_lanes.cuh"
 
 namespace mppi {
@@ -12,15 +11,6 @@ __global__ void __launch_bounds__(256) rollout_lanes_kernel(RolloutArgs<float> a
     if (!bulk_load_to_smem(&Ms, a.model, (uint32_t)sizeof(DevModel<float>), &mbar)) {
         if (threadIdx.x == 0 && a.status) atomicOr(a.status, DEV_ERR_TMA_TIMEOUT);
         return;
-    }
-    if (a.fuse_noise) {
-        // the knots of this block's samples (the noise step), drawn by the whole block; the
-        // rollouts below read them back (the block's own global writes, visible after the
-        // step's final barrier)
-        extern __shared__ float eps[];  // [NOISE_SPB][E]
-        const NoiseParams np = noise_params(a.noise, &Ms);
-        const int spb = blockDim.x / LANES, first = blockIdx.x * spb;
-        for (int s0 = 0; s0 < spb; s0 += NOISE_SPB) block_sample_knots(np, first + s0, min(NOISE_SPB, spb - s0), eps);
     }
     const int g = threadIdx.x % LANES;
     const int n = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
@@ -44,20 +34,18 @@ cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, 
     const int spb = block / LANES;
     const int grid = (a.N + spb - 1) / spb;
     if (grid == 0) return cudaSuccess;
-    // E <= MAXK * 2 * (MAXB - 1) = 992 floats per sample: at most 31.7 KB with the model's 5 KB
-    const size_t sm = a.fuse_noise ? (size_t)NOISE_SPB * a.noise.nk * 2 * a.noise.nj * sizeof(float) : 0;
     if (topology == TOPO_QUADRUPED) {
         const bool xyy = axis_plan == AXP_XYY;
         if (paper) {
-            if (xyy) rollout_lanes_kernel<3, false, true, AXP_XYY><<<grid, block, sm, s>>>(a);
-            else rollout_lanes_kernel<3, false, true, AXP_GENERIC><<<grid, block, sm, s>>>(a);
+            if (xyy) rollout_lanes_kernel<3, false, true, AXP_XYY><<<grid, block, 0, s>>>(a);
+            else rollout_lanes_kernel<3, false, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
         } else {
-            if (xyy) rollout_lanes_kernel<3, false, false, AXP_XYY><<<grid, block, sm, s>>>(a);
-            else rollout_lanes_kernel<3, false, false, AXP_GENERIC><<<grid, block, sm, s>>>(a);
+            if (xyy) rollout_lanes_kernel<3, false, false, AXP_XYY><<<grid, block, 0, s>>>(a);
+            else rollout_lanes_kernel<3, false, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
         }
     } else {
-        if (paper) rollout_lanes_kernel<6, true, true, AXP_GENERIC><<<grid, block, sm, s>>>(a);
-        else rollout_lanes_kernel<6, true, false, AXP_GENERIC><<<grid, block, sm, s>>>(a);
+        if (paper) rollout_lanes_kernel<6, true, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
+        else rollout_lanes_kernel<6, true, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

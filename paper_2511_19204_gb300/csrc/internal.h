@@ -56,9 +56,6 @@ struct RolloutArgs {
     uint32_t* status;     // DEV_ERR bits (nullable)
     int N, H, nk;
     T dt, dtk;
-    // lanes-per-chain kernels: draw each block's knots (noise step) before its rollouts
-    int fuse_noise = 0;
-    SampleArgs noise;
 };
 
 // launches (kernels.cu / rollout_*.cu)

@@ -19,7 +19,24 @@ constexpr int SAMPLE_THREADS = 256;
 
 __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs a) {
     extern __shared__ float eps[];  // [NOISE_SPB][E]
-    block_sample_knots(noise_params(a, a.model), blockIdx.x * NOISE_SPB, NOISE_SPB, eps);
+    NoiseParams p;
+    p.nominal = a.nominal;
+    p.sigma_row = a.sigma_row;
+    p.model = a.model;
+    p.knots = a.knots;
+    p.it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
+    p.inst = a.inst;
+    p.seed_lo = a.seed_lo;
+    p.seed_hi = a.seed_hi;
+    p.N = a.N;
+    p.nk = a.nk;
+    p.nj = a.nj;
+    p.has_limits = a.has_limits;
+    p.scale_q = a.scale_q;
+    p.scale_v = a.scale_v;
+    p.dtk = a.dtk;
+    p.spline = a.spline;
+    block_sample_knots(p, blockIdx.x * NOISE_SPB, NOISE_SPB, eps);
 }
 
 cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s) {

@@ -56,29 +56,6 @@ __device__ __forceinline__ void spline_slopes(int spline, int nk, float h, const
     d[(nk - 1) * st] = (q[(nk - 1) * st] - q[(nk - 2) * st]) / h + h * (M[nk - 2] + 2.f * M[nk - 1]) / 6.f;
 }
 
-// The noise step's parameters from the host-side arguments (model: where to read the
-// joint limits, global or shared memory).
-__device__ __forceinline__ NoiseParams noise_params(const SampleArgs& a, const DevModel<float>* model) {
-    NoiseParams p;
-    p.nominal = a.nominal;
-    p.sigma_row = a.sigma_row;
-    p.model = model;
-    p.knots = a.knots;
-    p.it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
-    p.inst = a.inst;
-    p.seed_lo = a.seed_lo;
-    p.seed_hi = a.seed_hi;
-    p.N = a.N;
-    p.nk = a.nk;
-    p.nj = a.nj;
-    p.has_limits = a.has_limits;
-    p.scale_q = a.scale_q;
-    p.scale_v = a.scale_v;
-    p.dtk = a.dtk;
-    p.spline = a.spline;
-    return p;
-}
-
 // Samples [n0, n0 + cnt) (cnt <= NOISE_SPB) by the whole block; eps: shared [NOISE_SPB][E].
 __device__ __noinline__ void block_sample_knots(const NoiseParams& a, int n0, int cnt, float* eps) {
     const int E = a.nk * 2 * a.nj;
