@@ -396,6 +396,14 @@ mppi_status mppi_server_stats(mppi_server* server, int64_t* h_out5);
  * 128, 256; negative = not supported). Writes the choice to *mapping / *block_size. */
 mppi_status mppi_autotune(mppi_ctx* ctx, int32_t* mapping, int32_t* block_size, float* h_ms);
 
+/* Persist the autotuner's choices in a JSON file (an array with one object per tuned
+ * shape: device type as name|SMs|compute capability, model hash, K, H, knots, mapping,
+ * block, the 16 timings). The file's entries are loaded now (a missing file is created
+ * by the next tuning) and every new tuning rewrites it; later processes on the same kind
+ * of GPU reuse the entries without timing. NULL or "" keeps the choices in the process
+ * only. Errors: INVALID_ARG (the file exists but is not in this format). */
+mppi_status mppi_autotune_cache_file(const char* path);
+
 /* Switch a context's rollout mapping and block size (MPPI_MAP_WARP/HALFWARP/CHAIN/THREAD). */
 mppi_status mppi_ctx_set_mapping(mppi_ctx* ctx, int32_t mapping, int32_t block_size);
 

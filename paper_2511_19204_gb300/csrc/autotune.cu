@@ -1,12 +1,15 @@
 // Rollout-mapping autotuner: for one context, time every supported (mapping, block size)
 // on the context's own buffers (knots drawn around the resident nominal) and keep the
-// fastest. Results are cached per (device, model contents, K, H, knots) for the life of
-// the process, so later contexts of the same shape reuse the choice without timing.
+// fastest. Results are cached per (device type, model contents, K, H, knots) for the life
+// of the process, and, once a cache file is named (mppi_autotune_cache_file), in that JSON
+// file too, so later processes on the same kind of GPU reuse the choice without timing.
 #include <cuda_runtime.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 
 #include "capi_internal.h"
@@ -16,7 +19,7 @@ namespace mppi {
 namespace {
 
 struct TuneKey {
-    int device;
+    std::string device;  // "<name>|<SM count>|<compute capability>"
     uint64_t model_hash;
     int N, H, nk;
     bool operator<(const TuneKey& o) const {
@@ -31,6 +34,117 @@ struct TuneVal {
 
 std::mutex g_mu;
 std::map<TuneKey, TuneVal> g_cache;
+std::string g_cache_path;  // empty: the process cache only
+
+std::string device_id(int dev) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "device" + std::to_string(dev);
+    std::string name(p.name);
+    for (char& ch : name)
+        if (ch == '"' || ch == '|' || ch == '\\') ch = '_';
+    return name + "|" + std::to_string(p.multiProcessorCount) + "|" + std::to_string(p.major) + "." +
+           std::to_string(p.minor);
+}
+
+// ---- the JSON cache file: an array with one object per line, written and read here ----
+// {"device": "<id>", "model": "<16 hex digits>", "K": n, "H": n, "knots": n, "mapping": n,
+//  "block": n, "ms": [16 numbers]}
+
+std::string entry_json(const TuneKey& k, const TuneVal& v) {
+    char head[512];
+    snprintf(head, sizeof head,
+             "{\"device\": \"%s\", \"model\": \"%016llx\", \"K\": %d, \"H\": %d, \"knots\": %d, "
+             "\"mapping\": %d, \"block\": %d, \"ms\": [",
+             k.device.c_str(), (unsigned long long)k.model_hash, k.N, k.H, k.nk, v.mapping, v.block);
+    std::string out(head);
+    for (int i = 0; i < 16; ++i) {
+        char num[32];
+        snprintf(num, sizeof num, "%s%.6g", i ? ", " : "", (double)v.ms[i]);
+        out += num;
+    }
+    return out + "]}";
+}
+
+// the value text after "<key>": in one line (nullptr if absent)
+const char* field(const std::string& line, const char* key) {
+    const std::string pat = std::string("\"") + key + "\":";
+    const size_t at = line.find(pat);
+    if (at == std::string::npos) return nullptr;
+    const char* p = line.c_str() + at + pat.size();
+    while (*p == ' ') ++p;
+    return p;
+}
+
+bool parse_entry(const std::string& line, TuneKey& k, TuneVal& v) {
+    const char* d = field(line, "device");
+    const char* m = field(line, "model");
+    const char* ms = field(line, "ms");
+    if (!d || !m || !ms || *d != '"' || *m != '"' || *ms != '[') return false;
+    const char* de = strchr(d + 1, '"');
+    if (!de) return false;
+    k.device.assign(d + 1, de);
+    unsigned long long h = 0;
+    if (sscanf(m + 1, "%16llx", &h) != 1) return false;
+    k.model_hash = h;
+    const char* fK = field(line, "K");
+    const char* fH = field(line, "H");
+    const char* fk = field(line, "knots");
+    const char* fm = field(line, "mapping");
+    const char* fb = field(line, "block");
+    if (!fK || !fH || !fk || !fm || !fb) return false;
+    if (sscanf(fK, "%d", &k.N) != 1 || sscanf(fH, "%d", &k.H) != 1 || sscanf(fk, "%d", &k.nk) != 1 ||
+        sscanf(fm, "%d", &v.mapping) != 1 || sscanf(fb, "%d", &v.block) != 1)
+        return false;
+    const char* p = ms + 1;
+    for (int i = 0; i < 16; ++i) {
+        char* end = nullptr;
+        v.ms[i] = strtof(p, &end);
+        if (end == p) return false;
+        p = end;
+        while (*p == ' ' || *p == ',') ++p;
+    }
+    return *p == ']';
+}
+
+// caller holds g_mu
+bool load_cache_file(const std::string& path) {
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return true;  // no file yet: it is created by the first tuning
+    std::map<TuneKey, TuneVal> got;
+    char buf[4096];
+    bool ok = true;
+    while (fgets(buf, sizeof buf, f)) {
+        std::string line(buf);
+        if (line.find('{') == std::string::npos) continue;  // the array's brackets
+        TuneKey k;
+        TuneVal v;
+        if (!parse_entry(line, k, v)) {
+            ok = false;
+            break;
+        }
+        got[k] = v;
+    }
+    fclose(f);
+    if (!ok) return false;
+    for (auto& kv : got) g_cache[kv.first] = kv.second;
+    return true;
+}
+
+// caller holds g_mu; written to a temporary file, then renamed over the old one
+bool save_cache_file(const std::string& path) {
+    const std::string tmp = path + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fputs("[\n", f);
+    size_t i = 0;
+    for (auto& kv : g_cache) {
+        fputs(entry_json(kv.first, kv.second).c_str(), f);
+        fputs(++i < g_cache.size() ? ",\n" : "\n", f);
+    }
+    fputs("]\n", f);
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path.c_str()) == 0;
+}
 
 uint64_t fnv1a(const void* p, size_t n) {
     const unsigned char* b = (const unsigned char*)p;
@@ -133,7 +247,7 @@ extern "C" mppi_status mppi_autotune(mppi_ctx* c, int32_t* mapping, int32_t* blo
     if (!c) return MPPI_ERR_INVALID_ARG;
     // the timed rollouts start from the context's last state if a solve ran, else from
     // the model's rest pose half a metre above the ground
-    TuneKey key{c->device, fnv1a(&c->model->host_f, sizeof(DevModel<float>)), c->N, c->H, c->nk};
+    TuneKey key{device_id(c->device), fnv1a(&c->model->host_f, sizeof(DevModel<float>)), c->N, c->H, c->nk};
     TuneVal v;
     bool hit = false;
     {
@@ -159,6 +273,10 @@ extern "C" mppi_status mppi_autotune(mppi_ctx* c, int32_t* mapping, int32_t* blo
         if (st != MPPI_OK) return st;
         std::lock_guard<std::mutex> lk(g_mu);
         g_cache[key] = v;
+        if (!g_cache_path.empty() && !save_cache_file(g_cache_path)) {
+            set_error(c, "mppi_autotune: the cache file could not be written");
+            // the choice stands for this process; only the file is missing the entry
+        }
     } else {
         c->mapping = v.mapping;
         c->block = v.block;
@@ -167,5 +285,19 @@ extern "C" mppi_status mppi_autotune(mppi_ctx* c, int32_t* mapping, int32_t* blo
     if (mapping) *mapping = v.mapping;
     if (block) *block = v.block;
     if (h_ms) memcpy(h_ms, v.ms, sizeof v.ms);
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_autotune_cache_file(const char* path) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!path || !*path) {
+        g_cache_path.clear();
+        return MPPI_OK;
+    }
+    if (!load_cache_file(path)) {
+        set_error(nullptr, std::string("mppi_autotune_cache_file: cannot parse ") + path);
+        return MPPI_ERR_INVALID_ARG;
+    }
+    g_cache_path = path;
     return MPPI_OK;
 }

@@ -114,6 +114,7 @@ SIGNATURES = [
     ("mppi_get_warm_start", C.c_int32, [_P, _fp]),
     ("mppi_model_info", C.c_int32, [_P, _ip]),
     ("mppi_selftest_math", C.c_int32, [C.c_int32, _fp, _fp, _fp]),
+    ("mppi_autotune_cache_file", C.c_int32, [C.c_char_p]),
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
     ("mppi_average", C.c_int32, [C.c_int32, C.c_int32, _fp, _dp, _dp]),
@@ -533,3 +534,8 @@ def selftest_math(x, y):
     out = np.zeros((xs.shape[0], 3), np.float32)
     _check(load().mppi_selftest_math(xs.shape[0], _pf(xs), _pf(ys), _pf(out)))
     return out
+
+
+def autotune_cache_file(path):
+    """Persist the autotuner's choices in the JSON file `path` (None: this process only)."""
+    _check(load().mppi_autotune_cache_file(path.encode() if path else None))

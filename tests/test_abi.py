@@ -121,3 +121,17 @@ def test_null_arguments(lib):
     assert lib.mppi_weights(0, None, 0.1, 0, None, None) == -1
     assert lib.mppi_average(0, 0, None, None, None) == -1
     assert lib.mppi_philox_words(0, None, None, None) == 0
+
+
+def test_autotune_cache_file_format(lib, tmp_path):
+    # host-side part of the autotune cache: a well-formed file loads, a malformed one is
+    # refused, a missing one is accepted (created by the next tuning), NULL turns it off
+    good = tmp_path / "tune.json"
+    good.write_text('[\n{"device": "GPU X|152|10.3", "model": "00000000deadbeef", "K": 64, "H": 50, "knots": 4, '
+                    '"mapping": 2, "block": 64, "ms": [' + ", ".join(["-1"] * 8 + ["0.5"] * 8) + ']}\n]\n')
+    assert lib.mppi_autotune_cache_file(str(good).encode()) == 0
+    bad = tmp_path / "bad.json"
+    bad.write_text('[\n{"device": "GPU X", "model": "zz", "K": 1}\n]\n')
+    assert lib.mppi_autotune_cache_file(str(bad).encode()) == -1
+    assert lib.mppi_autotune_cache_file(str(tmp_path / "new.json").encode()) == 0
+    assert lib.mppi_autotune_cache_file(None) == 0
