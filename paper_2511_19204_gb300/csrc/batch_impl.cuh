@@ -27,6 +27,7 @@
 #include "noise.cuh"
 #include "reduce.cuh"
 #include "rollout_lanes.cuh"
+#include "rollout_split.cuh"
 
 namespace mppi {
 
@@ -236,7 +237,24 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
             for (int s0 = 0; s0 < cnt; s0 += NOISE_SPB) block_sample_knots(np, n0 + s0, min(NOISE_SPB, cnt - s0), work);
             // rollouts of the tile with the instance's mapping
             const int last_n = n0 + cnt - 1;
-            if (I.mapping == MPPI_MAP_CHAIN) {
+            if (I.mapping == MPPI_MAP_CHAIN && M->axis_plan == AXP_HUM) {
+                // two-warp split: 4 pairs of 16 samples; `work` is free again after the
+                // noise pass
+                static_assert(4 * SPLIT_PAIR_FLOATS <= 27 * BATCH_THREADS, "split exchange area exceeds work");
+                static_assert(BATCH_THREADS / 4 == 4 * SPLIT_SPP, "tile = 4 warp pairs");
+                __syncthreads();
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pair = warp >> 1;
+                const int n = n0 + pair * SPLIT_SPP + (lane >> 1);
+                const int ne = min(n, last_n);
+                const float* kn = I.knots + (size_t)ne * I.E;
+                float* rec = work + pair * SPLIT_PAIR_FLOATS;
+                const float c = M->paper_cost
+                                    ? split_rollout<true>(*M, warp & 1, lane, rec, 1 + pair, I.x0, kn, I.H, I.nk, I.dt,
+                                                          I.dtk, nullptr)
+                                    : split_rollout<false>(*M, warp & 1, lane, rec, 1 + pair, I.x0, kn, I.H, I.nk, I.dt,
+                                                           I.dtk, nullptr);
+                if (n <= last_n && (warp & 1) == 0 && (lane & 1) == 0) I.costs[n] = c;
+            } else if (I.mapping == MPPI_MAP_CHAIN) {
                 const int g = threadIdx.x & 3;
                 const int n = n0 + (threadIdx.x >> 2);
                 const int ne = min(n, last_n);

@@ -64,6 +64,10 @@ static bool offset_along(const mppi_model_desc& d, int b, int k) {
     return true;
 }
 
+static bool offset_zero(const mppi_model_desc& d, int b) {
+    return d.jpos[3 * b] == 0.0 && d.jpos[3 * b + 1] == 0.0 && d.jpos[3 * b + 2] == 0.0;
+}
+
 static bool is_chain(const mppi_model_desc& d, int first, int len, int parent) {
     if (len < 1 || first + len > d.nb || d.parent[first] != parent) return false;
     for (int j = 1; j < len; ++j)
@@ -112,6 +116,24 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
             P.b0[3] = br + 1 + C;
             P.len[3] = C;
             P.branch = br;
+            // the usual humanoid layout (AXP_HUM): legs z, x, y, y, y, x with offsets in the
+            // yz-plane, on z, zero, on z, on z, zero; waist z on z; arms y, x, z, y with
+            // offsets in the yz-plane, on y, zero, on z
+            bool hum = A == 6 && C == 4 && axis_is(d, br, 2) && offset_along(d, br, 2);
+            for (int l = 0; l < 2 && hum; ++l) {
+                const int b = P.b0[l];
+                hum = axis_is(d, b, 2) && axis_is(d, b + 1, 0) && axis_is(d, b + 2, 1) && axis_is(d, b + 3, 1) &&
+                      axis_is(d, b + 4, 1) && axis_is(d, b + 5, 0) && d.jpos[3 * b] == 0.0 &&
+                      offset_along(d, b + 1, 2) && offset_zero(d, b + 2) && offset_along(d, b + 3, 2) &&
+                      offset_along(d, b + 4, 2) && offset_zero(d, b + 5);
+            }
+            for (int l = 2; l < 4 && hum; ++l) {
+                const int b = P.b0[l];
+                hum = axis_is(d, b, 1) && axis_is(d, b + 1, 0) && axis_is(d, b + 2, 2) && axis_is(d, b + 3, 1) &&
+                      d.jpos[3 * b] == 0.0 && offset_along(d, b + 1, 1) && offset_zero(d, b + 2) &&
+                      offset_along(d, b + 3, 2);
+            }
+            if (hum) P.axis_plan = AXP_HUM;
             return P;
         }
     }
@@ -498,6 +520,8 @@ bool mapping_valid(const mppi_model* m, int mapping, int block) {
         case MPPI_MAP_HALFWARP:
             return m->nb <= 16 && (block == 0 || (block % 32 == 0 && block >= 32 && block <= 256));
         case MPPI_MAP_CHAIN:
+            if (m->host_f.axis_plan == AXP_HUM)  // warp pairs
+                return block == 0 || (block % 64 == 0 && block >= 64 && block <= 256);
             return chain_mapping_supported(m->topology) && (block == 0 || (block % 32 == 0 && block >= 32 && block <= 256));
         case MPPI_MAP_THREAD:
             return m->topology != TOPO_GENERIC && thread_mapping_supported(m->topology) &&

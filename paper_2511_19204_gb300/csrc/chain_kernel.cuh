@@ -1,6 +1,7 @@
-// Lanes-per-chain rollout kernels (see rollout_lanes.cuh).
+// Lanes-per-chain rollout kernels (see rollout_lanes.cuh and rollout_split.cuh).
 #pragma once
 #include "rollout_lanes.cuh"
+#include "rollout_split.cuh"
 
 namespace mppi {
 
@@ -24,6 +25,31 @@ __global__ void __launch_bounds__(256) rollout_lanes_kernel(RolloutArgs<float> a
     if (active && g == 0) a.costs[n] = c;
 }
 
+// The two-warp split (humanoid layout): 64-thread warp pairs, 16 samples each, so the
+// same 4 threads per sample as the one-warp kernel; pair p of the block uses named
+// barrier 1 + p and its own exchange area.
+template <bool PAPER>
+__global__ void __launch_bounds__(256) rollout_split_kernel(RolloutArgs<float> a) {
+    __shared__ __align__(16) DevModel<float> Ms;
+    __shared__ uint64_t mbar;
+    __shared__ __align__(16) float xch[4 * SPLIT_PAIR_FLOATS];
+    if (!bulk_load_to_smem(&Ms, a.model, (uint32_t)sizeof(DevModel<float>), &mbar)) {
+        if (threadIdx.x == 0 && a.status) atomicOr(a.status, DEV_ERR_TMA_TIMEOUT);
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pair = warp >> 1;
+    const int n = blockIdx.x * (blockDim.x / LANES) + pair * SPLIT_SPP + (lane >> 1);
+    const bool active = n < a.N;
+    const int ne = active ? n : a.N - 1;
+    const int nj = Ms.nb - 1;
+    const int E = a.nk * 2 * nj;
+    const int nx = 13 + 2 * nj;
+    double* xf = (active && a.finals) ? a.finals + (size_t)n * nx : nullptr;
+    const float c = split_rollout<PAPER>(Ms, warp & 1, lane, xch + pair * SPLIT_PAIR_FLOATS, 1 + pair, a.x0,
+                                         a.knots + (size_t)ne * E, a.H, a.nk, a.dt, a.dtk, xf);
+    if (active && (warp & 1) == 0 && (lane & 1) == 0) a.costs[n] = c;
+}
+
 bool chain_mapping_supported(int topology) { return topology == TOPO_QUADRUPED || topology == TOPO_HUMANOID; }
 
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
@@ -43,6 +69,10 @@ cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, 
             if (xyy) rollout_lanes_kernel<3, false, false, AXP_XYY><<<grid, block, 0, s>>>(a);
             else rollout_lanes_kernel<3, false, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
         }
+    } else if (axis_plan == AXP_HUM) {
+        if (block % 64 != 0) return cudaErrorInvalidValue;
+        if (paper) rollout_split_kernel<true><<<grid, block, 0, s>>>(a);
+        else rollout_split_kernel<false><<<grid, block, 0, s>>>(a);
     } else {
         if (paper) rollout_lanes_kernel<6, true, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
         else rollout_lanes_kernel<6, true, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);

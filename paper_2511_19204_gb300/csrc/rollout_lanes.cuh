@@ -144,7 +144,8 @@ __device__ __forceinline__ void jfull_rotate(const JRot<AX>& J, const float* B, 
     }
 }
 // ------------------------------------------------------------------------------------
-// Joint offsets r along one coordinate axis (OF = 0, 1, 2: r = rho e_OF; OF = -1: any r).
+// Joint offsets r along one coordinate axis (OF = 0, 1, 2: r = rho e_OF), in the xy-plane
+// (OF = 3: r.z = 0) or the yz-plane (OF = 4: r.x = 0), zero (OF = 5), or any r (OF = -1).
 // (e_k x u)_i = eps_{i k p} u_p with p the third index: xk_src gives p (or -1 for i = k)
 // and xk_sgn the sign, so the products by zero components are never formed.
 // ------------------------------------------------------------------------------------
@@ -162,13 +163,24 @@ __device__ __forceinline__ float rlen(V3<float> r) {
 __device__ __forceinline__ V3<float> cross_rxy(V3<float> r, V3<float> u) {
     return v3(r.y * u.z, -(r.x * u.z), r.x * u.y - r.y * u.x);
 }
+// r x u for r in the yz-plane (OF == 4: r.x == 0), the products with r.x left out
+__device__ __forceinline__ V3<float> cross_ryz(V3<float> r, V3<float> u) {
+    return v3(r.y * u.z - r.z * u.y, r.z * u.x, -(r.y * u.x));
+}
+template <int OF>
+__device__ __forceinline__ V3<float> cross_rp(V3<float> r, V3<float> u) {
+    if constexpr (OF == 3) return cross_rxy(r, u);
+    else return cross_ryz(r, u);
+}
 // v + s (r x u), s = +1 or -1
 template <int OF>
 __device__ __forceinline__ V3<float> add_rcross(V3<float> v, V3<float> r, V3<float> u, float sgn) {
     if constexpr (OF < 0) {
         return sgn > 0.f ? v + cross(r, u) : v - cross(r, u);
-    } else if constexpr (OF == 3) {
-        return sgn > 0.f ? v + cross_rxy(r, u) : v - cross_rxy(r, u);
+    } else if constexpr (OF == 3 || OF == 4) {
+        return sgn > 0.f ? v + cross_rp<OF>(r, u) : v - cross_rp<OF>(r, u);
+    } else if constexpr (OF == 5) {
+        return v;
     } else {
         const float rho = sgn * rlen<OF>(r);
         float o[3] = {v.x, v.y, v.z};
@@ -185,6 +197,10 @@ __device__ __forceinline__ V3<float> rot_r(const M3<float>& R, V3<float> r) {
         return mul(R, r);
     } else if constexpr (OF == 3) {
         return v3(R.m[0] * r.x + R.m[1] * r.y, R.m[3] * r.x + R.m[4] * r.y, R.m[6] * r.x + R.m[7] * r.y);
+    } else if constexpr (OF == 4) {
+        return v3(R.m[1] * r.y + R.m[2] * r.z, R.m[4] * r.y + R.m[5] * r.z, R.m[7] * r.y + R.m[8] * r.z);
+    } else if constexpr (OF == 5) {
+        return v3(0.f, 0.f, 0.f);
     } else {
         const float rho = rlen<OF>(r);
         return v3(R.m[OF] * rho, R.m[3 + OF] * rho, R.m[6 + OF] * rho);
@@ -197,19 +213,26 @@ __device__ __forceinline__ void art_shift_r(const float* A, const float* B, cons
                                             Art<float>& out) {
     if constexpr (OF < 0) {
         art_shift(A, B, C, r, out);
-    } else if constexpr (OF == 3) {
-        // as art_shift with every r x (.) and (.) x r formed without r.z
-        const V3<float> x0 = cross_rxy(r, v3(C[0], C[3], C[4])), x1 = cross_rxy(r, v3(C[3], C[1], C[5])),
-                        x2 = cross_rxy(r, v3(C[4], C[5], C[2]));
+    } else if constexpr (OF == 5) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out.A[k] = A[k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out.B[k] = B[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out.C[k] = C[k];
+    } else if constexpr (OF == 3 || OF == 4) {
+        // as art_shift with every r x (.) and (.) x r formed without the zero component of r
+        const V3<float> x0 = cross_rp<OF>(r, v3(C[0], C[3], C[4])), x1 = cross_rp<OF>(r, v3(C[3], C[1], C[5])),
+                        x2 = cross_rp<OF>(r, v3(C[4], C[5], C[2]));
         const float B2[9] = {B[0] + x0.x, B[1] + x1.x, B[2] + x2.x, B[3] + x0.y, B[4] + x1.y,
                              B[5] + x2.y, B[6] + x0.z, B[7] + x1.z, B[8] + x2.z};
-        const V3<float> d0 = cross_rxy(r, v3(B[0], B[1], B[2]));
-        const V3<float> d1 = cross_rxy(r, v3(B[3], B[4], B[5]));
-        const V3<float> d2 = cross_rxy(r, v3(B[6], B[7], B[8]));
+        const V3<float> d0 = cross_rp<OF>(r, v3(B[0], B[1], B[2]));
+        const V3<float> d1 = cross_rp<OF>(r, v3(B[3], B[4], B[5]));
+        const V3<float> d2 = cross_rp<OF>(r, v3(B[6], B[7], B[8]));
         // f_i = (row i of B2) x r = -(r x row i)
-        const V3<float> f0 = cross_rxy(r, v3(B2[0], B2[1], B2[2]));
-        const V3<float> f1 = cross_rxy(r, v3(B2[3], B2[4], B2[5]));
-        const V3<float> f2 = cross_rxy(r, v3(B2[6], B2[7], B2[8]));
+        const V3<float> f0 = cross_rp<OF>(r, v3(B2[0], B2[1], B2[2]));
+        const V3<float> f1 = cross_rp<OF>(r, v3(B2[3], B2[4], B2[5]));
+        const V3<float> f2 = cross_rp<OF>(r, v3(B2[6], B2[7], B2[8]));
         out.A[0] = A[0] + d0.x + f0.x;
         out.A[1] = A[1] + d1.y + f1.y;
         out.A[2] = A[2] + d2.z + f2.z;
@@ -463,7 +486,8 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyC
         if (KEEP) m.R = J.R;
     }
     P.R = jcompose(Pp.R, J);
-    P.p = Pp.p + rot_r<OF>(Pp.R, r);
+    if constexpr (OF == 5) P.p = Pp.p;
+    else P.p = Pp.p + rot_r<OF>(Pp.R, r);
     P.w = add_ax<AX>(C, jrotT(J, Pp.w), qd);
     P.v = jrotT(J, add_rcross<OF>(Pp.v, r, Pp.w, -1.f));
     m.cw = cross_ax<AX>(C, P.w, qd);

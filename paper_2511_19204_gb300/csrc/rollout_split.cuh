@@ -1,0 +1,454 @@
+// Two-warp split of the lanes-per-chain rollout, for trees of the usual humanoid layout
+// (axis plan AXP_HUM in common.cuh): a pair of warps rolls out 16 samples. The leg warp
+// runs both leg chains of each sample (2 lanes per sample, one leg each) and owns the
+// floating base; its partner, the arm warp, runs the waist body and both arm chains
+// (2 lanes per sample, one arm each, the waist replicated on the two). Each warp's code
+// is compiled for its own chains' joint axes and offsets; one warp holding both kinds of
+// chain would have to run the two specialisations one after the other.
+//
+// Per step the warps meet twice in shared memory (one record per sample and direction,
+// each behind a 64-thread named barrier):
+//   A  arm -> leg: the waist subtree's articulated inertia and bias force (Featherstone's
+//      articulated-body recursion, carried to the base frame) and the arm warp's share
+//      of the running cost;
+//   B  leg -> arm: the base acceleration of this step and the base pose of the next.
+// The base is integrated once, by the leg warp, so every base quantity the arm warp uses
+// is bitwise the leg warp's. A record is written before a barrier and read after it, and
+// its next write comes after the following barrier, so one buffer per direction suffices.
+// Left and right chains meet by a pair shuffle (a commutative sum: both lanes of a pair
+// hold the same bits). Equations as in the other rollout kernels: Sec. III-A Hermite
+// setpoints, Sec. III-C PD tracking, the articulated-body algorithm, semi-implicit Euler,
+// Kahan-summed running cost (Alg. 1).
+#pragma once
+#include "rollout_lanes.cuh"
+
+namespace mppi {
+
+constexpr int SPLIT_SPP = 16;                                 // samples per warp pair
+constexpr int SPLIT_REC = 36;                                 // floats per record (16-B aligned, bank-spread)
+constexpr int SPLIT_PAIR_FLOATS = 2 * SPLIT_SPP * SPLIT_REC;  // records A, then records B
+constexpr int SPLIT_LEG = 6, SPLIT_ARM = 4;
+constexpr int SPLIT_WAIST_AX = 2, SPLIT_WAIST_OF = 2;         // waist: about z, offset along z
+
+// Joint axis and offset codes (as in rollout_lanes.cuh) of chain position J of the leg
+// (ROLE 0: z, x, y, y, y, x; offsets yz-plane, z, 0, z, z, 0) and arm chains (ROLE 1:
+// y, x, z, y; offsets yz-plane, y, 0, z).
+template <int ROLE, int J>
+__host__ __device__ constexpr int split_axis() {
+    return ROLE == 0 ? (J == 0 ? 2 : ((J == 1 || J == 5) ? 0 : 1)) : (J == 0 ? 1 : (J == 1 ? 0 : (J == 2 ? 2 : 1)));
+}
+template <int ROLE, int J>
+__host__ __device__ constexpr int split_offset() {
+    return ROLE == 0 ? (J == 0 ? 4 : ((J == 2 || J == 5) ? 5 : 2)) : (J == 0 ? 4 : (J == 1 ? 1 : (J == 2 ? 5 : 2)));
+}
+
+// Named barrier of the two warps of a pair (ids 1.. ; 0 is __syncthreads). Its memory
+// clobber makes the compiler reload the records after it: the record pointers must not be
+// declared __restrict__, since the partner warp writes the same words.
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("barrier.sync %0, 64;" ::"r"(id) : "memory"); }
+
+__device__ __forceinline__ float pair_sum(float v) { return v + __shfl_xor_sync(0xffffffffu, v, 1); }
+
+__device__ __forceinline__ void pair_sum(Art<float>& c, V3<float>& n, V3<float>& f) {
+#pragma unroll
+    for (int t = 0; t < 6; ++t) c.A[t] = pair_sum(c.A[t]);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) c.B[t] = pair_sum(c.B[t]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) c.C[t] = pair_sum(c.C[t]);
+    n = v3(pair_sum(n.x), pair_sum(n.y), pair_sum(n.z));
+    f = v3(pair_sum(f.x), pair_sum(f.y), pair_sum(f.z));
+}
+
+// N float4 of a record; both lanes of a pair write the same values to the same words
+template <int N>
+__device__ __forceinline__ void rec_store(float* rec, const float (&v)[4 * N]) {
+    float4* d = reinterpret_cast<float4*>(rec);
+#pragma unroll
+    for (int k = 0; k < N; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <int N>
+__device__ __forceinline__ void rec_load(const float* rec, float (&v)[4 * N]) {
+    const float4* s = reinterpret_cast<const float4*>(rec);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const float4 x = s[k];
+        v[4 * k] = x.x;
+        v[4 * k + 1] = x.y;
+        v[4 * k + 2] = x.z;
+        v[4 * k + 3] = x.w;
+    }
+}
+
+// record B: base acceleration (aw, av), then the next base pose (R, p, w, v)
+__device__ __forceinline__ void put_base(float* rec, V3<float> aw, V3<float> av, const Pose& B) {
+    const float v[24] = {aw.x,     aw.y,     aw.z,     av.x,     av.y,     av.z,     B.R.m[0], B.R.m[1],
+                         B.R.m[2], B.R.m[3], B.R.m[4], B.R.m[5], B.R.m[6], B.R.m[7], B.R.m[8], B.p.x,
+                         B.p.y,    B.p.z,    B.w.x,    B.w.y,    B.w.z,    B.v.x,    B.v.y,    B.v.z};
+    rec_store<6>(rec, v);
+}
+__device__ __forceinline__ void get_base(const float* rec, V3<float>& aw, V3<float>& av, Pose& B) {
+    float v[24];
+    rec_load<6>(rec, v);
+    aw = v3(v[0], v[1], v[2]);
+    av = v3(v[3], v[4], v[5]);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) B.R.m[t] = v[6 + t];
+    B.p = v3(v[15], v[16], v[17]);
+    B.w = v3(v[18], v[19], v[20]);
+    B.v = v3(v[21], v[22], v[23]);
+}
+
+// Leg warp: both legs of one sample on lanes side = 0, 1, the base, the cost sum. Returns
+// the sample's cost (the same on both lanes).
+template <bool PAPER>
+__device__ __noinline__ float split_legs(const DevModel<float>& M, int side, const float* recA, float* recB, int bar,
+                                         const double* __restrict__ x0,
+                                         const float* __restrict__ knots, int H, int nk, float dt, float dtk,
+                                         double* __restrict__ xf) {
+    constexpr int LEN = SPLIT_LEG;
+    const int nj = M.nb - 1, nq = 7 + nj;
+    const int b0 = M.lane_b0[side];
+    const bool lead = side == 0;
+    V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
+    const V3<float> p_start = p;
+    float qw = (float)x0[3], qx = (float)x0[4], qy = (float)x0[5], qz = (float)x0[6];
+    V3<float> vl = v3((float)x0[nq], (float)x0[nq + 1], (float)x0[nq + 2]);
+    V3<float> w = v3((float)x0[nq + 3], (float)x0[nq + 4], (float)x0[nq + 5]);
+    float q[LEN], qd[LEN];
+#pragma unroll
+    for (int j = 0; j < LEN; ++j) {
+        q[j] = (float)x0[7 + b0 - 1 + j];
+        qd[j] = (float)x0[nq + 6 + b0 - 1 + j];
+    }
+    const float inv_dtk = 1.0f / dtk;
+    float sum = 0.f, comp = 0.f;
+    const int cb = M.cost_body;
+    const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>()>(load_body(M, b0 + LEN - 1));
+    SegPoly kc[LEN];
+    int kcur = -1;
+    Pose B;
+    B.R = quat_to_R(qw, qx, qy, qz);
+    B.p = p;
+    B.w = w;
+    B.v = vl;
+    put_base(recB, v3(0.f, 0.f, 0.f), v3(0.f, 0.f, 0.f), B);  // the arm warp's first base pose
+    pair_sync(bar);
+    const float inv_H = 1.0f / (float)H;
+    int k = 0, rem = -(nk - 1);
+    for (int h = 0; h < H; ++h) {
+        rem += nk - 1;
+        while (rem >= H) {
+            rem -= H;
+            ++k;
+        }
+        const float s = (float)rem * inv_H;
+        if (k != kcur) {
+            kcur = k;
+#pragma unroll
+            for (int j = 0; j < LEN; ++j) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
+        }
+        float tau[LEN];
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
+        // ---- pass 1: base, then the leg ----
+        V3<float> p0n, p0f;
+        float pc = 0.f;  // this lane's share of the modular running cost
+        {
+            V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
+            body_contacts<PAPER>(M, 0, B, fen, fef, pc, lead);
+            body_bias(load_body(M, 0), B, fen, fef, p0n, p0f);
+        }
+        if (PAPER && lead) pc += base_cost(M, B.R, B.p);
+        float tz = 0.f, tt = 0.f;
+        if (cb == 0 && lead) cost_terms(M, B, tz, tt);
+        BodyMem mem[LEN];
+        {
+            Pose Pp = B;
+            static_for<0, LEN>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                Pose P;
+                body_pass1<false, PAPER, split_axis<0, j>(), split_offset<0, j>()>(M, load_body(M, b0 + j), q[j], qd[j],
+                                                                                 Pp, P, mem[j], pc, true);
+                if (cb == b0 + j) cost_terms(M, P, tz, tt);
+                Pp = P;
+            });
+        }
+        // ---- pass 2: the leg inward, both legs summed at the base ----
+        Art<float> carry;
+        V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
+        static_for<0, LEN>([&](auto ic) {
+            constexpr int j = LEN - 1 - decltype(ic)::value;
+            if constexpr (j == LEN - 1)
+                body_pass2<false, split_axis<0, j>(), split_offset<0, j>(), true>(load_body(M, b0 + j), tau[j], mem[j],
+                                                                                false, carry, cpn, cpf, &leafp);
+            else
+                body_pass2<false, split_axis<0, j>(), split_offset<0, j>()>(load_body(M, b0 + j), tau[j], mem[j], true,
+                                                                          carry, cpn, cpf);
+        });
+        pair_sum(carry, cpn, cpf);
+        float te = 0.f;
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) te += tau[j] * tau[j];
+        float lc = (tz + tt) + M.w_tau * te;
+        if (PAPER) lc += pc;
+        const float c_legs = pair_sum(lc);
+        // ---- A: the waist subtree from the arm warp; base solve ----
+        pair_sync(bar);
+        float a[28];
+        rec_load<7>(recA, a);
+        Art<float> IA0;
+        body_inertia(load_body(M, 0), IA0);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) IA0.A[t] = (IA0.A[t] + carry.A[t]) + a[t];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) IA0.B[t] = (IA0.B[t] + carry.B[t]) + a[6 + t];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) IA0.C[t] = (IA0.C[t] + carry.C[t]) + a[15 + t];
+        p0n = (p0n + cpn) + v3(a[21], a[22], a[23]);
+        p0f = (p0f + cpf) + v3(a[24], a[25], a[26]);
+        const float c_arms = a[27];
+        const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
+        V3<float> aw, av;
+        {
+            const float rhs[6] = {-p0n.x, -p0n.y, -p0n.z, -p0f.x, -p0f.y, -p0f.z};
+            float x[6];
+            art_solve(IA0, rhs, x);
+            aw = v3(x[0], x[1], x[2]);
+            av = v3(x[3], x[4], x[5]);
+        }
+        // ---- running cost on the pre-step state ----
+        {
+            const float vx = B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z;
+            const float dv = vx - M.vx_des;
+            const float c = (c_legs + c_arms) + M.w_vx * dv * dv;
+            const float y = c - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        // ---- base: semi-implicit Euler, quaternion exponential; B to the arm warp ----
+        w = w + dt * aw;
+        vl = vl + dt * (av + g_b);
+        p = p + dt * mul(B.R, vl);
+        {
+            const float wn = sqrtf(dot(w, w));
+            float dq0, dqs;
+            if (wn * dt < 1e-12f) {
+                dq0 = 1.f;
+                dqs = 0.5f * dt;
+            } else {
+                float sh, ch;
+                fast_sincos(0.5f * wn * dt, &sh, &ch);
+                dq0 = ch;
+                dqs = __fdividef(sh, wn);
+            }
+            const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
+            const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
+            const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
+            const float ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
+            const float nz = qw * dz + qx * dy - qy * dx + qz * dq0;
+            const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
+            qw = nw * inv;
+            qx = nx * inv;
+            qy = ny * inv;
+            qz = nz * inv;
+        }
+        B.R = quat_to_R(qw, qx, qy, qz);
+        B.p = p;
+        B.w = w;
+        B.v = vl;
+        put_base(recB, aw, av, B);
+        pair_sync(bar);
+        // ---- pass 3 and the legs' joints ----
+        float qdd[LEN];
+        {
+            V3<float> apw = aw, apv = av;
+            static_for<0, LEN>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                qdd[j] = body_pass3<false, split_axis<0, j>(), split_offset<0, j>()>(load_body(M, b0 + j), mem[j], apw,
+                                                                                   apv);
+            });
+        }
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) {
+            qd[j] += dt * qdd[j];
+            q[j] += dt * qd[j];
+        }
+    }
+    if (PAPER) {  // terminal cost
+        const float y = terminal_cost(M, p, p_start, H, dt) - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    if (xf) {
+        if (lead) {
+            xf[0] = p.x;
+            xf[1] = p.y;
+            xf[2] = p.z;
+            xf[3] = qw;
+            xf[4] = qx;
+            xf[5] = qy;
+            xf[6] = qz;
+            xf[nq] = vl.x;
+            xf[nq + 1] = vl.y;
+            xf[nq + 2] = vl.z;
+            xf[nq + 3] = w.x;
+            xf[nq + 4] = w.y;
+            xf[nq + 5] = w.z;
+        }
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) {
+            xf[7 + b0 - 1 + j] = q[j];
+            xf[nq + 6 + b0 - 1 + j] = qd[j];
+        }
+    }
+    return sum;
+}
+
+// Arm warp: the waist (replicated on both lanes) and one arm per lane. Returns 0; the
+// sample's cost is the leg warp's.
+template <bool PAPER>
+__device__ __noinline__ float split_arms(const DevModel<float>& M, int side, float* recA, const float* recB, int bar,
+                                         const double* __restrict__ x0,
+                                         const float* __restrict__ knots, int H, int nk, float dt, float dtk,
+                                         double* __restrict__ xf) {
+    constexpr int LEN = SPLIT_ARM;
+    const int nj = M.nb - 1, nq = 7 + nj;
+    const int b0 = M.lane_b0[2 + side];
+    const int bb = M.branch_body;
+    const bool lead = side == 0;
+    float qb = (float)x0[7 + bb - 1], qdb = (float)x0[nq + 6 + bb - 1];
+    float q[LEN], qd[LEN];
+#pragma unroll
+    for (int j = 0; j < LEN; ++j) {
+        q[j] = (float)x0[7 + b0 - 1 + j];
+        qd[j] = (float)x0[nq + 6 + b0 - 1 + j];
+    }
+    const float inv_dtk = 1.0f / dtk;
+    const int cb = M.cost_body;
+    const ArtProj leafp = leaf_projection<split_axis<1, LEN - 1>()>(load_body(M, b0 + LEN - 1));
+    SegPoly kc[LEN], kb;
+    int kcur = -1;
+    Pose B;
+    V3<float> aw, av;
+    pair_sync(bar);
+    get_base(recB, aw, av, B);
+    const float inv_H = 1.0f / (float)H;
+    int k = 0, rem = -(nk - 1);
+    for (int h = 0; h < H; ++h) {
+        rem += nk - 1;
+        while (rem >= H) {
+            rem -= H;
+            ++k;
+        }
+        const float s = (float)rem * inv_H;
+        if (k != kcur) {
+            kcur = k;
+#pragma unroll
+            for (int j = 0; j < LEN; ++j) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
+            kb = seg_poly(seg_knots(knots, nj, k, bb), dtk);
+        }
+        float tau[LEN];
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
+        const float taub = poly_pd(load_body(M, bb), kb, s, inv_dtk, qb, qdb);
+        // ---- pass 1: waist, then the arm ----
+        float pc = 0.f, tz = 0.f, tt = 0.f;
+        BodyMem mb;
+        Pose PB;
+        body_pass1<false, PAPER, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(M, load_body(M, bb), qb, qdb, B, PB, mb, pc, lead);
+        if (cb == bb && lead) cost_terms(M, PB, tz, tt);
+        BodyMem mem[LEN];
+        {
+            Pose Pp = PB;
+            static_for<0, LEN>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                Pose P;
+                body_pass1<false, PAPER, split_axis<1, j>(), split_offset<1, j>()>(M, load_body(M, b0 + j), q[j], qd[j],
+                                                                                 Pp, P, mem[j], pc, true);
+                if (cb == b0 + j) cost_terms(M, P, tz, tt);
+                Pp = P;
+            });
+        }
+        // ---- pass 2: the arm inward, both arms summed at the waist, the waist ----
+        Art<float> carry;
+        V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
+        static_for<0, LEN>([&](auto ic) {
+            constexpr int j = LEN - 1 - decltype(ic)::value;
+            if constexpr (j == LEN - 1)
+                body_pass2<false, split_axis<1, j>(), split_offset<1, j>(), true>(load_body(M, b0 + j), tau[j], mem[j],
+                                                                                false, carry, cpn, cpf, &leafp);
+            else
+                body_pass2<false, split_axis<1, j>(), split_offset<1, j>()>(load_body(M, b0 + j), tau[j], mem[j], true,
+                                                                          carry, cpn, cpf);
+        });
+        pair_sum(carry, cpn, cpf);
+        body_pass2<false, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(load_body(M, bb), taub, mb, true, carry, cpn, cpf);
+        float te = 0.f;
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) te += tau[j] * tau[j];
+        if (lead) te += taub * taub;
+        float lc = (tz + tt) + M.w_tau * te;
+        if (PAPER) lc += pc;
+        {
+            const float v[28] = {carry.A[0], carry.A[1], carry.A[2], carry.A[3], carry.A[4], carry.A[5], carry.B[0],
+                                 carry.B[1], carry.B[2], carry.B[3], carry.B[4], carry.B[5], carry.B[6], carry.B[7],
+                                 carry.B[8], carry.C[0], carry.C[1], carry.C[2], carry.C[3], carry.C[4], carry.C[5],
+                                 cpn.x,      cpn.y,      cpn.z,      cpf.x,      cpf.y,      cpf.z,      pair_sum(lc)};
+            rec_store<7>(recA, v);
+        }
+        pair_sync(bar);  // A: the leg warp may read
+        pair_sync(bar);  // B: base acceleration and next pose written
+        Pose Bn;
+        get_base(recB, aw, av, Bn);
+        // ---- pass 3 and the waist's and arm's joints ----
+        float qdd[LEN], qddb;
+        {
+            V3<float> apw = aw, apv = av;
+            qddb = body_pass3<false, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(load_body(M, bb), mb, apw, apv);
+            static_for<0, LEN>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                qdd[j] = body_pass3<false, split_axis<1, j>(), split_offset<1, j>()>(load_body(M, b0 + j), mem[j], apw,
+                                                                                   apv);
+            });
+        }
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) {
+            qd[j] += dt * qdd[j];
+            q[j] += dt * qd[j];
+        }
+        qdb += dt * qddb;
+        qb += dt * qdb;
+        B = Bn;
+    }
+    if (xf) {
+        if (lead) {
+            xf[7 + bb - 1] = qb;
+            xf[nq + 6 + bb - 1] = qdb;
+        }
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) {
+            xf[7 + b0 - 1 + j] = q[j];
+            xf[nq + 6 + b0 - 1 + j] = qd[j];
+        }
+    }
+    return 0.f;
+}
+
+// One warp pair's rollout of 16 samples: warp 2p + 0 the legs, 2p + 1 the waist and arms.
+// rec = this pair's exchange area (SPLIT_PAIR_FLOATS floats of shared memory), bar its
+// named barrier; every lane of both warps must call it the same number of times.
+template <bool PAPER>
+__device__ __forceinline__ float split_rollout(const DevModel<float>& M, int role, int lane, float* rec, int bar,
+                                               const double* __restrict__ x0, const float* __restrict__ knots, int H,
+                                               int nk, float dt, float dtk, double* __restrict__ xf) {
+    const int i = lane >> 1, side = lane & 1;
+    float* recA = rec + i * SPLIT_REC;
+    float* recB = rec + (SPLIT_SPP + i) * SPLIT_REC;
+    return role == 0 ? split_legs<PAPER>(M, side, recA, recB, bar, x0, knots, H, nk, dt, dtk, xf)
+                     : split_arms<PAPER>(M, side, recA, recB, bar, x0, knots, H, nk, dt, dtk, xf);
+}
+
+}  // namespace mppi

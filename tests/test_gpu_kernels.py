@@ -244,6 +244,46 @@ def test_chain_axis_plans(M, orc, tilt):
     assert err.max() < 1e-4 and err_f.max() < 1e-4
 
 
+@pytest.mark.parametrize("variant", ["layout", "tilted", "offset"])
+def test_humanoid_axis_plans(M, orc, variant):
+    # the humanoid's joint layout (legs z, x, y, y, y, x; waist z; arms y, x, z, y) selects
+    # the two-warp split kernel (axis plan 2); a tilted hip axis or an elbow offset off its
+    # axis selects the one-warp generic chain kernel. Both agree with the oracle, and the
+    # split kernel gives the same bits at every block size and rejects 32-thread blocks.
+    p = S.humanoid_problem(n=200)
+    p.horizon = 60
+    m = p.model
+    if variant == "tilted":
+        axis = m.axis.copy()
+        axis[1] = np.array([0.05, 0.0, 1.0]) / np.linalg.norm([0.05, 0.0, 1.0])
+        m = m.copy(axis=axis)
+    elif variant == "offset":
+        jpos = m.jpos.copy()
+        jpos[m.nb - 1, 0] = 0.01
+        m = m.copy(jpos=jpos)
+    p.model = m
+    mod = M.Model(m)
+    assert mod.info()["topology"] == 2
+    assert mod.info()["axis_plan"] == (2 if variant == "layout" else 0)
+    kn = orc.sample_knots(m.nj, p.nk, p.n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed).astype(np.float32)
+    c = M.Controller.from_problem(mod, p, mapping=M.MPPI_MAP_CHAIN)
+    got, fin = c.rollout_explicit(p.state, kn, finals=True)
+    ref_c, ref_f = orc.rollout_batch(m, p.state, kn.astype(np.float64), p.horizon, p.dt, finals=True)
+    err = np.abs(got - ref_c) / np.abs(ref_c)
+    err_f = np.max(np.abs(fin - ref_f), axis=1) / np.max(np.abs(ref_f), axis=1)
+    print(f"humanoid {variant}, axis plan {mod.info()['axis_plan']}: cost rel. error median {np.median(err):.2e} "
+          f"max {err.max():.2e}, final state max {err_f.max():.2e}")
+    assert err.max() < 1e-4 and err_f.max() < 1e-4
+    if variant == "layout":
+        for block in (64, 256):
+            c.set_mapping(M.MPPI_MAP_CHAIN, block)
+            g2, f2 = c.rollout_explicit(p.state, kn, finals=True)
+            np.testing.assert_array_equal(g2, got)
+            np.testing.assert_array_equal(f2, fin)
+        with pytest.raises(M.MppiError):
+            c.set_mapping(M.MPPI_MAP_CHAIN, 32)
+
+
 # ------------------------------------------------------------------------------------
 # Weights and average
 # ------------------------------------------------------------------------------------
