@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-receding", action="store_true", help="skip the receding-horizon cycle timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--no-configs", action="store_true", help="skip the other single-instance configurations")
+    ap.add_argument("--only-config", default=None, choices=sorted(CONFIGS),
+                    help="time one single-instance configuration alone and print its result (for profiling)")
     return ap.parse_args()
 
 
@@ -258,12 +260,12 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
-def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1, spline=0):
+def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1, spline=0, block=0):
     """One instance's solve timed on its stream (CUDA events, L2 flushed between solves),
     plus its rollout kernel's in-graph duration."""
     stream = torch.cuda.Stream()
     ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream, mapping=mapping,
-                                        spline=spline)
+                                        spline=spline, block=block)
     ctrl.profile(True)
     x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
     out = torch.zeros(ctrl.E, dtype=torch.float32, device="cuda")
@@ -311,16 +313,34 @@ def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1,
             "flops_per_step_sample": fl_step}
 
 
+# the other single-instance configurations: name -> (problem, spline variant)
+CONFIGS = {
+    "plain_quadruped_K32": (lambda S: S.plain_quadruped(), 0),
+    "scale_quadruped_K1024": (lambda S: S.scale_quadruped(n=1024), 0),
+    "scale_quadruped_K4096": (lambda S: S.scale_quadruped(n=4096), 0),
+    "humanoid_K2048": (lambda S: S.humanoid_problem(), 0),
+    "paper_cost_walking_K8192": (lambda S: S.paper_walking(), 0),
+    "scale_quadruped_K8192_natural_cubic_spline": (lambda S: S.scale_quadruped(), 1),
+}
+
+
 def other_configs(mppi, synth, torch, flops):
-    out = {}
-    out["plain_quadruped_K32"] = single_instance(mppi, synth, torch, flops, synth.plain_quadruped())
-    for n in (1024, 4096):
-        out[f"scale_quadruped_K{n}"] = single_instance(mppi, synth, torch, flops, synth.scale_quadruped(n=n))
-    out["humanoid_K2048"] = single_instance(mppi, synth, torch, flops, synth.humanoid_problem())
-    out["paper_cost_walking_K8192"] = single_instance(mppi, synth, torch, flops, synth.paper_walking())
-    out["scale_quadruped_K8192_natural_cubic_spline"] = single_instance(mppi, synth, torch, flops,
-                                                                        synth.scale_quadruped(), spline=1)
-    return out
+    return {name: single_instance(mppi, synth, torch, flops, make(synth), spline=spline)
+            for name, (make, spline) in CONFIGS.items()}
+
+
+def run_one_config(args):
+    import torch
+
+    from paper_2511_19204_gb300 import build as B
+    from paper_2511_19204_gb300 import flops, mppi, synth
+    B.build()
+    mppi.load()
+    make, spline = CONFIGS[args.only_config]
+    r = single_instance(mppi, synth, torch, flops, make(synth), reps=args.steps, warmup=args.warmup,
+                        mapping=args.mapping, spline=spline, block=args.block)
+    print(json.dumps({"config": args.only_config, **r}))
+    return 0
 
 
 def receding_extra(mppi, synth, torch, p, reps=20, warmup=3, delays=(1, 5, 20)):
@@ -667,6 +687,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only_config:
+        return run_one_config(args)
     return run_ours(args, rank, world, local)
 
 

@@ -538,12 +538,15 @@ __device__ __forceinline__ void art_project(const BodyConst& C, const Art<float>
     P.Ia.C[5] = IA.C[5] - ul.y * x1.z;
 }
 
-template <int AX>
+// PIN keeps the projection in registers for the whole rollout; without it the compiler may
+// recompute it where registers are short.
+template <int AX, bool PIN = true>
 __device__ __forceinline__ ArtProj leaf_projection(const BodyConst& C) {
     Art<float> IA;
     body_inertia(C, IA);
     ArtProj P;
     art_project<AX>(C, IA, P);
+    if (!PIN) return P;
 #pragma unroll
     for (int t = 0; t < 6; ++t) pin(P.Ia.A[t]);
 #pragma unroll

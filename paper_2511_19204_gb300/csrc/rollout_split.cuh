@@ -124,9 +124,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     const float inv_dtk = 1.0f / dtk;
     float sum = 0.f, comp = 0.f;
     const int cb = M.cost_body;
-    const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>()>(load_body(M, b0 + LEN - 1));
-    SegPoly kc[LEN];
-    int kcur = -1;
+    const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     Pose B;
     B.R = quat_to_R(qw, qx, qy, qz);
     B.p = p;
@@ -143,14 +141,11 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             ++k;
         }
         const float s = (float)rem * inv_H;
-        if (k != kcur) {
-            kcur = k;
-#pragma unroll
-            for (int j = 0; j < LEN; ++j) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
-        }
+        // the legs read their segment knots each step (fewer registers held across the step)
         float tau[LEN];
 #pragma unroll
-        for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
+        for (int j = 0; j < LEN; ++j)
+            tau[j] = hermite_pd(load_body(M, b0 + j), seg_knots(knots, nj, k, b0 + j), s, dtk, inv_dtk, q[j], qd[j]);
         // ---- pass 1: base, then the leg ----
         V3<float> p0n, p0f;
         float pc = 0.f;  // this lane's share of the modular running cost
@@ -328,7 +323,7 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
     }
     const float inv_dtk = 1.0f / dtk;
     const int cb = M.cost_body;
-    const ArtProj leafp = leaf_projection<split_axis<1, LEN - 1>()>(load_body(M, b0 + LEN - 1));
+    const ArtProj leafp = leaf_projection<split_axis<1, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     SegPoly kc[LEN], kb;
     int kcur = -1;
     Pose B;

@@ -45,6 +45,14 @@ setpoint from a power-basis form of its segment (formed once per segment). Per s
         10), shift 32, force transform 16, pass 3 36, the rest as the hip               481
   calf  (y axis, offset along z, leaf): as the thigh without the child accumulation,
         D and the projection (u 1 instead of 3 + 48)                                  404
+Humanoids of the usual layout (legs turning about z, x, y, y, y, x; a waist about z; arms
+about y, x, z, y; offsets in the yz-plane, on one axis or zero) run the two-warp split
+kernel with the same specialisations; a zero offset drops the origin, the offset cross
+products and the congruence shift, and legs evaluate their setpoints in the Hermite form
+(55) where arms and waist use the power-basis form (20). Per step:
+  leg:   yaw 568, roll 516, thigh 466, shin 516, ankle 516, foot (leaf) 389           2971
+  arm:   shoulder pitch 533, shoulder roll 481, upper arm 431, forearm (leaf) 404    1849
+  waist: two children (54), offset along z                                             508
 """
 from __future__ import annotations
 
@@ -58,6 +66,48 @@ MOD_WEIGHTS = ("w_h", "w_orient", "w_q", "w_cvel", "w_cforce", "w_term")
 PER_JOINT_XYY_HIP = 20 + 1 + 51 + 4 + 78 + 27 + (3 + 48 + 61 + 174 + 20) + 40 + 4 + 2
 PER_JOINT_XYY_THIGH = 20 + 1 + 41 + 4 + 78 + 27 + (3 + 48 + 61 + 140 + 16) + 36 + 4 + 2
 PER_JOINT_XYY_CALF = 20 + 1 + 41 + 4 + 78 + 0 + (1 + 0 + 61 + 140 + 16) + 36 + 4 + 2
+
+# split humanoid kernel: (setpoint, pass 1, child accumulation, pass 2, pass 3) per body,
+# each plus sincos 1, velocity product 4, bias 78, Euler 4, effort 2
+_SPLIT_FIXED = 1 + 4 + 78 + 4 + 2
+PER_JOINT_HUM_LEG = [55 + 51 + 27 + 306 + 40, 55 + 41 + 27 + 268 + 36, 55 + 31 + 27 + 232 + 32,
+                     55 + 41 + 27 + 268 + 36, 55 + 41 + 27 + 268 + 36, 55 + 31 + 0 + 182 + 32]
+PER_JOINT_HUM_ARM = [20 + 51 + 27 + 306 + 40, 20 + 41 + 27 + 268 + 36, 20 + 31 + 27 + 232 + 32,
+                     20 + 41 + 0 + 218 + 36]
+PER_JOINT_HUM_WAIST = 20 + 41 + 54 + 268 + 36
+
+
+def axis_plan_hum(model) -> bool:
+    """True when the model runs the two-warp split kernel: a floating base with 2 legs of 6
+    bodies, a waist body on the base carrying 2 arms of 4, axes and offsets as above."""
+    import numpy as np
+    if model.fixed_base or model.nb != 22:
+        return False
+    e = np.eye(3)
+    par = list(model.parent)
+    if par[13] != 0 or any(par[1 + 6 * l] != 0 for l in range(2)) or any(par[14 + 4 * l] != 13 for l in range(2)):
+        return False
+
+    def chain(b0, n):
+        return all(par[b0 + j] == b0 + j - 1 for j in range(1, n))
+
+    def off(b, kind):   # kind: axis index, "yz" or "zero"
+        r = model.jpos[b]
+        if kind == "zero":
+            return not np.any(r)
+        if kind == "yz":
+            return r[0] == 0.0
+        return all(r[i] == 0.0 for i in range(3) if i != kind)
+
+    legs = [(2, "yz"), (0, 2), (1, "zero"), (1, 2), (1, 2), (0, "zero")]
+    arms = [(1, "yz"), (0, 1), (2, "zero"), (1, 2)]
+    for b0, plan in [(1, legs), (7, legs), (14, arms), (18, arms)]:
+        if not chain(b0, len(plan)):
+            return False
+        for j, (ax, kind) in enumerate(plan):
+            if not (np.array_equal(model.axis[b0 + j], e[ax]) and off(b0 + j, kind)):
+                return False
+    return bool(np.array_equal(model.axis[13], e[2]) and off(13, 2))
 
 
 def axis_plan_xyy(model) -> bool:
@@ -88,10 +138,13 @@ def flops_per_step(model, contacts_active=None, mapping_chain=True) -> int:
     """Flops of one step of one sample. ``contacts_active`` defaults to every contact
     point (the standing / walking regime); pass a number for another regime.
     ``mapping_chain``: the rollout runs the lanes-per-chain kernel (which specialises the
-    axes of x, y, y quadrupeds)."""
+    axes of x, y, y quadrupeds and of the usual humanoid layout)."""
     nc = model.nc if contacts_active is None else contacts_active
     if mapping_chain and axis_plan_xyy(model):
         joints = 4 * (PER_JOINT_XYY_HIP + PER_JOINT_XYY_THIGH + PER_JOINT_XYY_CALF)
+    elif mapping_chain and axis_plan_hum(model):
+        joints = (2 * sum(PER_JOINT_HUM_LEG) + 2 * sum(PER_JOINT_HUM_ARM) + PER_JOINT_HUM_WAIST
+                  + 21 * _SPLIT_FIXED)
     else:
         joints = PER_JOINT * model.nj
     f = joints + PER_CONTACT * nc + PER_BASE
