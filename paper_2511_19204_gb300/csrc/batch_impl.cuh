@@ -458,7 +458,7 @@ int batch_tile(int mapping) {
 }
 
 // Writes the image (queue header, descriptors pointing at each context's buffers, the
-// prefill list with the largest instances first, and the packed inputs) into `img`.
+// prefill list with the longest tiles first, and the packed inputs) into `img`.
 void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double* const* states,
                       const float* const* warm, unsigned char* img, std::vector<size_t>* in_off,
                       std::vector<size_t>* out_off) {
@@ -524,8 +524,13 @@ void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double*
         ooff += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
         order[i] = i;
     }
-    // largest instances first: the long rollouts start early and the tail stays short
+    // longest tiles first (a tile lasts about H steps of a cost that grows with the body
+    // count), then the largest instances: the long rollouts start early and the queue ends
+    // on short tiles, which keeps the tail of the launch short
+    std::vector<long> tile_cost(L.count);
+    for (int i = 0; i < L.count; ++i) tile_cost[i] = (long)hi[i].H * ctxs[i]->model->nb;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (tile_cost[a] != tile_cost[b]) return tile_cost[a] > tile_cost[b];
         return (long)hi[a].N * hi[a].H > (long)hi[b].N * hi[b].H;
     });
     int* pre = reinterpret_cast<int*>(img + L.o_pre);
