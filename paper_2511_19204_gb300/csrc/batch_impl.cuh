@@ -9,9 +9,18 @@
 // functions as the per-instance kernels, so each instance's result is bit-identical to
 // its mppi_solve result.
 //
-// Progress needs no co-residency: a block waits only for an item whose producer is a
-// block that has already taken and finished its own item and publishes without waiting.
-// Every wait is bounded by the global timer and sets an error word when it gives up.
+// The instances of a batch are grouped by rollout variant (mapping, axis plan, modular
+// cost on or off) and each group walks its own queue in its own instantiation of the
+// persistent kernel, the groups' kernels running side by side on a share of the SMs in
+// proportion to their estimated work. A kernel that can call several rollout functions
+// gets fewer registers for each (ptxas spilled 450-950 bytes per rollout function when
+// all variants shared one kernel, none with one variant per kernel; a quadruped-only batch
+// ran 18 % faster).
+//
+// Progress needs no co-residency: a block waits only for an item of its own queue whose
+// producer is a block that has already taken and finished its own item and publishes
+// without waiting. Every wait is bounded by the global timer and sets an error word when
+// it gives up.
 #pragma once
 #include <cuda_runtime.h>
 #include <string.h>
@@ -70,6 +79,15 @@ struct BatchQueue {
     int head, append, total, nprefill;
     uint32_t error, pad0, pad1, pad2;
 };
+
+// Where a group's queue, items and prefill list sit in the device block (byte offsets).
+struct GroupDev {
+    long long q, items, pre;
+};
+
+// Rollout variants of batched instances: one persistent kernel instantiation each.
+constexpr int BV_XYY = 0, BV_XYY_P = 1, BV_QUAD = 2, BV_QUAD_P = 3, BV_HUMG = 4, BV_HUMG_P = 5, BV_SPLIT = 6,
+              BV_SPLIT_P = 7, BV_HALF = 8, BV_WARP = 9, BV_COUNT = 10;
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -152,6 +170,51 @@ __device__ __forceinline__ FinalizeArgs finalize_args(const BatchInst& I, int it
     return f;
 }
 
+// One tile's rollouts in variant V (the instance's mapping, axis plan and cost).
+template <int V>
+__device__ __forceinline__ void rollout_tile(const DevModel<float>& M, const BatchInst& I, int n0, int last_n,
+                                             float* work) {
+    if constexpr (V == BV_SPLIT || V == BV_SPLIT_P) {
+        // two-warp split: 4 pairs of 16 samples; `work` is free again after the noise pass
+        static_assert(4 * SPLIT_PAIR_FLOATS <= 27 * BATCH_THREADS, "split exchange area exceeds work");
+        static_assert(BATCH_THREADS / 4 == 4 * SPLIT_SPP, "tile = 4 warp pairs");
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pair = warp >> 1;
+        const int n = n0 + pair * SPLIT_SPP + (lane >> 1);
+        const int ne = min(n, last_n);
+        const float* kn = I.knots + (size_t)ne * I.E;
+        float* rec = work + pair * SPLIT_PAIR_FLOATS;
+        const float c =
+            split_rollout<V == BV_SPLIT_P>(M, warp & 1, lane, rec, 1 + pair, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+        if (n <= last_n && (warp & 1) == 0 && (lane & 1) == 0) I.costs[n] = c;
+    } else if constexpr (V <= BV_HUMG_P) {
+        const int g = threadIdx.x & 3;
+        const int n = n0 + (threadIdx.x >> 2);
+        const int ne = min(n, last_n);
+        const float* kn = I.knots + (size_t)ne * I.E;
+        constexpr bool paper = V == BV_XYY_P || V == BV_QUAD_P || V == BV_HUMG_P;
+        float c;
+        if constexpr (V == BV_XYY || V == BV_XYY_P)
+            c = lanes_rollout<3, false, paper, AXP_XYY>(M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+        else if constexpr (V == BV_QUAD || V == BV_QUAD_P)
+            c = lanes_rollout<3, false, paper, AXP_GENERIC>(M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+        else
+            c = lanes_rollout<6, true, paper, AXP_GENERIC>(M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
+        if (n <= last_n && g == 0) I.costs[n] = c;
+    } else {
+        constexpr int G = V == BV_HALF ? 16 : 32;
+        const int gl = threadIdx.x & (G - 1);
+        const int n = n0 + (threadIdx.x / G);
+        const int ne = min(n, last_n);
+        LaneConst<float> L;
+        load_lane_const(M, gl, L);
+        const float c = warp_rollout<float, G, double>(M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H, I.H, I.nk,
+                                                       I.dt, I.dtk, work, nullptr);
+        if (n <= last_n && gl == 0) I.costs[n] = c;
+    }
+}
+
+template <int V>
 __global__ void __launch_bounds__(BATCH_THREADS, 1)
     persistent_kernel(const BatchInst* __restrict__ insts, InstCounters* ctr, QueueItem* items, BatchQueue* q,
                       uint64_t budget_ns) {
@@ -236,66 +299,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
             np.spline = I.spline;
             for (int s0 = 0; s0 < cnt; s0 += NOISE_SPB) block_sample_knots(np, n0 + s0, min(NOISE_SPB, cnt - s0), work);
             // rollouts of the tile with the instance's mapping
-            const int last_n = n0 + cnt - 1;
-            if (I.mapping == MPPI_MAP_CHAIN && M->axis_plan == AXP_HUM) {
-                // two-warp split: 4 pairs of 16 samples; `work` is free again after the
-                // noise pass
-                static_assert(4 * SPLIT_PAIR_FLOATS <= 27 * BATCH_THREADS, "split exchange area exceeds work");
-                static_assert(BATCH_THREADS / 4 == 4 * SPLIT_SPP, "tile = 4 warp pairs");
-                __syncthreads();
-                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pair = warp >> 1;
-                const int n = n0 + pair * SPLIT_SPP + (lane >> 1);
-                const int ne = min(n, last_n);
-                const float* kn = I.knots + (size_t)ne * I.E;
-                float* rec = work + pair * SPLIT_PAIR_FLOATS;
-                const float c = M->paper_cost
-                                    ? split_rollout<true>(*M, warp & 1, lane, rec, 1 + pair, I.x0, kn, I.H, I.nk, I.dt,
-                                                          I.dtk, nullptr)
-                                    : split_rollout<false>(*M, warp & 1, lane, rec, 1 + pair, I.x0, kn, I.H, I.nk, I.dt,
-                                                           I.dtk, nullptr);
-                if (n <= last_n && (warp & 1) == 0 && (lane & 1) == 0) I.costs[n] = c;
-            } else if (I.mapping == MPPI_MAP_CHAIN) {
-                const int g = threadIdx.x & 3;
-                const int n = n0 + (threadIdx.x >> 2);
-                const int ne = min(n, last_n);
-                const float* kn = I.knots + (size_t)ne * I.E;
-                float c;
-                if (M->topology == TOPO_QUADRUPED) {
-                    if (M->axis_plan == AXP_XYY)
-                        c = M->paper_cost
-                                ? lanes_rollout<3, false, true, AXP_XYY>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
-                                : lanes_rollout<3, false, false, AXP_XYY>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk,
-                                                                          nullptr);
-                    else
-                        c = M->paper_cost ? lanes_rollout<3, false, true, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk, I.dt,
-                                                                                      I.dtk, nullptr)
-                                          : lanes_rollout<3, false, false, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk,
-                                                                                       I.dt, I.dtk, nullptr);
-                } else {
-                    c = M->paper_cost
-                            ? lanes_rollout<6, true, true, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr)
-                            : lanes_rollout<6, true, false, AXP_GENERIC>(*M, g, I.x0, kn, I.H, I.nk, I.dt, I.dtk, nullptr);
-                }
-                if (n <= last_n && g == 0) I.costs[n] = c;
-            } else if (I.mapping == MPPI_MAP_HALFWARP) {
-                const int gl = threadIdx.x & 15;
-                const int n = n0 + (threadIdx.x >> 4);
-                const int ne = min(n, last_n);
-                LaneConst<float> L;
-                load_lane_const(*M, gl, L);
-                const float c = warp_rollout<float, 16, double>(*M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H,
-                                                                I.H, I.nk, I.dt, I.dtk, work, nullptr);
-                if (n <= last_n && gl == 0) I.costs[n] = c;
-            } else {
-                const int gl = threadIdx.x & 31;
-                const int n = n0 + (threadIdx.x >> 5);
-                const int ne = min(n, last_n);
-                LaneConst<float> L;
-                load_lane_const(*M, gl, L);
-                const float c = warp_rollout<float, 32, double>(*M, L, gl, I.x0, I.knots + (size_t)ne * I.E, I.H,
-                                                                I.H, I.nk, I.dt, I.dtk, work, nullptr);
-                if (n <= last_n && gl == 0) I.costs[n] = c;
-            }
+            rollout_tile<V>(*M, I, n0, n0 + cnt - 1, work);
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) s_last = atomicAdd(&ctr[ii].done_roll, 1) == I.ntiles - 1;
@@ -334,24 +338,30 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
     }
 }
 
-// Reset of a batch before the persistent launch: queue counters, prefilled iteration-0
-// ROLLOUT items, per-instance counters and solve state (as solve_begin), and the inputs
-// scattered from the packed host record: state [nx] doubles, then (if flagged) the warm
-// start [E] floats into the nominal.
+// Reset of a batch before the persistent launches: each group's queue counters and its
+// prefilled iteration-0 ROLLOUT items, per-instance counters and solve state (as
+// solve_begin), and the inputs scattered from the packed host record: state [nx] doubles,
+// then (if flagged) the warm start [E] floats into the nominal.
 __global__ void batch_reset_kernel(const BatchInst* __restrict__ insts, int count, InstCounters* ctr,
-                                   QueueItem* items, BatchQueue* q, const int* __restrict__ prefill,
+                                   const GroupDev* __restrict__ groups, int ngroups, unsigned char* base,
                                    const unsigned char* __restrict__ packed_in) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
-    for (int k = tid; k < q->total; k += nth) {
-        if (k < q->nprefill) {
-            items[k].type = ITEM_ROLLOUT;
-            items[k].inst = prefill[2 * k];
-            items[k].idx = prefill[2 * k + 1];
-            items[k].ready = 1;
-        } else {
-            items[k].type = 0;
-            items[k].ready = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        BatchQueue* q = reinterpret_cast<BatchQueue*>(base + groups[g].q);
+        QueueItem* items = reinterpret_cast<QueueItem*>(base + groups[g].items);
+        const int* prefill = reinterpret_cast<const int*>(base + groups[g].pre);
+        const int total = q->total, npre = q->nprefill;
+        for (int k = tid; k < total; k += nth) {
+            if (k < npre) {
+                items[k].type = ITEM_ROLLOUT;
+                items[k].inst = prefill[2 * k];
+                items[k].idx = prefill[2 * k + 1];
+                items[k].ready = 1;
+            } else {
+                items[k].type = 0;
+                items[k].ready = 0;
+            }
         }
     }
     for (int i = blockIdx.x; i < count; i += gridDim.x) {
@@ -377,7 +387,10 @@ __global__ void batch_reset_kernel(const BatchInst* __restrict__ insts, int coun
             I.solve->status = MPPI_OK;
         }
     }
-    if (tid == 0) {
+    // head, append and error are read by no thread of this kernel (total and nprefill,
+    // which are, stay as the image set them)
+    if (tid < ngroups) {
+        BatchQueue* q = reinterpret_cast<BatchQueue*>(base + groups[tid].q);
         q->head = 0;
         q->append = q->nprefill;
         q->error = 0;
@@ -385,10 +398,14 @@ __global__ void batch_reset_kernel(const BatchInst* __restrict__ insts, int coun
 }
 
 // Outputs of every instance into one packed record per instance: result, mean [E],
-// best [E]; and the queue's error word at offset 0.
-__global__ void batch_gather_kernel(const BatchInst* __restrict__ insts, int count, const BatchQueue* q,
-                                    unsigned char* __restrict__ packed_out) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<uint32_t*>(packed_out) = q->error;
+// best [E]; and the groups' error words (or-ed) at offset 0.
+__global__ void batch_gather_kernel(const BatchInst* __restrict__ insts, int count, const GroupDev* __restrict__ groups,
+                                    int ngroups, const unsigned char* base, unsigned char* __restrict__ packed_out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t err = 0;
+        for (int g = 0; g < ngroups; ++g) err |= reinterpret_cast<const BatchQueue*>(base + groups[g].q)->error;
+        *reinterpret_cast<uint32_t*>(packed_out) = err;
+    }
     for (int i = blockIdx.x; i < count; i += gridDim.x) {
         const BatchInst& I = insts[i];
         unsigned char* rec = packed_out + I.out_off;
@@ -411,17 +428,66 @@ __global__ void batch_gather_kernel(const BatchInst* __restrict__ insts, int cou
 // ------------------------------------------------------------------------------------
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+int batch_variant(const mppi_ctx* c) {
+    const DevModel<float>& M = c->model->host_f;
+    const bool paper = M.paper_cost != 0;
+    if (c->mapping == MPPI_MAP_CHAIN) {
+        if (M.axis_plan == AXP_HUM) return paper ? BV_SPLIT_P : BV_SPLIT;
+        if (M.topology == TOPO_QUADRUPED) {
+            if (M.axis_plan == AXP_XYY) return paper ? BV_XYY_P : BV_XYY;
+            return paper ? BV_QUAD_P : BV_QUAD;
+        }
+        return paper ? BV_HUMG_P : BV_HUMG;
+    }
+    return c->mapping == MPPI_MAP_HALFWARP ? BV_HALF : BV_WARP;
+}
+
+// Estimated duration (us) of one of an instance's tiles: H steps of its variant's step
+// time in the persistent kernel (one 256-thread block per SM), measured on GB300 for the
+// specialised chain variants (quadruped 3.2 us, humanoid split 7.5 us, +10 % with the
+// modular cost) and scaled from the per-instance kernels' ratios for the others. Orders
+// the prefill (longest first) and shares the SMs between groups.
+static double step_us(const mppi_ctx* c) {
+    switch (batch_variant(c)) {
+        case BV_XYY: return 3.2;
+        case BV_XYY_P: return 3.5;
+        case BV_QUAD: return 6.5;
+        case BV_QUAD_P: return 7.2;
+        case BV_SPLIT: return 7.5;
+        case BV_SPLIT_P: return 8.2;
+        case BV_HUMG: return 15.0;
+        case BV_HUMG_P: return 16.5;
+        case BV_HALF: return 0.8 * c->model->nb;
+        default: return 1.0 * c->model->nb;
+    }
+}
+static double tile_cost(const mppi_ctx* c) { return c->H * step_us(c); }
+
 BatchLayout layout_batch(mppi_ctx* const* ctxs, int count) {
     BatchLayout L;
     L.count = count;
     long total = 0, nprefill = 0;
     size_t in_bytes = 0, out_bytes = 16;
     int max_E = 0;
+    int gidx[BV_COUNT];
+    for (int v = 0; v < BV_COUNT; ++v) gidx[v] = -1;
     for (int i = 0; i < count; ++i) {
         mppi_ctx* c = ctxs[i];
         const int tile = batch_tile(c->mapping);
         const int ntiles = (c->N + tile - 1) / tile;
-        total += (long)c->iters * (ntiles + num_chunks(c->N));
+        const long items = (long)c->iters * (ntiles + num_chunks(c->N));
+        const int v = batch_variant(c);
+        if (gidx[v] < 0) {
+            gidx[v] = (int)L.groups.size();
+            BatchGroup g;
+            g.variant = v;
+            L.groups.push_back(g);
+        }
+        BatchGroup& g = L.groups[gidx[v]];
+        g.total += items;
+        g.nprefill += ntiles;
+        g.work += (double)c->iters * ntiles * tile_cost(c);
+        total += items;
         nprefill += ntiles;
         in_bytes += ((size_t)8 * c->nx + 16 + 4 * (size_t)c->E + 15) & ~(size_t)15;
         out_bytes += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
@@ -432,9 +498,12 @@ BatchLayout layout_batch(mppi_ctx* const* ctxs, int count) {
     L.max_E = max_E;
     L.in_bytes = in_bytes;
     L.out_bytes = out_bytes;
+    const int ng = (int)L.groups.size();
     size_t off = 0;
+    L.o_groups = off;
+    off += al256(sizeof(GroupDev) * ng);
     L.o_q = off;
-    off += al256(sizeof(BatchQueue));
+    off += al256(sizeof(BatchQueue) * ng);
     L.o_insts = off;
     off += al256(sizeof(BatchInst) * count);
     L.o_pre = off;
@@ -449,6 +518,15 @@ BatchLayout layout_batch(mppi_ctx* const* ctxs, int count) {
     L.o_out = off;
     off += al256(out_bytes);
     L.dev_bytes = off;
+    long pre = 0, it = 0;
+    for (int k = 0; k < ng; ++k) {
+        BatchGroup& g = L.groups[k];
+        g.o_q = L.o_q + sizeof(BatchQueue) * k;
+        g.o_pre = L.o_pre + sizeof(int) * 2 * pre;
+        g.o_items = L.o_items + sizeof(QueueItem) * it;
+        pre += g.nprefill;
+        it += g.total;
+    }
     return L;
 }
 
@@ -462,10 +540,18 @@ int batch_tile(int mapping) {
 void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double* const* states,
                       const float* const* warm, unsigned char* img, std::vector<size_t>* in_off,
                       std::vector<size_t>* out_off) {
-    BatchQueue* q = reinterpret_cast<BatchQueue*>(img + L.o_q);
-    memset(q, 0, sizeof *q);
-    q->total = (int)L.total;
-    q->nprefill = (int)L.nprefill;
+    const int ng = (int)L.groups.size();
+    GroupDev* gd = reinterpret_cast<GroupDev*>(img + L.o_groups);
+    for (int k = 0; k < ng; ++k) {
+        const BatchGroup& g = L.groups[k];
+        BatchQueue* q = reinterpret_cast<BatchQueue*>(img + g.o_q);
+        memset(q, 0, sizeof *q);
+        q->total = (int)g.total;
+        q->nprefill = (int)g.nprefill;
+        gd[k].q = (long long)g.o_q;
+        gd[k].items = (long long)g.o_items;
+        gd[k].pre = (long long)g.o_pre;
+    }
     BatchInst* hi = reinterpret_cast<BatchInst*>(img + L.o_insts);
     size_t ioff = 0, ooff = 16;
     if (in_off) in_off->clear();
@@ -524,23 +610,26 @@ void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double*
         ooff += (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
         order[i] = i;
     }
-    // longest tiles first (a tile lasts about H steps of a cost that grows with the body
-    // count), then the largest instances: the long rollouts start early and the queue ends
-    // on short tiles, which keeps the tail of the launch short
-    std::vector<long> tile_cost(L.count);
-    for (int i = 0; i < L.count; ++i) tile_cost[i] = (long)hi[i].H * ctxs[i]->model->nb;
+    // per group: longest tiles first, then the largest instances: the long rollouts start
+    // early and the queue ends on short tiles, which keeps the tail of the launch short
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        if (tile_cost[a] != tile_cost[b]) return tile_cost[a] > tile_cost[b];
+        const double ta = tile_cost(ctxs[a]), tb = tile_cost(ctxs[b]);
+        if (ta != tb) return ta > tb;
         return (long)hi[a].N * hi[a].H > (long)hi[b].N * hi[b].H;
     });
-    int* pre = reinterpret_cast<int*>(img + L.o_pre);
-    long k = 0;
-    for (int i : order)
-        for (int t = 0; t < hi[i].ntiles; ++t) {
-            pre[2 * k] = i;
-            pre[2 * k + 1] = t;
-            ++k;
+    for (int k = 0; k < ng; ++k) {
+        const BatchGroup& g = L.groups[k];
+        int* pre = reinterpret_cast<int*>(img + g.o_pre);
+        long n = 0;
+        for (int i : order) {
+            if (batch_variant(ctxs[i]) != g.variant) continue;
+            for (int t = 0; t < hi[i].ntiles; ++t) {
+                pre[2 * n] = i;
+                pre[2 * n + 1] = t;
+                ++n;
+            }
         }
+    }
 }
 
 // Packed inputs of instance i only (states / warm starts change between launches).
@@ -556,35 +645,105 @@ void fill_batch_inputs(mppi_ctx* const* ctxs, const BatchLayout& L, const std::v
     }
 }
 
+using PersistentFn = void (*)(const BatchInst*, InstCounters*, QueueItem*, BatchQueue*, uint64_t);
+static const PersistentFn kPersistent[BV_COUNT] = {
+    persistent_kernel<0>, persistent_kernel<1>, persistent_kernel<2>, persistent_kernel<3>, persistent_kernel<4>,
+    persistent_kernel<5>, persistent_kernel<6>, persistent_kernel<7>, persistent_kernel<8>, persistent_kernel<9>};
+
 cudaError_t prepare_batch_kernel(int max_E, size_t* smem, int* per_sm) {
     *smem = batch_smem_bytes(max_E);
-    cudaError_t e =
-        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(992));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel, BATCH_THREADS, *smem);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < BV_COUNT && e == cudaSuccess; ++v)
+        e = cudaFuncSetAttribute(kPersistent[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(992));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kPersistent[BV_XYY], BATCH_THREADS, *smem);
     return e;
 }
 
-// H2D image, reset/scatter, persistent walk, gather, D2H outputs (host image and device
-// block share the layout `L`).
+cudaError_t BatchStreams::ensure(int n) {
+    cudaError_t e = cudaSuccess;
+    if (!fork && (e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    while ((int)aux.size() < n) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaStreamDestroy(st);
+            return e;
+        }
+        aux.push_back(st);
+        join.push_back(ev);
+    }
+    return e;
+}
+
+void BatchStreams::release() {
+    for (cudaStream_t st : aux) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : join) cudaEventDestroy(ev);
+    if (fork) cudaEventDestroy(fork);
+    aux.clear();
+    join.clear();
+    fork = nullptr;
+}
+
+// Blocks per group, in proportion to the groups' estimated work, at least one each and
+// `grid` in all where there are no more groups than that.
+static std::vector<int> group_grids(const BatchLayout& L, int grid) {
+    const int ng = (int)L.groups.size();
+    std::vector<int> out(ng, 1);
+    double W = 0.0;
+    for (const BatchGroup& g : L.groups) W += g.work;
+    if (ng == 0 || grid <= ng || W <= 0.0) return out;
+    int used = 0;
+    for (int k = 0; k < ng; ++k) {
+        out[k] = std::max(1, (int)(grid * L.groups[k].work / W));
+        used += out[k];
+    }
+    // hand the blocks lost to rounding down to the groups with the most work per block
+    while (used < grid) {
+        int best = 0;
+        for (int k = 1; k < ng; ++k)
+            if (L.groups[k].work / out[k] > L.groups[best].work / out[best]) best = k;
+        ++out[best];
+        ++used;
+    }
+    for (int k = 0; k < ng; ++k) out[k] = (int)std::min<long>(out[k], std::max<long>(1, L.groups[k].nprefill));
+    return out;
+}
+
+// H2D image, reset/scatter, the groups' persistent kernels side by side (forked onto the
+// auxiliary streams and joined back), gather, D2H outputs (host image and device block
+// share the layout `L`).
 cudaError_t enqueue_batch(const BatchLayout& L, const unsigned char* h_img, unsigned char* d_block,
-                          unsigned char* h_out, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaMemcpyAsync(d_block, h_img, L.image_bytes, cudaMemcpyHostToDevice, s);
+                          unsigned char* h_out, int grid, size_t smem, cudaStream_t s, BatchStreams& bs) {
+    const int ng = (int)L.groups.size();
+    cudaError_t e = bs.ensure(std::max(0, ng - 1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_block, h_img, L.image_bytes, cudaMemcpyHostToDevice, s);
     const BatchInst* insts = reinterpret_cast<const BatchInst*>(d_block + L.o_insts);
     InstCounters* ctr = reinterpret_cast<InstCounters*>(d_block + L.o_ctr);
-    QueueItem* items = reinterpret_cast<QueueItem*>(d_block + L.o_items);
-    BatchQueue* q = reinterpret_cast<BatchQueue*>(d_block + L.o_q);
-    const int* pre = reinterpret_cast<const int*>(d_block + L.o_pre);
+    const GroupDev* gd = reinterpret_cast<const GroupDev*>(d_block + L.o_groups);
     if (e == cudaSuccess) {
-        batch_reset_kernel<<<std::min(L.count, 1024), 256, 0, s>>>(insts, L.count, ctr, items, q, pre, d_block + L.o_in);
+        batch_reset_kernel<<<std::min(L.count, 1024), 256, 0, s>>>(insts, L.count, ctr, gd, ng, d_block,
+                                                                  d_block + L.o_in);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) {
+    const std::vector<int> grids = group_grids(L, grid);
+    if (e == cudaSuccess && ng > 1) e = cudaEventRecord(bs.fork, s);
+    for (int k = 0; k < ng && e == cudaSuccess; ++k) {
+        cudaStream_t st = k == 0 ? s : bs.aux[k - 1];
+        if (k > 0) e = cudaStreamWaitEvent(st, bs.fork, 0);
+        if (e != cudaSuccess) break;
+        const BatchGroup& g = L.groups[k];
         const uint64_t budget_ns = 20ull * 1000 * 1000 * 1000;  // 20 s
-        persistent_kernel<<<grid, BATCH_THREADS, smem, s>>>(insts, ctr, items, q, budget_ns);
+        kPersistent[g.variant]<<<grids[k], BATCH_THREADS, smem, st>>>(
+            insts, ctr, reinterpret_cast<QueueItem*>(d_block + g.o_items), reinterpret_cast<BatchQueue*>(d_block + g.o_q),
+            budget_ns);
         e = cudaGetLastError();
+        if (e == cudaSuccess && k > 0) e = cudaEventRecord(bs.join[k - 1], st);
     }
+    for (int k = 1; k < ng && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s, bs.join[k - 1], 0);
     if (e == cudaSuccess) {
-        batch_gather_kernel<<<std::min(L.count, 1024), 128, 0, s>>>(insts, L.count, q, d_block + L.o_out);
+        batch_gather_kernel<<<std::min(L.count, 1024), 128, 0, s>>>(insts, L.count, gd, ng, d_block, d_block + L.o_out);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_block + L.o_out, L.out_bytes, cudaMemcpyDeviceToHost, s);
@@ -627,10 +786,12 @@ struct BatchPlan {
     unsigned char* h_out = nullptr;
     unsigned char* d_block = nullptr;
     cudaStream_t stream = nullptr;
+    BatchStreams streams;
     cudaGraphExec_t graph = nullptr;
     ~BatchPlan() {
         if (graph) cudaGraphExecDestroy(graph);
         if (stream) cudaStreamDestroy(stream);
+        streams.release();
         if (d_block) cudaFree(d_block);
         if (h_img) cudaFreeHost(h_img);
         if (h_out) cudaFreeHost(h_out);
@@ -666,9 +827,11 @@ static mppi_status build_plan(mppi_ctx* const* ctxs, int count, BatchPlan* P) {
     const int grid = (int)std::min<long>((long)std::max(1, per_sm) * sms, P->L.total);
     // the launch sequence, captured once
     cudaGraph_t g = nullptr;
+    e = P->streams.ensure((int)P->L.groups.size() - 1);  // before the capture
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch streams");
     e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch capture");
-    cudaError_t ce = enqueue_batch(P->L, P->h_img, P->d_block, P->h_out, grid, smem, P->stream);
+    cudaError_t ce = enqueue_batch(P->L, P->h_img, P->d_block, P->h_out, grid, smem, P->stream, P->streams);
     e = cudaStreamEndCapture(P->stream, &g);
     if (ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -792,7 +955,7 @@ mppi_status queue_timeout_selftest(int64_t budget_us, int32_t* observed) {
     int per_sm = 0;
     if (e == cudaSuccess) e = prepare_batch_kernel(8, &smem, &per_sm);
     if (e == cudaSuccess) {
-        persistent_kernel<<<1, BATCH_THREADS, smem>>>(nullptr, nullptr, reinterpret_cast<QueueItem*>(d + 256),
+        persistent_kernel<BV_XYY><<<1, BATCH_THREADS, smem>>>(nullptr, nullptr, reinterpret_cast<QueueItem*>(d + 256),
                                                     reinterpret_cast<BatchQueue*>(d), (uint64_t)budget_us * 1000ull);
         e = cudaGetLastError();
     }

@@ -53,6 +53,7 @@ struct Request {
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    BatchStreams aux;  // the groups' kernels fork onto these
     cudaEvent_t ev = nullptr;
     unsigned char* h_img = nullptr;
     unsigned char* h_out = nullptr;
@@ -191,7 +192,7 @@ static bool admit(mppi_server* S) {
             // grid: one block per prefilled tile, at most the resident capacity, so small
             // launches leave SMs to the launches running beside them
             const int grid = (int)std::max<long>(1, std::min<long>(S->capacity, s.L.nprefill));
-            e = enqueue_batch(s.L, s.h_img, s.d_block, s.h_out, grid, S->smem, s.stream);
+            e = enqueue_batch(s.L, s.h_img, s.d_block, s.h_out, grid, S->smem, s.stream, s.aux);
         }
         if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
         if (e != cudaSuccess) {
@@ -282,6 +283,7 @@ void mppi_server_destroy(mppi_server* S) {
         if (s.stream) cudaStreamSynchronize(s.stream);
         if (s.ev) cudaEventDestroy(s.ev);
         if (s.stream) cudaStreamDestroy(s.stream);
+        s.aux.release();
         if (s.h_img) cudaFreeHost(s.h_img);
         if (s.h_out) cudaFreeHost(s.h_out);
         if (s.d_block) cudaFree(s.d_block);
