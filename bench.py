@@ -484,8 +484,13 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1
                        f"H 100-200, 4-8 knots, 1 iteration; {seconds:.0f} s per load after {warm_s:.0f} s warm-up",
            "memory_budget_bytes": 8 << 30, "max_inflight_launches": 4,
            "plain_single_instance_solves_per_s": plain_solves_per_s, "loads": []}
+    import gc
     for load in loads:
         rate = load / n_ctrl
+        # the load generator is Python: its garbage collector is paused during each load,
+        # so that a collection pause (tens of ms) is not charged to the server's latency
+        gc.collect()
+        gc.disable()
         now0 = time.monotonic_ns()
         heap = [(now0 + int(rng.exponential(1e9 / rate)), i) for i in range(n_ctrl)]
         heapq.heapify(heap)
@@ -533,6 +538,7 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=4.0, warm_s=1
                 else:
                     backlog[i] = []
                 nc = srv.next_completed(timeout_us=0)
+        gc.enable()
         s1 = srv.stats()
         lat.sort()
         q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None

@@ -100,3 +100,41 @@ def test_batch_rejects_bad_input(M):
     x[0] = np.inf
     rc, *_ = _batch(M, c, [mix[0]["x0"], x], [None, None])
     assert rc == M.MPPI_ERR_NONFINITE_STATE
+
+
+def test_every_rollout_variant_in_one_batch(M):
+    # one batch holding an instance of every rollout variant (axis-specialised and generic
+    # chain kernels for both robots, with and without the modular cost; half-warp and warp
+    # mappings), so every group runs its own persistent kernel beside the others: each
+    # instance gives the bits of its single solve
+    quad, hum = S.quadruped(), S.humanoid()
+    qaxis = quad.axis.copy()
+    qaxis[1] = np.array([1.0, 0.0, 0.05]) / np.linalg.norm([1.0, 0.0, 0.05])
+    hjpos = hum.jpos.copy()
+    hjpos[hum.nb - 1, 0] = 0.01
+    robots = {"xyy": quad, "quad_generic": quad.copy(axis=qaxis), "split": hum, "hum_generic": hum.copy(jpos=hjpos)}
+    paper = {k: S.with_paper_cost(r, "walking", pdot_des=(0.4, 0.0, 0.0)) for k, r in robots.items()}
+    specs = []   # (robot, mapping, K, H, nk)
+    for k in robots:
+        specs.append((robots[k], 2, 70, 30, 5))
+        specs.append((paper[k], 2, 33, 25, 4))
+    specs += [(quad, 1, 19, 30, 4), (quad, 0, 11, 20, 6), (hum, 0, 9, 20, 5)]
+    models = {}
+    alone, batch, states, warms = [], [], [], []
+    for i, (rob, mp, K, H, nk) in enumerate(specs):
+        mod = models.setdefault(id(rob), M.Model(rob))
+        sig = S.linear_sigma(nk, 1)
+        kw = dict(iters=1, dt=0.005, seed=70 + i, instance=i, mapping=mp)
+        alone.append(M.Controller(mod, K, H, nk, 0.2, sig, **kw))
+        batch.append(M.Controller(mod, K, H, nk, 0.2, sig, **kw))
+        states.append(S.standing_state(rob, jitter=0.02, base_vel=0.2, seed=500 + i))
+        warms.append(S.nominal_knots(rob, nk).astype(np.float32))
+    plans = {models[id(r)].info()["axis_plan"] for r, *_ in specs}
+    assert plans == {0, 1, 2}
+    ref = [c.solve(x, warm=w) for c, x, w in zip(alone, states, warms)]
+    rc, means, bests, infos = _batch(M, batch, states, warms)
+    assert rc == 0
+    for i, (r, m, b, inf) in enumerate(zip(ref, means, bests, infos)):
+        np.testing.assert_array_equal(m, r[0].reshape(-1), err_msg=f"instance {i}")
+        np.testing.assert_array_equal(b, r[1].reshape(-1), err_msg=f"instance {i}")
+        assert inf["best_cost"] == r[2]["best_cost"]
