@@ -116,6 +116,32 @@ def test_scale_config_full_size_sampled(M, orc):
     assert info["best_cost"] == pytest.approx(ref["best_cost"], rel=1e-3)
 
 
+def test_humanoid_config_full_size_sampled(M, orc):
+    # the humanoid workload at full size (K = 2048, H = 200) in the benchmark's launch
+    # configuration (two-warp split kernel, 256-thread blocks): 32 sampled rollouts and the
+    # full solve's updated control points against the oracle
+    p = S.humanoid_problem()
+    c = M.Controller.from_problem(M.Model(p.model), p, mapping=M.MPPI_MAP_CHAIN, block=256)
+    assert c.info()["block"] == 256 and M.Model(p.model).info()["axis_plan"] == 2
+    nom32 = p.nominal.astype(np.float32)
+    kn = orc.sample_knots(p.model.nj, p.nk, p.n, p.horizon, p.dt, nom32.astype(np.float64), p.sigma[0],
+                          seed=p.seed).astype(np.float32)
+    costs = c.rollout_explicit(p.state, kn)
+    idx = np.random.default_rng(1).choice(p.n, 32, replace=False)
+    idx[0], idx[1] = 0, p.n - 1
+    ref_c = orc.rollout_batch(p.model, p.state, kn.astype(np.float64)[idx], p.horizon, p.dt)
+    err = np.abs(costs[idx] - ref_c) / np.abs(ref_c)
+    print(f"humanoid: sampled FP32 cost error median {np.median(err):.2e} max {err.max():.2e}")
+    assert err.max() < 1e-3 and np.all(np.isfinite(costs))
+    mean, best, info = c.solve(p.state, warm=nom32)
+    ref = orc.solve(p.model, p.n, p.nk, p.horizon, p.iters, p.dt, p.lam, p.sigma, p.state,
+                    nom32.astype(np.float64), seed=p.seed)
+    err, ok = _close(mean, ref["mean"])
+    print(f"humanoid full size: mean knot error {err:.2e}; best cost {info['best_cost']:.4f} vs {ref['best_cost']:.4f}")
+    assert ok
+    assert info["best_cost"] == pytest.approx(ref["best_cost"], rel=1e-3)
+
+
 # ------------------------------------------------------------------------------------
 # API behaviour
 # ------------------------------------------------------------------------------------
