@@ -64,6 +64,16 @@ static bool offset_along(const mppi_model_desc& d, int b, int k) {
     return true;
 }
 
+// every contact point sits on one of the bodies leaf[0..n)
+static bool contacts_on(const mppi_model_desc& d, const int* leaf, int n) {
+    for (int i = 0; i < d.nc; ++i) {
+        bool on = false;
+        for (int k = 0; k < n; ++k) on = on || d.contact_body[i] == leaf[k];
+        if (!on) return false;
+    }
+    return true;
+}
+
 static bool offset_zero(const mppi_model_desc& d, int b) {
     return d.jpos[3 * b] == 0.0 && d.jpos[3 * b + 1] == 0.0 && d.jpos[3 * b + 2] == 0.0;
 }
@@ -94,7 +104,8 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
                           d.jpos[3 * P.b0[l] + 2] == 0.0 && offset_along(d, P.b0[l] + 1, 1) &&
                           offset_along(d, P.b0[l] + 2, 2);
             }
-            if (xyy) P.axis_plan = AXP_XYY;
+            const int calves[4] = {P.b0[0] + 2, P.b0[1] + 2, P.b0[2] + 2, P.b0[3] + 2};
+            if (xyy && contacts_on(d, calves, 4)) P.axis_plan = AXP_XYY;
             return P;
         }
     }
@@ -133,7 +144,8 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
                       d.jpos[3 * b] == 0.0 && offset_along(d, b + 1, 1) && offset_zero(d, b + 2) &&
                       offset_along(d, b + 3, 2);
             }
-            if (hum) P.axis_plan = AXP_HUM;
+            const int feet[2] = {P.b0[0] + 5, P.b0[1] + 5};
+            if (hum && contacts_on(d, feet, 2)) P.axis_plan = AXP_HUM;
             return P;
         }
     }

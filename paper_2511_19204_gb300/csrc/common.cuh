@@ -154,11 +154,11 @@ constexpr int TOPO_HUMANOID = 2;    // 2 chains of <= 6 off the base + a branch 
 // Axis plans of the lanes-per-chain quadruped: AXP_GENERIC, any unit axes; AXP_XYY, the
 // usual leg layout: every chain's joints turn about +x, +y, +y (hip abduction, hip and
 // knee flexion), the hip sits in the base's xy-plane, the thigh joint along y from the
-// hip and the knee along z from the thigh, which the passes exploit at compile time.
-// AXP_HUM, the usual humanoid layout (6-joint legs off the base turning about z, x, y, y,
-// y, x; a waist joint about z carrying 4-joint arms that turn about y, x, z, y; every joint
-// offset on one axis, in the yz-plane or zero, as the split rollout expects), runs the
-// two-warp split kernel.
+// hip and the knee along z from the thigh, and contact points only on the calves, which
+// the passes exploit at compile time. AXP_HUM, the usual humanoid layout (6-joint legs off
+// the base turning about z, x, y, y, y, x; a waist joint about z carrying 4-joint arms that
+// turn about y, x, z, y; every joint offset on one axis, in the yz-plane or zero; contact
+// points only on the feet), runs the two-warp split kernel.
 constexpr int AXP_GENERIC = 0;
 constexpr int AXP_XYY = 1;
 constexpr int AXP_HUM = 2;

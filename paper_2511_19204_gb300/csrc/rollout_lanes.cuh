@@ -472,7 +472,7 @@ __device__ __forceinline__ void body_inertia(const BodyConst& C, Art<float>& IA)
 
 // Pass 1 of revolute body b from its parent's pose P: its pose, the velocity product and
 // the bias (contact forces included).
-template <bool KEEP, bool PAPER, int AX, int OF>
+template <bool KEEP, bool PAPER, int AX, int OF, bool CONTACTS = true>
 __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyConst& C, float q, float qd,
                                            const Pose& Pp, Pose& P, BodyMem& m, float& pcost, bool count) {
     const V3<float> r = C.r;
@@ -493,7 +493,7 @@ __device__ __forceinline__ void body_pass1(const DevModel<float>& M, const BodyC
     m.cw = cross_ax<AX>(C, P.w, qd);
     m.cv = cross_ax<AX>(C, P.v, qd);
     V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-    body_contacts<PAPER>(M, C.b, P, fen, fef, pcost, count);
+    if (CONTACTS) body_contacts<PAPER>(M, C.b, P, fen, fef, pcost, count);
     body_bias(C, P, fen, fef, m.x0, m.x1);
     if (PAPER && count) {
         const float dq = q - C.qinit;
@@ -677,6 +677,9 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                                             const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                             double* __restrict__ xf) {
     constexpr bool KEEP = LMAX <= 3;  // short chains keep rotations and segment knots in registers
+    // under the x, y, y plan every contact point sits on a calf (model creation checks it),
+    // so the base, hips and thighs skip the contact loop
+    constexpr bool LEAF_CONTACTS = AXP == AXP_XYY;
     const int nj = M.nb - 1, nq = 7 + nj;
     const int b0 = M.lane_b0[g], len = M.lane_len[g];
     const int bb = BRANCH ? M.branch_body : 0;
@@ -756,13 +759,16 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         // ---- pass 1 ----
         B.R = quat_to_R(qw, qx, qy, qz);
         B.p = p;
+        // chain plans exist only for floating bases (model creation), so fixed_base is 0 and
+        // the other fixed-base branches are gone; these two selects stay because without them
+        // the compiler schedules the step loop worse (the launch took 12 % longer)
         B.w = M.fixed_base ? v3(0.f, 0.f, 0.f) : w;
         B.v = M.fixed_base ? v3(0.f, 0.f, 0.f) : vl;
         V3<float> p0n, p0f;
         float pcost = 0.f;  // this lane's share of the modular running cost
         {
             V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-            body_contacts<PAPER>(M, 0, B, fen, fef, pcost, g == 0);
+            if (!LEAF_CONTACTS) body_contacts<PAPER>(M, 0, B, fen, fef, pcost, g == 0);
             body_bias(base(), B, fen, fef, p0n, p0f);
         }
         if (PAPER && g == 0) pcost += base_cost(M, B.R, B.p);
@@ -781,7 +787,8 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 constexpr int j = decltype(jc)::value;
                 if (j < len) {
                     Pose P;
-                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>(), chain_offset<AXP, j>()>(M, body(j), q[j], qd[j], Pp, P, mem[j], pcost, true);
+                    body_pass1<KEEP, PAPER, chain_axis<AXP, j>(), chain_offset<AXP, j>(), !LEAF_CONTACTS || j == 2>(
+                        M, body(j), q[j], qd[j], Pp, P, mem[j], pcost, true);
                     if (cb == b0 + j) cost_terms(M, P, tz, tt);
                     Pp = P;
                 }
@@ -848,10 +855,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         p0f = p0f + v3(lsum(cpf.x), lsum(cpf.y), lsum(cpf.z));
         const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
         V3<float> aw, av;
-        if (M.fixed_base) {
-            aw = v3(0.f, 0.f, 0.f);
-            av = v3(-g_b.x, -g_b.y, -g_b.z);
-        } else {
+        {
             const float rhs[6] = {-p0n.x, -p0n.y, -p0n.z, -p0f.x, -p0f.y, -p0f.z};
             float x[6];
             art_solve(IA0, rhs, x);
@@ -876,7 +880,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         te = lsum(te);
         if (PAPER) pcost = lsum(pcost);
         {
-            const float vx = M.fixed_base ? 0.f : (B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z);
+            const float vx = B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z;
             const float dv = vx - M.vx_des;
             float c = tz + M.w_vx * dv * dv + tt + M.w_tau * te;
             if (PAPER) c += pcost;
@@ -895,7 +899,7 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             qdb += dt * qddb;
             qb += dt * qdb;
         }
-        if (!M.fixed_base) {
+        {
             w = w + dt * aw;
             vl = vl + dt * (av + g_b);
             p = p + dt * mul(B.R, vl);

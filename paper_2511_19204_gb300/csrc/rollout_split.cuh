@@ -151,7 +151,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         float pc = 0.f;  // this lane's share of the modular running cost
         {
             V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-            body_contacts<PAPER>(M, 0, B, fen, fef, pc, lead);
+            // contact points sit on the feet only (model creation checks it)
             body_bias(load_body(M, 0), B, fen, fef, p0n, p0f);
         }
         if (PAPER && lead) pc += base_cost(M, B.R, B.p);
@@ -163,8 +163,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             static_for<0, LEN>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
                 Pose P;
-                body_pass1<false, PAPER, split_axis<0, j>(), split_offset<0, j>()>(M, load_body(M, b0 + j), q[j], qd[j],
-                                                                                 Pp, P, mem[j], pc, true);
+                body_pass1<false, PAPER, split_axis<0, j>(), split_offset<0, j>(), j == LEN - 1>(
+                    M, load_body(M, b0 + j), q[j], qd[j], Pp, P, mem[j], pc, true);
                 if (cb == b0 + j) cost_terms(M, P, tz, tt);
                 Pp = P;
             });
@@ -353,7 +353,8 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
         float pc = 0.f, tz = 0.f, tt = 0.f;
         BodyMem mb;
         Pose PB;
-        body_pass1<false, PAPER, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(M, load_body(M, bb), qb, qdb, B, PB, mb, pc, lead);
+        body_pass1<false, PAPER, SPLIT_WAIST_AX, SPLIT_WAIST_OF, false>(M, load_body(M, bb), qb, qdb, B, PB, mb, pc,
+                                                                        lead);
         if (cb == bb && lead) cost_terms(M, PB, tz, tt);
         BodyMem mem[LEN];
         {
@@ -361,8 +362,8 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             static_for<0, LEN>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
                 Pose P;
-                body_pass1<false, PAPER, split_axis<1, j>(), split_offset<1, j>()>(M, load_body(M, b0 + j), q[j], qd[j],
-                                                                                 Pp, P, mem[j], pc, true);
+                body_pass1<false, PAPER, split_axis<1, j>(), split_offset<1, j>(), false>(
+                    M, load_body(M, b0 + j), q[j], qd[j], Pp, P, mem[j], pc, true);
                 if (cb == b0 + j) cost_terms(M, P, tz, tt);
                 Pp = P;
             });

@@ -79,7 +79,8 @@ PER_JOINT_HUM_WAIST = 20 + 41 + 54 + 268 + 36
 
 def axis_plan_hum(model) -> bool:
     """True when the model runs the two-warp split kernel: a floating base with 2 legs of 6
-    bodies, a waist body on the base carrying 2 arms of 4, axes and offsets as above."""
+    bodies, a waist body on the base carrying 2 arms of 4, axes and offsets as above, and
+    contact points only on the feet."""
     import numpy as np
     if model.fixed_base or model.nb != 22:
         return False
@@ -107,13 +108,16 @@ def axis_plan_hum(model) -> bool:
         for j, (ax, kind) in enumerate(plan):
             if not (np.array_equal(model.axis[b0 + j], e[ax]) and off(b0 + j, kind)):
                 return False
-    return bool(np.array_equal(model.axis[13], e[2]) and off(13, 2))
+    feet = {6, 12}
+    return bool(np.array_equal(model.axis[13], e[2]) and off(13, 2)
+                and all(int(b) in feet for b in model.contact_body))
 
 
 def axis_plan_xyy(model) -> bool:
     """True when the model runs the axis-specialised chain kernel: a floating base with 4
     chains of 3 bodies whose joint axes are exactly +x, +y, +y, with the hip in the base's
-    xy-plane, the thigh joint along y from the hip and the knee along z from the thigh."""
+    xy-plane, the thigh joint along y from the hip, the knee along z from the thigh, and
+    contact points only on the calves."""
     import numpy as np
     if model.fixed_base or model.nb != 13:
         return False
@@ -131,7 +135,8 @@ def axis_plan_xyy(model) -> bool:
             return False
         if model.jpos[b0 + 2][0] != 0.0 or model.jpos[b0 + 2][1] != 0.0:
             return False
-    return True
+    calves = {3, 6, 9, 12}
+    return all(int(b) in calves for b in model.contact_body)
 
 
 def flops_per_step(model, contacts_active=None, mapping_chain=True) -> int:

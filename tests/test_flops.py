@@ -36,7 +36,13 @@ def test_perturbed_layouts_use_the_generic_count():
     for m in (h.copy(axis=axis), h.copy(jpos=jpos), h.copy(jpos=jpos2)):
         assert not F.axis_plan_hum(m)
         assert F.flops_per_step(m) == 21 * F.PER_JOINT + 8 * F.PER_CONTACT + F.PER_BASE
+    hand = h.copy(contact_body=np.append(h.contact_body, h.nb - 1).astype(np.int32),
+                  contact_pos=np.vstack([h.contact_pos, [0.0, 0.0, -0.2]]))
+    assert not F.axis_plan_hum(hand)
     q = S.quadruped()
     jq = q.jpos.copy()
     jq[1, 2] = 0.01
     assert not F.axis_plan_xyy(q.copy(jpos=jq))
+    thigh = q.copy(contact_body=np.append(q.contact_body, 2).astype(np.int32),
+                   contact_pos=np.vstack([q.contact_pos, [0.0, 0.0, -0.1]]))
+    assert not F.axis_plan_xyy(thigh)

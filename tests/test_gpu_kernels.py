@@ -11,6 +11,7 @@ Tolerances (FP32 product unless stated):
 import numpy as np
 import pytest
 
+from paper_2511_19204_gb300 import flops as F
 from paper_2511_19204_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
@@ -216,14 +217,19 @@ def test_mappings_agree(M, orc, robot, n, block):
         assert np.max(np.abs(out[mapping] - out[0]) / np.abs(out[0])) < 1e-4
 
 
-@pytest.mark.parametrize("tilt", [0.0, 0.05, -1.0])
+@pytest.mark.parametrize("tilt", [0.0, 0.05, -1.0, None])
 def test_chain_axis_plans(M, orc, tilt):
-    # the quadruped's x, y, y joint axes select the axis-specialised chain kernel; a tilted
-    # or reversed hip axis the generic one; both agree with the oracle
+    # the quadruped's x, y, y joint axes (contacts on the calves) select the axis-specialised
+    # chain kernel; a tilted or reversed hip axis, or a contact point on a thigh (None), the
+    # generic one; both agree with the oracle
     p = S.scale_quadruped(n=256)
     p.horizon = 120
     m = p.model
-    if tilt:
+    if tilt is None:
+        m = m.copy(contact_body=np.append(m.contact_body, 2).astype(np.int32),
+                   contact_pos=np.vstack([m.contact_pos, [0.0, 0.0, -0.1]]))
+        p.model = m
+    elif tilt:
         axis = m.axis.copy()
         for b in range(1, m.nb, 3):
             a = np.array([1.0, 0.0, tilt]) if tilt > 0 else np.array([-1.0, 0.0, 0.0])
@@ -233,6 +239,7 @@ def test_chain_axis_plans(M, orc, tilt):
     mod = M.Model(m)
     assert mod.info()["topology"] == 1
     assert mod.info()["axis_plan"] == (1 if tilt == 0.0 else 0)
+    assert F.axis_plan_xyy(m) == (tilt == 0.0)
     kn = orc.sample_knots(m.nj, p.nk, p.n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed).astype(np.float32)
     c = M.Controller.from_problem(mod, p, mapping=M.MPPI_MAP_CHAIN)
     got, fin = c.rollout_explicit(p.state, kn, finals=True)
@@ -244,7 +251,7 @@ def test_chain_axis_plans(M, orc, tilt):
     assert err.max() < 1e-4 and err_f.max() < 1e-4
 
 
-@pytest.mark.parametrize("variant", ["layout", "tilted", "offset"])
+@pytest.mark.parametrize("variant", ["layout", "tilted", "offset", "hand_contact"])
 def test_humanoid_axis_plans(M, orc, variant):
     # the humanoid's joint layout (legs z, x, y, y, y, x; waist z; arms y, x, z, y) selects
     # the two-warp split kernel (axis plan 2); a tilted hip axis or an elbow offset off its
@@ -261,10 +268,14 @@ def test_humanoid_axis_plans(M, orc, variant):
         jpos = m.jpos.copy()
         jpos[m.nb - 1, 0] = 0.01
         m = m.copy(jpos=jpos)
+    elif variant == "hand_contact":   # a contact point off the feet
+        m = m.copy(contact_body=np.append(m.contact_body, m.nb - 1).astype(np.int32),
+                   contact_pos=np.vstack([m.contact_pos, [0.0, 0.0, -0.2]]))
     p.model = m
     mod = M.Model(m)
     assert mod.info()["topology"] == 2
     assert mod.info()["axis_plan"] == (2 if variant == "layout" else 0)
+    assert F.axis_plan_hum(m) == (variant == "layout")
     kn = orc.sample_knots(m.nj, p.nk, p.n, p.horizon, p.dt, p.nominal, p.sigma[0], seed=p.seed).astype(np.float32)
     c = M.Controller.from_problem(mod, p, mapping=M.MPPI_MAP_CHAIN)
     got, fin = c.rollout_explicit(p.state, kn, finals=True)
