@@ -446,7 +446,9 @@ int batch_variant(const mppi_ctx* c) {
 // time in the persistent kernel (one 256-thread block per SM), measured on GB300 for the
 // specialised chain variants (quadruped 3.2 us, humanoid split 7.5 us, +10 % with the
 // modular cost) and scaled from the per-instance kernels' ratios for the others. Orders
-// the prefill (longest first) and shares the SMs between groups.
+// the prefill (longest first) and shares the SMs between groups. Only the ratios matter:
+// later kernels run these steps in 2.6 and 6.8 us, but weights in that ratio gave a
+// slower mixed batch (8.7 against 8.3 ms), so these stay.
 static double step_us(const mppi_ctx* c) {
     switch (batch_variant(c)) {
         case BV_XYY: return 3.2;
