@@ -9,8 +9,9 @@
 // Per step the warps meet twice in shared memory (one record per sample and direction,
 // each behind a 64-thread named barrier):
 //   A  arm -> leg: the waist subtree's articulated inertia and bias force (Featherstone's
-//      articulated-body recursion, carried to the base frame) and the arm warp's share
-//      of the running cost;
+//      articulated-body recursion, carried to the base frame) plus the base's own
+//      inertia and bias force, and the arm warp's share of the running cost (with the
+//      base's terms), so the leg warp, whose chain is the longer one, only adds;
 //   B  leg -> arm: the base acceleration of this step and the base pose of the next.
 // The base is integrated once, by the leg warp, so every base quantity the arm warp uses
 // is bitwise the leg warp's. A record is written before a barrier and read after it, and
@@ -107,8 +108,10 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
                                          const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                          double* __restrict__ xf) {
     constexpr int LEN = SPLIT_LEG;
-    const int nj = M.nb - 1, nq = 7 + nj;
-    const int b0 = M.lane_b0[side];
+    // the plan fixes the numbering: legs from bodies 1 and 7, the waist 13, arms from 14
+    // and 18, 21 joints (compile-time, which shortens the launch)
+    constexpr int nj = 21, nq = 7 + nj;
+    const int b0 = 1 + 6 * side;
     const bool lead = side == 0;
     V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
     const V3<float> p_start = p;
@@ -147,16 +150,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         for (int j = 0; j < LEN; ++j)
             tau[j] = hermite_pd(load_body(M, b0 + j), seg_knots(knots, nj, k, b0 + j), s, dtk, inv_dtk, q[j], qd[j]);
         // ---- pass 1: base, then the leg ----
-        V3<float> p0n, p0f;
         float pc = 0.f;  // this lane's share of the modular running cost
-        {
-            V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
-            // contact points sit on the feet only (model creation checks it)
-            body_bias(load_body(M, 0), B, fen, fef, p0n, p0f);
-        }
-        if (PAPER && lead) pc += base_cost(M, B.R, B.p);
         float tz = 0.f, tt = 0.f;
-        if (cb == 0 && lead) cost_terms(M, B, tz, tt);
         BodyMem mem[LEN];
         {
             Pose Pp = B;
@@ -192,16 +187,16 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         pair_sync(bar);
         float a[28];
         rec_load<7>(recA, a);
+        // record A holds the waist subtree plus the base's own inertia and bias force
         Art<float> IA0;
-        body_inertia(load_body(M, 0), IA0);
 #pragma unroll
-        for (int t = 0; t < 6; ++t) IA0.A[t] = (IA0.A[t] + carry.A[t]) + a[t];
+        for (int t = 0; t < 6; ++t) IA0.A[t] = carry.A[t] + a[t];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) IA0.B[t] = (IA0.B[t] + carry.B[t]) + a[6 + t];
+        for (int t = 0; t < 9; ++t) IA0.B[t] = carry.B[t] + a[6 + t];
 #pragma unroll
-        for (int t = 0; t < 6; ++t) IA0.C[t] = (IA0.C[t] + carry.C[t]) + a[15 + t];
-        p0n = (p0n + cpn) + v3(a[21], a[22], a[23]);
-        p0f = (p0f + cpf) + v3(a[24], a[25], a[26]);
+        for (int t = 0; t < 6; ++t) IA0.C[t] = carry.C[t] + a[15 + t];
+        const V3<float> p0n = cpn + v3(a[21], a[22], a[23]);
+        const V3<float> p0f = cpf + v3(a[24], a[25], a[26]);
         const float c_arms = a[27];
         const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
         V3<float> aw, av;
@@ -212,11 +207,9 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             aw = v3(x[0], x[1], x[2]);
             av = v3(x[3], x[4], x[5]);
         }
-        // ---- running cost on the pre-step state ----
+        // ---- running cost on the pre-step state (the base terms came with record A) ----
         {
-            const float vx = B.R.m[0] * vl.x + B.R.m[1] * vl.y + B.R.m[2] * vl.z;
-            const float dv = vx - M.vx_des;
-            const float c = (c_legs + c_arms) + M.w_vx * dv * dv;
+            const float c = c_legs + c_arms;
             const float y = c - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
@@ -310,9 +303,9 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
                                          const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                          double* __restrict__ xf) {
     constexpr int LEN = SPLIT_ARM;
-    const int nj = M.nb - 1, nq = 7 + nj;
-    const int b0 = M.lane_b0[2 + side];
-    const int bb = M.branch_body;
+    constexpr int nj = 21, nq = 7 + nj;
+    const int b0 = 14 + 4 * side;
+    constexpr int bb = 13;
     const bool lead = side == 0;
     float qb = (float)x0[7 + bb - 1], qdb = (float)x0[nq + 6 + bb - 1];
     float q[LEN], qd[LEN];
@@ -382,12 +375,35 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
         });
         pair_sum(carry, cpn, cpf);
         body_pass2<false, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(load_body(M, bb), taub, mb, true, carry, cpn, cpf);
+        // the base's own inertia and bias force, and its cost terms, off the leg warp's path
+        {
+            Art<float> IB;
+            body_inertia(load_body(M, 0), IB);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) carry.A[t] += IB.A[t];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) carry.B[t] += IB.B[t];
+#pragma unroll
+            for (int t = 0; t < 6; ++t) carry.C[t] += IB.C[t];
+            V3<float> bn, bf;
+            const V3<float> z0 = v3(0.f, 0.f, 0.f);
+            body_bias(load_body(M, 0), B, z0, z0, bn, bf);
+            cpn = cpn + bn;
+            cpf = cpf + bf;
+        }
+        if (PAPER && lead) pc += base_cost(M, B.R, B.p);
+        if (cb == 0 && lead) cost_terms(M, B, tz, tt);
         float te = 0.f;
 #pragma unroll
         for (int j = 0; j < LEN; ++j) te += tau[j] * tau[j];
         if (lead) te += taub * taub;
         float lc = (tz + tt) + M.w_tau * te;
         if (PAPER) lc += pc;
+        if (lead) {
+            const float vx = B.R.m[0] * B.v.x + B.R.m[1] * B.v.y + B.R.m[2] * B.v.z;
+            const float dv = vx - M.vx_des;
+            lc += M.w_vx * dv * dv;
+        }
         {
             const float v[28] = {carry.A[0], carry.A[1], carry.A[2], carry.A[3], carry.A[4], carry.A[5], carry.B[0],
                                  carry.B[1], carry.B[2], carry.B[3], carry.B[4], carry.B[5], carry.B[6], carry.B[7],
