@@ -424,8 +424,13 @@ mppi_status mppi_ctx_info(const mppi_ctx* ctx, int32_t* h_out8);
 
 /* What the library derived from a model: h_out4 = (topology: 0 generic tree, 1 base + 4
  * chains of <= 3, 2 base + 2 chains + a branch body with 2 chains; axis plan of the
- * lanes-per-chain quadruped: 0 any axes, 1 every chain turns about +x, +y, +y; 1 when the
- * modular cost of Sec. IV-A is on, else 0; the number of bodies). */
+ * lanes-per-chain kernels: 0 any axes, 1 the quadruped layout (every chain turns about +x,
+ * +y, +y, hip offsets in the base's xy-plane, thigh and knee offsets on one axis, contact
+ * points only on the calves), 2 the humanoid layout run by the two-warp split kernel
+ * (legs z, x, y, y, y, x; waist z; arms y, x, z, y; offsets on one axis, in the yz-plane
+ * or zero; contact points only on the feet); 1 when the modular cost of Sec. IV-A is on,
+ * else 0; the number of bodies). With plan 2 the lanes-per-chain mapping needs blocks of
+ * 64, 128 or 256 threads. */
 mppi_status mppi_model_info(const mppi_model* model, int32_t* h_out4);
 
 /* Device bytes one solve of a context occupies (its buffers). */
