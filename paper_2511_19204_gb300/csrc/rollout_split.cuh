@@ -6,16 +6,18 @@
 // is compiled for its own chains' joint axes and offsets; one warp holding both kinds of
 // chain would have to run the two specialisations one after the other.
 //
-// Per step the warps meet twice in shared memory (one record per sample and direction,
-// each behind a 64-thread named barrier):
+// Per step the warps meet three times in shared memory (records per sample, each part
+// written by one warp and read by the other behind a 64-thread named barrier):
 //   A  arm -> leg: the waist subtree's articulated inertia and bias force (Featherstone's
 //      articulated-body recursion, carried to the base frame) plus the base's own
 //      inertia and bias force, and the arm warp's share of the running cost (with the
 //      base's terms), so the leg warp, whose chain is the longer one, only adds;
-//   B  leg -> arm: the base acceleration of this step and the base pose of the next.
-// The base is integrated once, by the leg warp, so every base quantity the arm warp uses
-// is bitwise the leg warp's. A record is written before a barrier and read after it, and
-// its next write comes after the following barrier, so one buffer per direction suffices.
+//   B  leg -> arm: the base acceleration of this step, from the leg warp's base solve;
+//   C  arm -> leg: the base pose of the next step: the arm warp integrates the base while
+//      the leg warp runs its third pass.
+// The base is integrated once, by the arm warp, so every base quantity the two warps use
+// is the same bits. A record part is written before a barrier and read after it, and its
+// next write comes after a later barrier, so one buffer per direction suffices.
 // Left and right chains meet by a pair shuffle (a commutative sum: both lanes of a pair
 // hold the same bits). Equations as in the other rollout kernels: Sec. III-A Hermite
 // setpoints, Sec. III-C PD tracking, the articulated-body algorithm, semi-implicit Euler,
@@ -81,27 +83,37 @@ __device__ __forceinline__ void rec_load(const float* rec, float (&v)[4 * N]) {
     }
 }
 
-// record B: base acceleration (aw, av), then the next base pose (R, p, w, v)
-__device__ __forceinline__ void put_base(float* rec, V3<float> aw, V3<float> av, const Pose& B) {
-    const float v[24] = {aw.x,     aw.y,     aw.z,     av.x,     av.y,     av.z,     B.R.m[0], B.R.m[1],
-                         B.R.m[2], B.R.m[3], B.R.m[4], B.R.m[5], B.R.m[6], B.R.m[7], B.R.m[8], B.p.x,
-                         B.p.y,    B.p.z,    B.w.x,    B.w.y,    B.w.z,    B.v.x,    B.v.y,    B.v.z};
-    rec_store<6>(rec, v);
+// record B holds two parts with different writers: the base acceleration (aw, av) at
+// floats [0, 8), written by the leg warp, and the next base pose (R, p, w, v) at [8, 28),
+// written by the arm warp, which integrates the base.
+__device__ __forceinline__ void put_acc(float* rec, V3<float> aw, V3<float> av) {
+    const float v[8] = {aw.x, aw.y, aw.z, av.x, av.y, av.z, 0.f, 0.f};
+    rec_store<2>(rec, v);
 }
-__device__ __forceinline__ void get_base(const float* rec, V3<float>& aw, V3<float>& av, Pose& B) {
-    float v[24];
-    rec_load<6>(rec, v);
+__device__ __forceinline__ void get_acc(const float* rec, V3<float>& aw, V3<float>& av) {
+    float v[8];
+    rec_load<2>(rec, v);
     aw = v3(v[0], v[1], v[2]);
     av = v3(v[3], v[4], v[5]);
+}
+__device__ __forceinline__ void put_pose(float* rec, const Pose& B) {
+    const float v[20] = {B.R.m[0], B.R.m[1], B.R.m[2], B.R.m[3], B.R.m[4], B.R.m[5], B.R.m[6],
+                         B.R.m[7], B.R.m[8], B.p.x,    B.p.y,    B.p.z,    B.w.x,    B.w.y,
+                         B.w.z,    B.v.x,    B.v.y,    B.v.z,    0.f,      0.f};
+    rec_store<5>(rec + 8, v);
+}
+__device__ __forceinline__ void get_pose(const float* rec, Pose& B) {
+    float v[20];
+    rec_load<5>(rec + 8, v);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) B.R.m[t] = v[6 + t];
-    B.p = v3(v[15], v[16], v[17]);
-    B.w = v3(v[18], v[19], v[20]);
-    B.v = v3(v[21], v[22], v[23]);
+    for (int t = 0; t < 9; ++t) B.R.m[t] = v[t];
+    B.p = v3(v[9], v[10], v[11]);
+    B.w = v3(v[12], v[13], v[14]);
+    B.v = v3(v[15], v[16], v[17]);
 }
 
-// Leg warp: both legs of one sample on lanes side = 0, 1, the base, the cost sum. Returns
-// the sample's cost (the same on both lanes).
+// Leg warp: both legs of one sample on lanes side = 0, 1, the base solve, the cost sum.
+// Returns the sample's cost (the same on both lanes).
 template <bool PAPER>
 __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, const float* recA, float* recB, int bar,
                                          const double* __restrict__ x0,
@@ -112,12 +124,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     // and 18, 21 joints (compile-time, which shortens the launch)
     constexpr int nj = 21, nq = 7 + nj;
     const int b0 = 1 + 6 * side;
-    const bool lead = side == 0;
-    V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
-    const V3<float> p_start = p;
-    float qw = (float)x0[3], qx = (float)x0[4], qy = (float)x0[5], qz = (float)x0[6];
-    V3<float> vl = v3((float)x0[nq], (float)x0[nq + 1], (float)x0[nq + 2]);
-    V3<float> w = v3((float)x0[nq + 3], (float)x0[nq + 4], (float)x0[nq + 5]);
+    const V3<float> p_start = v3((float)x0[0], (float)x0[1], (float)x0[2]);
     float q[LEN], qd[LEN];
 #pragma unroll
     for (int j = 0; j < LEN; ++j) {
@@ -129,12 +136,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     const int cb = M.cost_body;
     const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     Pose B;
-    B.R = quat_to_R(qw, qx, qy, qz);
-    B.p = p;
-    B.w = w;
-    B.v = vl;
-    put_base(recB, v3(0.f, 0.f, 0.f), v3(0.f, 0.f, 0.f), B);  // the arm warp's first base pose
     pair_sync(bar);
+    get_pose(recB, B);  // the first base pose, from the arm warp
     const float inv_H = 1.0f / (float)H;
     int k = 0, rem = -(nk - 1);
     for (int h = 0; h < H; ++h) {
@@ -198,7 +201,6 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         const V3<float> p0n = cpn + v3(a[21], a[22], a[23]);
         const V3<float> p0f = cpf + v3(a[24], a[25], a[26]);
         const float c_arms = a[27];
-        const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
         V3<float> aw, av;
         {
             const float rhs[6] = {-p0n.x, -p0n.y, -p0n.z, -p0f.x, -p0f.y, -p0f.z};
@@ -215,39 +217,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             comp = (t - sum) - y;
             sum = t;
         }
-        // ---- base: semi-implicit Euler, quaternion exponential; B to the arm warp ----
-        w = w + dt * aw;
-        vl = vl + dt * (av + g_b);
-        p = p + dt * mul(B.R, vl);
-        {
-            const float wn = sqrtf(dot(w, w));
-            float dq0, dqs;
-            if (wn * dt < 1e-12f) {
-                dq0 = 1.f;
-                dqs = 0.5f * dt;
-            } else {
-                float sh, ch;
-                fast_sincos(0.5f * wn * dt, &sh, &ch);
-                dq0 = ch;
-                dqs = __fdividef(sh, wn);
-            }
-            const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
-            const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
-            const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
-            const float ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
-            const float nz = qw * dz + qx * dy - qy * dx + qz * dq0;
-            const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
-            qw = nw * inv;
-            qx = nx * inv;
-            qy = ny * inv;
-            qz = nz * inv;
-        }
-        B.R = quat_to_R(qw, qx, qy, qz);
-        B.p = p;
-        B.w = w;
-        B.v = vl;
-        put_base(recB, aw, av, B);
-        pair_sync(bar);
+        put_acc(recB, aw, av);
+        pair_sync(bar);  // B: the arm warp integrates the base meanwhile
         // ---- pass 3 and the legs' joints ----
         float qdd[LEN];
         {
@@ -263,29 +234,16 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             qd[j] += dt * qdd[j];
             q[j] += dt * qd[j];
         }
+        pair_sync(bar);  // C: the next base pose is written
+        get_pose(recB, B);
     }
-    if (PAPER) {  // terminal cost
-        const float y = terminal_cost(M, p, p_start, H, dt) - comp;
+    if (PAPER) {  // terminal cost (B holds the final base pose)
+        const float y = terminal_cost(M, B.p, p_start, H, dt) - comp;
         const float t = sum + y;
         comp = (t - sum) - y;
         sum = t;
     }
     if (xf) {
-        if (lead) {
-            xf[0] = p.x;
-            xf[1] = p.y;
-            xf[2] = p.z;
-            xf[3] = qw;
-            xf[4] = qx;
-            xf[5] = qy;
-            xf[6] = qz;
-            xf[nq] = vl.x;
-            xf[nq + 1] = vl.y;
-            xf[nq + 2] = vl.z;
-            xf[nq + 3] = w.x;
-            xf[nq + 4] = w.y;
-            xf[nq + 5] = w.z;
-        }
 #pragma unroll
         for (int j = 0; j < LEN; ++j) {
             xf[7 + b0 - 1 + j] = q[j];
@@ -295,10 +253,11 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     return sum;
 }
 
-// Arm warp: the waist (replicated on both lanes) and one arm per lane. Returns 0; the
-// sample's cost is the leg warp's.
+// Arm warp: the waist (replicated on both lanes), one arm per lane, and the integration of
+// the floating base (replicated on both lanes). Returns 0; the sample's cost is the leg
+// warp's.
 template <bool PAPER>
-__device__ __noinline__ float split_arms(const DevModel<float>& M, int side, float* recA, const float* recB, int bar,
+__device__ __noinline__ float split_arms(const DevModel<float>& M, int side, float* recA, float* recB, int bar,
                                          const double* __restrict__ x0,
                                          const float* __restrict__ knots, int H, int nk, float dt, float dtk,
                                          double* __restrict__ xf) {
@@ -319,10 +278,19 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
     const ArtProj leafp = leaf_projection<split_axis<1, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     SegPoly kc[LEN], kb;
     int kcur = -1;
+    // the floating base: integrated here, its pose handed to the leg warp each step
+    V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
+    float qw = (float)x0[3], qx = (float)x0[4], qy = (float)x0[5], qz = (float)x0[6];
+    V3<float> vl = v3((float)x0[nq], (float)x0[nq + 1], (float)x0[nq + 2]);
+    V3<float> w = v3((float)x0[nq + 3], (float)x0[nq + 4], (float)x0[nq + 5]);
     Pose B;
-    V3<float> aw, av;
+    B.R = quat_to_R(qw, qx, qy, qz);
+    B.p = p;
+    B.w = w;
+    B.v = vl;
+    put_pose(recB, B);
     pair_sync(bar);
-    get_base(recB, aw, av, B);
+    V3<float> aw, av;
     const float inv_H = 1.0f / (float)H;
     int k = 0, rem = -(nk - 1);
     for (int h = 0; h < H; ++h) {
@@ -412,9 +380,42 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             rec_store<7>(recA, v);
         }
         pair_sync(bar);  // A: the leg warp may read
-        pair_sync(bar);  // B: base acceleration and next pose written
+        pair_sync(bar);  // B: base acceleration written
+        get_acc(recB, aw, av);
+        // ---- base: semi-implicit Euler, quaternion exponential; the next pose to the leg warp ----
+        {
+            const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
+            w = w + dt * aw;
+            vl = vl + dt * (av + g_b);
+            p = p + dt * mul(B.R, vl);
+            const float wn = sqrtf(dot(w, w));
+            float dq0, dqs;
+            if (wn * dt < 1e-12f) {
+                dq0 = 1.f;
+                dqs = 0.5f * dt;
+            } else {
+                float sh, ch;
+                fast_sincos(0.5f * wn * dt, &sh, &ch);
+                dq0 = ch;
+                dqs = __fdividef(sh, wn);
+            }
+            const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
+            const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
+            const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
+            const float ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
+            const float nz = qw * dz + qx * dy - qy * dx + qz * dq0;
+            const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
+            qw = nw * inv;
+            qx = nx * inv;
+            qy = ny * inv;
+            qz = nz * inv;
+        }
         Pose Bn;
-        get_base(recB, aw, av, Bn);
+        Bn.R = quat_to_R(qw, qx, qy, qz);
+        Bn.p = p;
+        Bn.w = w;
+        Bn.v = vl;
+        put_pose(recB, Bn);
         // ---- pass 3 and the waist's and arm's joints ----
         float qdd[LEN], qddb;
         {
@@ -433,12 +434,26 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
         }
         qdb += dt * qddb;
         qb += dt * qdb;
+        pair_sync(bar);  // C: the leg warp may read the next pose
         B = Bn;
     }
     if (xf) {
         if (lead) {
             xf[7 + bb - 1] = qb;
             xf[nq + 6 + bb - 1] = qdb;
+            xf[0] = p.x;
+            xf[1] = p.y;
+            xf[2] = p.z;
+            xf[3] = qw;
+            xf[4] = qx;
+            xf[5] = qy;
+            xf[6] = qz;
+            xf[nq] = vl.x;
+            xf[nq + 1] = vl.y;
+            xf[nq + 2] = vl.z;
+            xf[nq + 3] = w.x;
+            xf[nq + 4] = w.y;
+            xf[nq + 5] = w.z;
         }
 #pragma unroll
         for (int j = 0; j < LEN; ++j) {
