@@ -774,7 +774,10 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             if (!LEAF_CONTACTS) body_contacts<PAPER>(M, 0, B, fen, fef, pcost, g == 0);
             body_bias(base(), B, fen, fef, p0n, p0f);
         }
-        if (PAPER && g == 0) pcost += base_cost(M, B.R, B.p);
+        if constexpr (PAPER) {  // every lane holds the base: no divergent branch, lane 0 counts it
+            const float bcst = base_cost(M, B.R, B.p);
+            pcost += g == 0 ? bcst : 0.f;
+        }
         float tz = 0.f, tt = 0.f;
         if (cb == 0) cost_terms(M, B, tz, tt);
         BodyMem mb;
