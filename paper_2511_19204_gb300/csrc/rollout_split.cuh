@@ -135,6 +135,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     float sum = 0.f, comp = 0.f;
     const int cb = M.cost_body;
     const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
+    SegPoly kc[LEN];
+    int kcur = -1;
     Pose B;
     pair_sync(bar);
     get_pose(recB, B);  // the first base pose, from the arm warp
@@ -147,11 +149,16 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             ++k;
         }
         const float s = (float)rem * inv_H;
-        // the legs read their segment knots each step (fewer registers held across the step)
+        // power-basis setpoints, formed once per segment (the registers they hold became
+        // free once the base's integration moved to the arm warp)
+        if (k != kcur) {
+            kcur = k;
+#pragma unroll
+            for (int j = 0; j < LEN; ++j) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
+        }
         float tau[LEN];
 #pragma unroll
-        for (int j = 0; j < LEN; ++j)
-            tau[j] = hermite_pd(load_body(M, b0 + j), seg_knots(knots, nj, k, b0 + j), s, dtk, inv_dtk, q[j], qd[j]);
+        for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
         // ---- pass 1: base, then the leg ----
         float pc = 0.f;  // this lane's share of the modular running cost
         float tz = 0.f, tt = 0.f;
