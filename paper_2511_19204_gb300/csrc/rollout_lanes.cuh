@@ -910,16 +910,12 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             vl = vl + dt * (av + g_b);
             p = p + dt * mul(B.R, vl);
             const float wn = sqrtf(dot(w, w));
-            float dq0, dqs;
-            if (wn * dt < 1e-12f) {
-                dq0 = 1.f;
-                dqs = 0.5f * dt;
-            } else {
-                float sh, ch;
-                fast_sincos(0.5f * wn * dt, &sh, &ch);
-                dq0 = ch;
-                dqs = __fdividef(sh, wn);
-            }
+            // both branches evaluated, one selected: no branch splits the step's last block
+            const bool tiny = wn * dt < 1e-12f;
+            float sh, ch;
+            fast_sincos(0.5f * wn * dt, &sh, &ch);
+            const float dq0 = tiny ? 1.f : ch;
+            const float dqs = tiny ? 0.5f * dt : __fdividef(sh, wn);
             const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
             const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
             const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;

@@ -112,6 +112,29 @@ __device__ __forceinline__ void get_pose(const float* rec, Pose& B) {
     B.v = v3(v[15], v[16], v[17]);
 }
 
+// Contact forces of a foot's points, evaluated whether or not a point penetrates (no
+// branch): a point above the ground gets fn = 0, so F = 0 and the sums are unchanged.
+template <bool PAPER>
+__device__ __forceinline__ void foot_contacts(const DevModel<float>& M, int b, const Pose& P, V3<float>& fen,
+                                              V3<float>& fef, float& pcost) {
+    const int c0 = M.cfirst[b], cn = M.ccount[b];
+    for (int c = 0; c < cn; ++c) {
+        const int ci = c0 + c;
+        const V3<float> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
+        const V3<float> pc = P.p + mul(P.R, rc);
+        const float depth = -pc.z;
+        const bool touch = depth > 0.f;
+        const V3<float> vw = mul(P.R, P.v + cross(P.w, rc));
+        const float fn = touch ? fmaxf(M.contact_k * depth - M.contact_c * vw.z, 0.f) : 0.f;
+        const float sc = -M.mu * fn * rsqrtf(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
+        const V3<float> F = v3(sc * vw.x, sc * vw.y, fn);
+        const V3<float> fb = mulT(P.R, F);
+        fef = fef + fb;
+        fen = fen + cross(rc, fb);
+        if (PAPER) pcost += touch ? contact_cost(M, vw, F) : M.cf_off;
+    }
+}
+
 // Leg warp: both legs of one sample on lanes side = 0, 1, the base solve, the cost sum.
 // Returns the sample's cost (the same on both lanes).
 template <bool PAPER>
@@ -168,8 +191,14 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             static_for<0, LEN>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
                 Pose P;
-                body_pass1<false, PAPER, split_axis<0, j>(), split_offset<0, j>(), j == LEN - 1>(
+                body_pass1<false, PAPER, split_axis<0, j>(), split_offset<0, j>(), false>(
                     M, load_body(M, b0 + j), q[j], qd[j], Pp, P, mem[j], pc, true);
+                if constexpr (j == LEN - 1) {  // the foot: its contact forces enter its bias
+                    V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
+                    foot_contacts<PAPER>(M, b0 + j, P, fen, fef, pc);
+                    mem[j].x0 = mem[j].x0 - fen;
+                    mem[j].x1 = mem[j].x1 - fef;
+                }
                 if (cb == b0 + j) cost_terms(M, P, tz, tt);
                 Pp = P;
             });
@@ -396,16 +425,12 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             vl = vl + dt * (av + g_b);
             p = p + dt * mul(B.R, vl);
             const float wn = sqrtf(dot(w, w));
-            float dq0, dqs;
-            if (wn * dt < 1e-12f) {
-                dq0 = 1.f;
-                dqs = 0.5f * dt;
-            } else {
-                float sh, ch;
-                fast_sincos(0.5f * wn * dt, &sh, &ch);
-                dq0 = ch;
-                dqs = __fdividef(sh, wn);
-            }
+            // both branches evaluated, one selected (no branch in the step)
+            const bool tiny = wn * dt < 1e-12f;
+            float sh, ch;
+            fast_sincos(0.5f * wn * dt, &sh, &ch);
+            const float dq0 = tiny ? 1.f : ch;
+            const float dqs = tiny ? 0.5f * dt : __fdividef(sh, wn);
             const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
             const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
             const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
