@@ -50,8 +50,8 @@ __device__ __forceinline__ double sc_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float fast_atan2_pos(float y, float x) {
     const float ax = fabsf(x);
     const float mx = fmaxf(y, ax), mn = fminf(y, ax);
-    if (!(mx > 0.f)) return signbit(x) ? 3.14159265358979f : 0.f;  // atan2(0, -0) = pi
-    const float t = __fdividef(mn, mx);
+    const bool zero = !(mx > 0.f);  // y = x = 0: atan2(0, +-0) = 0 or pi, selected at the end
+    const float t = zero ? 0.f : __fdividef(mn, mx);
     const bool red = t > 0.414213562373095f;
     const float u = red ? __fdividef(t - 1.f, t + 1.f) : t;
     const float u2 = u * u;
@@ -65,7 +65,8 @@ __device__ __forceinline__ float fast_atan2_pos(float y, float x) {
     float a = fmaf(u * u2, p, u);
     if (red) a += 0.785398163397448f;           // pi / 4
     if (y > ax) a = 1.57079632679490f - a;      // pi / 2
-    return x < 0.f ? 3.14159265358979f - a : a;
+    const float r = x < 0.f ? 3.14159265358979f - a : a;
+    return zero ? (signbit(x) ? 3.14159265358979f : 0.f) : r;
 }
 
 // sin and cos of an FP32 angle of moderate size (joint angles, |x| up to ~1e4): Cody and
