@@ -778,8 +778,13 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             const float bcst = base_cost(M, B.R, B.p);
             pcost += g == 0 ? bcst : 0.f;
         }
-        float tz = 0.f, tt = 0.f;
-        if (cb == 0) cost_terms(M, B, tz, tt);
+        float tz, tt;
+        {  // the base's cost terms, selected when the base is the cost body (no branch)
+            float bz, bt;
+            cost_terms(M, B, bz, bt);
+            tz = cb == 0 ? bz : 0.f;
+            tt = cb == 0 ? bt : 0.f;
+        }
         BodyMem mb;
         Pose PB;
         if (on_branch) {
@@ -800,10 +805,9 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                 }
             });
         }
-        if (cb != 0) {
-            tz = __shfl_sync(0xffffffffu, tz, cowner, LANES);
-            tt = __shfl_sync(0xffffffffu, tt, cowner, LANES);
-        }
+        // from the lane that owns the cost body (lane 0 holds the base's terms like every lane)
+        tz = __shfl_sync(0xffffffffu, tz, cowner, LANES);
+        tt = __shfl_sync(0xffffffffu, tt, cowner, LANES);
         // ---- pass 2 ----
         Art<float> carry;
         V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
