@@ -762,9 +762,6 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
         // ---- pass 1 ----
         B.R = quat_to_R(qw, qx, qy, qz);
         B.p = p;
-        // chain plans exist only for floating bases (model creation), so fixed_base is 0 and
-        // the other fixed-base branches are gone; these two selects stay because without them
-        // the compiler schedules the step loop worse (the launch took 12 % longer)
         B.w = w;  // chain plans exist only for floating bases (model creation)
         B.v = vl;
         V3<float> p0n, p0f;
@@ -778,13 +775,10 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
             const float bcst = base_cost(M, B.R, B.p);
             pcost += g == 0 ? bcst : 0.f;
         }
-        float tz, tt;
-        {  // the base's cost terms, selected when the base is the cost body (no branch)
-            float bz, bt;
-            cost_terms(M, B, bz, bt);
-            tz = cb == 0 ? bz : 0.f;
-            tt = cb == 0 ? bt : 0.f;
-        }
+        float tz = 0.f, tt = 0.f;
+        // inputs of the cost terms (height and the rotation's last column) of this lane's
+        // cost body, picked by selects along pass 1 (the base unless a chain body is it)
+        float cpz = B.p.z, cr2 = B.R.m[2], cr5 = B.R.m[5], cr8 = B.R.m[8];
         BodyMem mb;
         Pose PB;
         if (on_branch) {
@@ -800,10 +794,28 @@ __device__ __noinline__ float lanes_rollout(const DevModel<float>& M, int g, con
                     Pose P;
                     body_pass1<KEEP, PAPER, chain_axis<AXP, j>(), chain_offset<AXP, j>(), !LEAF_CONTACTS || j == 2>(
                         M, body(j), q[j], qd[j], Pp, P, mem[j], pcost, true);
-                    if (cb == b0 + j) cost_terms(M, P, tz, tt);
+                    if constexpr (AXP == AXP_XYY) {
+                        const bool own = cb == b0 + j;
+                        cpz = own ? P.p.z : cpz;
+                        cr2 = own ? P.R.m[2] : cr2;
+                        cr5 = own ? P.R.m[5] : cr5;
+                        cr8 = own ? P.R.m[8] : cr8;
+                    } else if (cb == b0 + j) {
+                        cost_terms(M, P, tz, tt);
+                    }
                     Pp = P;
                 }
             });
+        }
+        if constexpr (AXP == AXP_XYY) {
+            Pose Pc;
+            Pc.p.z = cpz;
+            Pc.R.m[2] = cr2;
+            Pc.R.m[5] = cr5;
+            Pc.R.m[8] = cr8;
+            cost_terms(M, Pc, tz, tt);
+        } else if (cb == 0) {
+            cost_terms(M, B, tz, tt);
         }
         // from the lane that owns the cost body (lane 0 holds the base's terms like every lane)
         tz = __shfl_sync(0xffffffffu, tz, cowner, LANES);
