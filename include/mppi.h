@@ -428,7 +428,8 @@ mppi_status mppi_ctx_info(const mppi_ctx* ctx, int32_t* h_out8);
  * +y, +y, hip offsets in the base's xy-plane, thigh and knee offsets on one axis, contact
  * points only on the calves), 2 the humanoid layout run by the two-warp split kernel
  * (legs z, x, y, y, y, x; waist z; arms y, x, z, y; offsets on one axis, in the yz-plane
- * or zero; contact points only on the feet); 1 when the modular cost of Sec. IV-A is on,
+ * or zero; contact points only on the feet; the cost body not on a leg); 1 when the
+ * modular cost of Sec. IV-A is on,
  * else 0; the number of bodies). With plan 2 the lanes-per-chain mapping needs blocks of
  * 64, 128 or 256 threads. */
 mppi_status mppi_model_info(const mppi_model* model, int32_t* h_out4);

@@ -145,7 +145,8 @@ static LanePlan detect_topology(const mppi_model_desc& d) {
                       offset_along(d, b + 3, 2);
             }
             const int feet[2] = {P.b0[0] + 5, P.b0[1] + 5};
-            if (hum && contacts_on(d, feet, 2)) P.axis_plan = AXP_HUM;
+            const bool cost_off_legs = d.cost_body < P.b0[0] || d.cost_body >= P.b0[1] + 6;
+            if (hum && contacts_on(d, feet, 2) && cost_off_legs) P.axis_plan = AXP_HUM;
             return P;
         }
     }

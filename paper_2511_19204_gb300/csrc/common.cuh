@@ -159,7 +159,7 @@ constexpr int TOPO_HUMANOID = 2;    // 2 chains of <= 6 off the base + a branch 
 // the passes exploit at compile time. AXP_HUM, the usual humanoid layout (6-joint legs off
 // the base turning about z, x, y, y, y, x; a waist joint about z carrying 4-joint arms that
 // turn about y, x, z, y; every joint offset on one axis, in the yz-plane or zero; contact
-// points only on the feet), runs the two-warp split kernel.
+// points only on the feet; the cost body not on a leg), runs the two-warp split kernel.
 constexpr int AXP_GENERIC = 0;
 constexpr int AXP_XYY = 1;
 constexpr int AXP_HUM = 2;

@@ -156,7 +156,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     }
     const float inv_dtk = 1.0f / dtk;
     float sum = 0.f, comp = 0.f;
-    const int cb = M.cost_body;
+    // the plan keeps the cost body off the legs (model creation checks it): no cost terms here
     const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     SegPoly kc[LEN];
     int kcur = -1;
@@ -184,7 +184,6 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
         // ---- pass 1: base, then the leg ----
         float pc = 0.f;  // this lane's share of the modular running cost
-        float tz = 0.f, tt = 0.f;
         BodyMem mem[LEN];
         {
             Pose Pp = B;
@@ -199,7 +198,6 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
                     mem[j].x0 = mem[j].x0 - fen;
                     mem[j].x1 = mem[j].x1 - fef;
                 }
-                if (cb == b0 + j) cost_terms(M, P, tz, tt);
                 Pp = P;
             });
         }
@@ -219,7 +217,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         float te = 0.f;
 #pragma unroll
         for (int j = 0; j < LEN; ++j) te += tau[j] * tau[j];
-        float lc = (tz + tt) + M.w_tau * te;
+        float lc = M.w_tau * te;
         if (PAPER) lc += pc;
         const float c_legs = pair_sum(lc);
         // ---- A: the waist subtree from the arm warp; base solve ----

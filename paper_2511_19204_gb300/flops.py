@@ -79,8 +79,8 @@ PER_JOINT_HUM_WAIST = 20 + 41 + 54 + 268 + 36
 
 def axis_plan_hum(model) -> bool:
     """True when the model runs the two-warp split kernel: a floating base with 2 legs of 6
-    bodies, a waist body on the base carrying 2 arms of 4, axes and offsets as above, and
-    contact points only on the feet."""
+    bodies, a waist body on the base carrying 2 arms of 4, axes and offsets as above,
+    contact points only on the feet and the cost body not on a leg."""
     import numpy as np
     if model.fixed_base or model.nb != 22:
         return False
@@ -110,7 +110,7 @@ def axis_plan_hum(model) -> bool:
                 return False
     feet = {6, 12}
     return bool(np.array_equal(model.axis[13], e[2]) and off(13, 2)
-                and all(int(b) in feet for b in model.contact_body))
+                and all(int(b) in feet for b in model.contact_body) and not 1 <= model.cost_body <= 12)
 
 
 def axis_plan_xyy(model) -> bool:

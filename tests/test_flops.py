@@ -39,6 +39,8 @@ def test_perturbed_layouts_use_the_generic_count():
     hand = h.copy(contact_body=np.append(h.contact_body, h.nb - 1).astype(np.int32),
                   contact_pos=np.vstack([h.contact_pos, [0.0, 0.0, -0.2]]))
     assert not F.axis_plan_hum(hand)
+    assert not F.axis_plan_hum(h.copy(cost_body=4))
+    assert F.axis_plan_hum(h.copy(cost_body=0))
     q = S.quadruped()
     jq = q.jpos.copy()
     jq[1, 2] = 0.01

@@ -251,7 +251,7 @@ def test_chain_axis_plans(M, orc, tilt):
     assert err.max() < 1e-4 and err_f.max() < 1e-4
 
 
-@pytest.mark.parametrize("variant", ["layout", "tilted", "offset", "hand_contact"])
+@pytest.mark.parametrize("variant", ["layout", "tilted", "offset", "hand_contact", "leg_cost"])
 def test_humanoid_axis_plans(M, orc, variant):
     # the humanoid's joint layout (legs z, x, y, y, y, x; waist z; arms y, x, z, y) selects
     # the two-warp split kernel (axis plan 2); a tilted hip axis or an elbow offset off its
@@ -271,6 +271,8 @@ def test_humanoid_axis_plans(M, orc, variant):
     elif variant == "hand_contact":   # a contact point off the feet
         m = m.copy(contact_body=np.append(m.contact_body, m.nb - 1).astype(np.int32),
                    contact_pos=np.vstack([m.contact_pos, [0.0, 0.0, -0.2]]))
+    elif variant == "leg_cost":       # the cost body on a leg
+        m = m.copy(cost_body=4)
     p.model = m
     mod = M.Model(m)
     assert mod.info()["topology"] == 2
