@@ -45,6 +45,7 @@ typedef int32_t mppi_status;
 #define MPPI_ERR_CUDA (-7)
 #define MPPI_ERR_UNSUPPORTED (-8)
 #define MPPI_ERR_NOT_FOUND (-9)
+#define MPPI_ERR_DEADLINE (-10)   /* a served request waited past the server's deadline and was shed */
 
 /* Rollout mappings (chosen per context, MPPI_MAP_AUTO asks the autotuner). */
 #define MPPI_MAP_AUTO (-1)
@@ -306,9 +307,11 @@ mppi_status mppi_average(int32_t K, int32_t E, const float* h_knots, const doubl
  * the work is enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and
  * nothing is allocated or freed. The FP64 partial sums live in one file-scope device
  * array of 2^20 doubles (8 MiB held on every device that loads the library), so
- * ceil(K / 64) * E must not exceed 1048576 (else MPPI_ERR_INVALID_ARG). The first call on
- * each device looks up that array's device address (cudaGetSymbolAddress, with the
- * device current); make that first call before any stream capture. Every call shares
+ * ceil(K / 64) * E must not exceed 1048576 (else MPPI_ERR_INVALID_ARG). The first call in
+ * each CUDA context looks up that array's device address (cudaGetSymbolAddress, with the
+ * device current) and caches it under the context's unique id; a device reset gives the
+ * device a new context, whose first call looks the address up again. Make the first call
+ * on a device (and the first after a reset) before any stream capture. Every call shares
  * the array and leaves its contents behind; each call writes every element it reads
  * before reading it, so nothing needs clearing, but calls that overlap on the GPU (on
  * different streams) race. Results equal mppi_average's. */
@@ -357,7 +360,15 @@ mppi_status mppi_selftest_queue_timeout(int64_t budget_us, int32_t* h_error_bits
 /* A request loop on `device` that admits solves while their device memory fits in
  * mem_budget_bytes and at most max_inflight launch groups are on the GPU; requests that
  * arrive while others run are admitted as slots and memory free up, and their work
- * overlaps on the device (separate streams). *out owned by the caller. */
+ * overlaps on the device (separate streams). Each of the max_inflight launch slots gets a
+ * device launch block (queue, descriptors, packed inputs and outputs) and two pinned host
+ * images of slot_bytes = min(4 MiB, floor(mem_budget_bytes / (4 max_inflight)) rounded
+ * down to 256 B) when the server is created; that reservation (max_inflight * slot_bytes,
+ * at most a quarter of the budget) counts against the budget for the server's lifetime, so
+ * the contexts of admitted requests may use the rest, and nothing is allocated while
+ * requests run. A batch is closed when the next request's launch block would overflow its
+ * slot. Errors: INVALID_ARG (slot_bytes below 16 KiB, max_inflight outside 1..64),
+ * OUT_OF_MEMORY, CUDA. *out owned by the caller. */
 mppi_status mppi_server_create(int32_t device, size_t mem_budget_bytes, int32_t max_inflight,
                                mppi_server** out);
 void mppi_server_destroy(mppi_server* server);
@@ -382,9 +393,21 @@ mppi_status mppi_poll(mppi_server* server, uint64_t ticket, float* h_out_mean,
  * polled to fetch its results and release it. */
 mppi_status mppi_next_completed(mppi_server* server, int64_t timeout_us, uint64_t* ticket, int64_t* times_ns);
 
-/* Server counters: [0] submitted, [1] completed, [2] launches, [3] peak bytes admitted,
- * [4] admissions deferred by the memory budget. */
+/* Load shedding: a request still waiting for admission deadline_us after it was submitted
+ * completes with MPPI_ERR_DEADLINE without running (its context's warm start and noise
+ * counter are unchanged), so the queue and the latency of the requests that run stay
+ * bounded when the offered load exceeds the server's capacity. 0 (the default) never
+ * sheds. A control loop sets it to the control period: a solve that starts later is of no
+ * use to it. Errors: INVALID_ARG (deadline_us < 0). */
+mppi_status mppi_server_set_deadline(mppi_server* server, int64_t deadline_us);
+
+/* Server counters: [0] submitted, [1] completed (shed requests included), [2] launches,
+ * [3] peak device bytes charged to the budget (the slots' reservation plus the admitted
+ * contexts' buffers), [4] admissions deferred by the memory budget. */
 mppi_status mppi_server_stats(mppi_server* server, int64_t* h_out5);
+/* The same counters and more: h_out[k] for k < n (n <= 8): [0..4] as above, [5] requests
+ * shed by the deadline, [6] bytes reserved for the launch slots, [7] bytes per slot. */
+mppi_status mppi_server_stats_ex(mppi_server* server, int64_t* h_out, int32_t n);
 
 /* ---------------------------------------------------------------------------------- */
 /* Autotuning and introspection                                                         */

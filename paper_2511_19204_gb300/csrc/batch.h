@@ -9,6 +9,7 @@
 namespace mppi {
 
 constexpr int BATCH_THREADS = 256;
+constexpr int BATCH_VARIANTS = 10;  // rollout variants, one persistent kernel each
 
 // The instances of one rollout variant (mapping, axis plan, modular cost), which walk
 // their own queue in their own persistent kernel: item counts, estimated work (tiles x
@@ -41,6 +42,10 @@ struct BatchStreams {
 };
 
 int batch_tile(int mapping);
+// Bounds of layout_batch(...).dev_bytes: batch_fixed_bound() + the sum of
+// batch_instance_bound() over the batch's contexts.
+size_t batch_fixed_bound();
+size_t batch_instance_bound(const mppi_ctx* c);
 size_t batch_smem_bytes(int max_E);
 BatchLayout layout_batch(mppi_ctx* const* ctxs, int count);
 void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double* const* states,

@@ -88,6 +88,7 @@ struct GroupDev {
 // Rollout variants of batched instances: one persistent kernel instantiation each.
 constexpr int BV_XYY = 0, BV_XYY_P = 1, BV_QUAD = 2, BV_QUAD_P = 3, BV_HUMG = 4, BV_HUMG_P = 5, BV_SPLIT = 6,
               BV_SPLIT_P = 7, BV_HALF = 8, BV_WARP = 9, BV_COUNT = 10;
+static_assert(BV_COUNT == BATCH_VARIANTS, "one persistent kernel per rollout variant");
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -530,6 +531,22 @@ BatchLayout layout_batch(mppi_ctx* const* ctxs, int count) {
         it += g.total;
     }
     return L;
+}
+
+// Upper bound of a launch block's bytes (layout_batch's dev_bytes): the fixed part (every
+// group's queue header and descriptor, the output header, the 256-byte rounding of each
+// section) plus each instance's share (descriptor, prefill entries, counters, queue items
+// of all its iterations, packed input and output records).
+size_t batch_fixed_bound() { return al256(sizeof(GroupDev) * BV_COUNT) + al256(sizeof(BatchQueue) * BV_COUNT) + 6 * 256 + 16; }
+
+size_t batch_instance_bound(const mppi_ctx* c) {
+    const size_t tile = (size_t)batch_tile(c->mapping);
+    const size_t ntiles = ((size_t)c->N + tile - 1) / tile;
+    const size_t items = (size_t)c->iters * (ntiles + (size_t)num_chunks(c->N));
+    const size_t in_rec = ((size_t)8 * c->nx + 16 + 4 * (size_t)c->E + 15) & ~(size_t)15;
+    const size_t out_rec = (sizeof(mppi_result) + 8 * (size_t)c->E + 15) & ~(size_t)15;
+    return sizeof(BatchInst) + sizeof(int) * 2 * ntiles + sizeof(InstCounters) + sizeof(QueueItem) * items + in_rec +
+           out_rec;
 }
 
 int batch_tile(int mapping) {

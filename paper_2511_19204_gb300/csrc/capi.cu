@@ -276,6 +276,7 @@ const char* mppi_status_str(mppi_status s) {
         case MPPI_ERR_CUDA: return "CUDA error";
         case MPPI_ERR_UNSUPPORTED: return "unsupported";
         case MPPI_ERR_NOT_FOUND: return "unknown ticket";
+        case MPPI_ERR_DEADLINE: return "shed: waited past the server's deadline";
         default: return "unknown status";
     }
 }

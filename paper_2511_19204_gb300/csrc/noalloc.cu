@@ -6,6 +6,7 @@
 // or a host whose allocator is owned by another framework. This entry point takes the
 // caller's device inputs and output and keeps its scratch (the per-chunk FP64 partial
 // sums) in a file-scope device array of fixed size instead of allocating it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -22,25 +23,59 @@ static __device__ __align__(256) double g_avg_scratch[NOALLOC_SCRATCH_DOUBLES];
 namespace {
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+// The scratch address is only valid in the context it was looked up in: a device reset
+// (cudaDeviceReset, or another framework releasing and recreating the primary context)
+// gives the device a new context whose copy of the array may sit elsewhere. So the cache
+// is keyed on the context's process-unique id (cuCtxGetId), not on the device number.
+struct ScratchEntry {
+    unsigned long long ctx_id = 0;
+    bool valid = false;
+    double* addr = nullptr;
+};
+ScratchEntry g_scratch[kMaxDevices];
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_ctx_get_id_looked_up = false;
+
+// Id of the context current on this thread; false when there is none yet or the driver
+// cannot tell.
+bool current_context_id(unsigned long long* id) {
+    if (!g_ctx_get_id_looked_up) {
+        g_ctx_get_id_looked_up = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(fn);
+    }
+    return g_ctx_get_id && g_ctx_get_id(nullptr, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
-// Device address of the scratch array on the current device. In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per device (with
-// that device current) and cached.
+// Device address of the scratch array in the current device's context. In host code the
+// array's name is only a host-side stand-in, so the address is looked up with the device
+// current (cudaGetSymbolAddress) once per context and cached; a new context on the device
+// (after a reset) is detected by its id and looked up again.
 static cudaError_t scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    ScratchEntry& c = g_scratch[dev];
+    if (!have_id || !c.valid || c.ctx_id != id) {
         double* p = nullptr;
+        // also makes the runtime's context current when no context was current yet
         e = cudaGetSymbolAddress((void**)&p, g_avg_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        if (!have_id) have_id = current_context_id(&id);
+        c.addr = p;
+        c.ctx_id = id;
+        c.valid = have_id;  // without a context id every call looks the address up again
     }
-    *out = g_scratch_addr[dev];
+    *out = c.addr;
     return cudaSuccess;
 }
 

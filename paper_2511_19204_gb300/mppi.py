@@ -29,6 +29,7 @@ MPPI_ERR_TIMEOUT = -6
 MPPI_ERR_CUDA = -7
 MPPI_ERR_UNSUPPORTED = -8
 MPPI_ERR_NOT_FOUND = -9
+MPPI_ERR_DEADLINE = -10
 
 MPPI_MAP_AUTO = -1
 MPPI_MAP_WARP = 0
@@ -130,6 +131,8 @@ SIGNATURES = [
     ("mppi_poll", C.c_int32, [_P, C.c_uint64, _fp, _fp, C.POINTER(mppi_result), C.c_int64]),
     ("mppi_next_completed", C.c_int32, [_P, C.c_int64, _u64p, _i64p]),
     ("mppi_server_stats", C.c_int32, [_P, _i64p]),
+    ("mppi_server_stats_ex", C.c_int32, [_P, _i64p, C.c_int32]),
+    ("mppi_server_set_deadline", C.c_int32, [_P, C.c_int64]),
     ("mppi_autotune", C.c_int32, [_P, _ip, _ip, _fp]),
     ("mppi_ctx_set_mapping", C.c_int32, [_P, C.c_int32, C.c_int32]),
     ("mppi_ctx_set_fp64_check", C.c_int32, [_P, C.c_int32]),
@@ -541,11 +544,16 @@ class Server:
         _check(st)
         return t.value, int(tm[0]), int(tm[1])
 
+    def set_deadline(self, deadline_us: int):
+        """Shed requests still waiting for admission deadline_us after submission
+        (they complete with MPPI_ERR_DEADLINE); 0 never sheds."""
+        _check(load().mppi_server_set_deadline(self.h, int(deadline_us)))
+
     def stats(self):
-        o = np.zeros(5, np.int64)
-        _check(load().mppi_server_stats(self.h, o.ctypes.data_as(_i64p)))
+        o = np.zeros(8, np.int64)
+        _check(load().mppi_server_stats_ex(self.h, o.ctypes.data_as(_i64p), 8))
         return dict(submitted=int(o[0]), completed=int(o[1]), launches=int(o[2]), peak_bytes=int(o[3]),
-                    deferred=int(o[4]))
+                    deferred=int(o[4]), shed=int(o[5]), reserved_bytes=int(o[6]), slot_bytes=int(o[7]))
 
     def close(self):
         if getattr(self, "h", None):

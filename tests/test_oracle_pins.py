@@ -487,6 +487,85 @@ def test_running_cost_on_ballistic_body(orc):
     assert S_or == pytest.approx(Sx, rel=1e-12)
 
 
+def _effort_only(m, w_tau):
+    """The model with every cost term off except the effort term w_tau |tau|^2."""
+    return m.copy(w_z=0.0, w_vx=0.0, w_tilt=0.0, w_tau=w_tau, w_h=0.0, w_orient=0.0, w_q=0.0,
+                  w_cvel=0.0, w_cforce=0.0, w_term=0.0)
+
+
+@pytest.mark.parametrize("target", [10.0, -10.0])
+def test_effort_cost_saturated_torque(orc, target):
+    # Sec. IV-A cost sum with only the effort term, Eq. (pd-controller) clipped to the
+    # actuator limit: a setpoint 10 rad away saturates the PD torque at +-tau_max on every
+    # step (the pendulum stays within 1 rad over 40 steps), so the sum is H w_tau tau_max^2.
+    # An unclipped torque would give ~(Kp 10)^2 per step, a dropped weight tau_max^2.
+    m = _effort_only(S.pendulum().copy(kp=np.array([30.0]), kd=np.array([2.0]), tau_max=np.array([0.5])), 0.37)
+    x = np.zeros(m.nx)
+    x[3] = 1.0
+    x[7] = 0.1
+    H, dt = 40, 0.01
+    kn = np.array([[[target], [0.0]], [[target], [0.0]]])
+    S_or, xf = orc.rollout(m, x, kn, H, dt)
+    # |q| < 1 and |v| < 10 keep |Kp (q_ref - q) + Kd (v_ref - v)| >= 30 * 9 - 2 * 10 >> tau_max
+    assert abs(xf[7]) < 1.0 and abs(xf[m.nq + 6]) < 10.0
+    assert S_or == pytest.approx(H * 0.37 * 0.5 ** 2, rel=1e-12)
+
+
+def test_effort_cost_charges_the_pre_step_torque(orc):
+    # Two steps, unsaturated: c(x_h, u_h) is charged at the pre-step states x_0 and x_1.
+    # The setpoint spline reproduces the line q(t) = 0.3 + 0.8 t exactly (knot values and
+    # slopes of a line), so q_ref(t_h) and v_ref(t_h) are known without the Hermite basis;
+    # x_1 is the pendulum's closed-form first step (semi-implicit Euler, Eq. for theta'' =
+    # (tau - m g l_c sin theta) / I_pivot). A torque charged after the step, or a missing
+    # square, changes the sum.
+    kp, kd, wt = 30.0, 2.0, 0.37
+    m = _effort_only(S.pendulum().copy(kp=np.array([kp]), kd=np.array([kd]), tau_max=np.array([50.0])), wt)
+    x = np.zeros(m.nx)
+    x[3] = 1.0
+    q0, v0 = 0.2, -0.5
+    x[7] = q0
+    x[m.nq + 6] = v0
+    H, dt = 2, 0.01
+    T = H * dt
+    a_line, b_line = 0.3, 0.8
+    kn = np.array([[[a_line], [b_line]], [[a_line + b_line * T], [b_line]]])
+    tau0 = kp * (a_line - q0) + kd * (b_line - v0)
+    ip = 0.02 + 1.3 * 0.16
+    acc = (tau0 - 1.3 * 9.81 * 0.4 * math.sin(q0)) / ip
+    v1 = v0 + dt * acc
+    q1 = q0 + dt * v1
+    tau1 = kp * (a_line + b_line * dt - q1) + kd * (b_line - v1)
+    assert max(abs(tau0), abs(tau1)) < 50.0
+    S_or, _ = orc.rollout(m, x, kn, H, dt)
+    assert S_or == pytest.approx(wt * (tau0 ** 2 + tau1 ** 2), rel=1e-12)
+    # one step charges tau_0 alone
+    S1, _ = orc.rollout(m, x, np.array([[[a_line], [b_line]], [[a_line + b_line * dt], [b_line]]]), 1, dt)
+    assert S1 == pytest.approx(wt * tau0 ** 2, rel=1e-12)
+
+
+def test_effort_cost_sums_joints_of_clipped_torques(orc):
+    # One step on a 2-joint chain: the effort is w_tau sum_j clip(tau_j)^2 with the first
+    # joint saturated and the second not (its setpoint is the current state plus a small
+    # offset); the dynamics do not enter a one-step sum.
+    kp = np.array([200.0, 3.0])
+    kd = np.array([1.0, 0.5])
+    tmax = np.array([0.8, 10.0])
+    m = _effort_only(S.chain2().copy(kp=kp, kd=kd, tau_max=tmax), 1.9)
+    x = np.zeros(m.nx)
+    x[3] = 1.0
+    q = np.array([0.1, -0.4])
+    v = np.array([0.3, 0.2])
+    x[7:9] = q
+    x[m.nq + 6:m.nq + 8] = v
+    qr = np.array([0.5, -0.35])
+    vr = np.array([0.0, 0.25])
+    kn = np.array([[qr, vr], [qr + vr * 0.01, vr]])
+    S_or, _ = orc.rollout(m, x, kn, 1, 0.01)
+    tau = np.clip(kp * (qr - q) + kd * (vr - v), -tmax, tmax)
+    assert abs(tau[0]) == 0.8 and abs(tau[1]) < 10.0
+    assert S_or == pytest.approx(1.9 * float(np.sum(tau ** 2)), rel=1e-12)
+
+
 # ------------------------------------------------------------------------------------
 # Weights (Eqs. omega-weights, softmax_minmax) and the average (Eq. update-nominal)
 # ------------------------------------------------------------------------------------
