@@ -282,6 +282,11 @@ mppi_status mppi_get_warm_start(const mppi_ctx* ctx, float* h_out);
  * pairs: h_out [n][3] = (sin x, cos x, atan2(y, x)). For accuracy checks. */
 mppi_status mppi_selftest_math(int32_t n, const float* h_x, const float* h_y, float* h_out);
 
+/* The knot average's exact FP32 -> FP64 widening by integer operations (no counterpart in
+ * the paper: the FP64 pipe of this part is narrow, so the average converts knots without
+ * it): h_out[i] = (double)h_x[i] for every float, NaNs quieted. For exactness checks. */
+mppi_status mppi_selftest_widen(int32_t n, const float* h_x, double* h_out);
+
 /* Philox4x32-10 (Salmon et al., SC'11) words for n counters: h_ctr [n][4], key [2],
  * h_out [n][4]. */
 mppi_status mppi_philox_words(int32_t n, const uint32_t* h_ctr, const uint32_t* h_key,

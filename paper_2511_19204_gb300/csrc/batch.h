@@ -9,6 +9,7 @@
 namespace mppi {
 
 constexpr int BATCH_THREADS = 256;
+static_assert(BATCH_THREADS >= 160, "the finalize holds up to 8 elements per thread of B - 32");
 constexpr int BATCH_VARIANTS = 10;  // rollout variants, one persistent kernel each
 
 // The instances of one rollout variant (mapping, axis plan, modular cost), which walk

@@ -50,6 +50,9 @@ struct BatchInst {
     float* costs;
     double* zq;
     double* partial;
+    double* gpartial;
+    double* gzq;
+    uint32_t* gcount;
     float* nominal;
     float* mean;
     float* best;
@@ -58,7 +61,7 @@ struct BatchInst {
     DevSolve* solve;
     mppi_result* result;
     double lambda;
-    int N, H, nk, nj, E, iters, mapping, tile, ntiles, nchunks, normalize, warm_from, has_limits, spline;
+    int N, H, nk, nj, E, iters, mapping, tile, ntiles, nchunks, ngroups, normalize, warm_from, has_limits, spline;
     float dt, dtk, scale_q, scale_v;
     uint32_t inst, seed_lo, seed_hi;
     // packed host <-> device exchange
@@ -67,7 +70,7 @@ struct BatchInst {
 };
 
 struct InstCounters {
-    int it, done_roll, done_red, pad;
+    int it, done_roll, pad0, pad1;
 };
 
 struct QueueItem {
@@ -155,7 +158,11 @@ __device__ __forceinline__ FinalizeArgs finalize_args(const BatchInst& I, int it
     FinalizeArgs f;
     f.partial = I.partial;
     f.zq = I.zq;
+    f.gpartial = I.gpartial;
+    f.gzq = I.gzq;
+    f.gcount = I.gcount;
     f.nchunks = I.nchunks;
+    f.ngroups = I.ngroups;
     f.E = I.E;
     f.iter = it;
     f.iters = I.iters;
@@ -311,24 +318,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 publish(items, q, ITEM_REDUCE, ii, I.nchunks);
             }
         } else {
-            const int c = s_item;
-            for (int ey = 0; ey * BATCH_THREADS < I.E; ++ey)
-                chunk_weights_average(I.costs, I.knots, I.N, I.E, I.lambda, I.normalize, c, ey, nullptr, I.zq,
-                                      I.partial, I.info);
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) s_last = atomicAdd(&ctr[ii].done_red, 1) == I.nchunks - 1;
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                finalize_iteration(finalize_args(I, it));
+            // the chunk's weights and partial sums; the last chunk of its group sums the
+            // group, the last group runs the finalize (the same function as single solves)
+            if (reduce_chunk(finalize_args(I, it), I.N, I.lambda, I.normalize, s_item)) {
                 __threadfence();
                 __syncthreads();
                 if (it + 1 < I.iters) {
-                    if (threadIdx.x == 0) {
-                        ctr[ii].done_red = 0;
-                        ctr[ii].it = it + 1;
-                    }
+                    if (threadIdx.x == 0) ctr[ii].it = it + 1;
                     __threadfence();
                     __syncthreads();
                     publish(items, q, ITEM_ROLLOUT, ii, I.ntiles);
@@ -378,14 +374,15 @@ __global__ void batch_reset_kernel(const BatchInst* __restrict__ insts, int coun
             I.nominal[e] = v;
             I.best[e] = v;
         }
+        for (int g = threadIdx.x; g < I.ngroups; g += blockDim.x) I.gcount[g] = 0;
         if (threadIdx.x == 0) {
             ctr[i].it = 0;
             ctr[i].done_roll = 0;
-            ctr[i].done_red = 0;
             I.solve->best_cost = INFINITY;
             I.solve->best_index = -1;
             I.solve->best_iter = -1;
             I.solve->status = MPPI_OK;
+            I.solve->blocks_done = 0;
         }
     }
     // head, append and error are read by no thread of this kernel (total and nprefill,
@@ -585,6 +582,9 @@ void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double*
         I.costs = c->d_costs;
         I.zq = c->d_zq;
         I.partial = c->d_partial;
+        I.gpartial = c->d_gpartial;
+        I.gzq = c->d_gzq;
+        I.gcount = c->d_gcount;
         I.nominal = c->d_nominal;
         I.mean = c->d_mean;
         I.best = c->d_best;
@@ -603,6 +603,7 @@ void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double*
         I.tile = batch_tile(c->mapping);
         I.ntiles = (c->N + I.tile - 1) / I.tile;
         I.nchunks = num_chunks(c->N);
+        I.ngroups = num_groups(c->N);
         I.normalize = c->normalize;
         I.warm_from = c->warm_from;
         I.has_limits = c->model->host_f.has_limits;

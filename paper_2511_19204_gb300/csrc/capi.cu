@@ -393,6 +393,9 @@ size_t ctx_layout(mppi_ctx* c, bool assign) {
     take(sizeof(double) * N, (void**)&c->d_w);
     take(sizeof(double) * num_chunks((int)N) * E, (void**)&c->d_partial);
     take(sizeof(double) * num_chunks((int)N) * 2, (void**)&c->d_zq);
+    take(sizeof(double) * num_groups((int)N) * E, (void**)&c->d_gpartial);
+    take(sizeof(double) * num_groups((int)N) * 2, (void**)&c->d_gzq);
+    take(sizeof(uint32_t) * num_groups((int)N), (void**)&c->d_gcount);
     take(sizeof(float) * E, (void**)&c->d_nominal);
     take(sizeof(float) * E, (void**)&c->d_mean);
     take(sizeof(float) * E, (void**)&c->d_best);
@@ -457,7 +460,11 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
         FinalizeArgs f;
         f.partial = c->d_partial;
         f.zq = c->d_zq;
+        f.gpartial = c->d_gpartial;
+        f.gzq = c->d_gzq;
+        f.gcount = c->d_gcount;
         f.nchunks = num_chunks(c->N);
+        f.ngroups = num_groups(c->N);
         f.E = c->E;
         f.iter = it;
         f.iters = c->iters;
@@ -470,13 +477,13 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
         f.mean_out = c->d_mean;
         f.best_out = c->d_best;
         f.result = c->d_result;
-        e = launch_weights_finalize(f, c->d_zq, c->d_partial, c->N, c->lambda, c->normalize, s);
+        e = launch_weights_finalize(f, c->N, c->lambda, c->normalize, s);
     }
     return e;
 }
 
 cudaError_t enqueue_solve_kernels(mppi_ctx* c, cudaStream_t s) {
-    cudaError_t e = launch_solve_begin(c->d_solve, c->d_nominal, c->d_best, c->E, s);
+    cudaError_t e = launch_solve_begin(c->d_solve, c->d_gcount, num_groups(c->N), c->d_nominal, c->d_best, c->E, s);
     for (int it = 0; it < c->iters && e == cudaSuccess; ++it) e = enqueue_iteration(c, it, s);
     return e;
 }
@@ -520,7 +527,8 @@ int default_mapping(const mppi_model* m, int N) {
 }
 
 cudaError_t prepare_kernels() {
-    cudaError_t e = prepare_warp_f32();
+    cudaError_t e = prepare_weights_kernels();
+    if (e == cudaSuccess) e = prepare_warp_f32();
     if (e == cudaSuccess) e = prepare_warp_f64();
     if (e == cudaSuccess) e = prepare_thread_f32();
     return e;
@@ -635,6 +643,7 @@ mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t k
     e = cudaMemcpy(c->d_sigma, h_sigma, sizeof(float) * iters * knots, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_nominal, nom.data(), sizeof(float) * c->E, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_solve, &ds, sizeof ds, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_gcount, 0, sizeof(uint32_t) * num_groups(c->N));
     if (e == cudaSuccess) e = prepare_kernels();
     if (e != cudaSuccess) {
         mppi_status st = cuda_fail(nullptr, e, "context initialisation");
@@ -960,6 +969,22 @@ mppi_status mppi_selftest_math(int32_t n, const float* h_x, const float* h_y, fl
     if (d_y) cudaFree(d_y);
     if (d_o) cudaFree(d_o);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest_math");
+    return MPPI_OK;
+}
+
+mppi_status mppi_selftest_widen(int32_t n, const float* h_x, double* h_out) {
+    if (n < 0 || (n > 0 && (!h_x || !h_out))) return MPPI_ERR_INVALID_ARG;
+    if (n == 0) return MPPI_OK;
+    float* d_x = nullptr;
+    double* d_o = nullptr;
+    cudaError_t e = cudaMalloc(&d_x, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_o, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(d_x, h_x, sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_widen(n, d_x, d_o, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(h_out, d_o, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    if (d_x) cudaFree(d_x);
+    if (d_o) cudaFree(d_o);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest_widen");
     return MPPI_OK;
 }
 

@@ -47,6 +47,9 @@ struct mppi_ctx {
     double* d_w = nullptr;
     double* d_partial = nullptr;
     double* d_zq = nullptr;                      // [nchunks][2] per-chunk sum e, sum e^2
+    double* d_gpartial = nullptr;                // [ngroups][E] group totals of the partials
+    double* d_gzq = nullptr;                     // [ngroups][2]
+    uint32_t* d_gcount = nullptr;                // [ngroups] finished chunks per group
     float* d_nominal = nullptr;
     float* d_mean = nullptr;
     float* d_best = nullptr;

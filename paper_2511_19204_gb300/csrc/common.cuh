@@ -511,5 +511,6 @@ __device__ __forceinline__ bool bulk_load_to_smem(void* smem_dst, const void* gm
 constexpr uint32_t DEV_ERR_TMA_TIMEOUT = 1u;
 constexpr uint32_t DEV_ERR_QUEUE_TIMEOUT = 2u;
 constexpr uint32_t DEV_ERR_BAD_ITEM = 4u;
+constexpr uint32_t DEV_ERR_GRID_TIMEOUT = 8u;
 
 }  // namespace mppi

@@ -13,6 +13,7 @@ namespace mppi {
 
 constexpr int REDUCE_THREADS = 256;   // fixed: the weight reduction order depends on it
 constexpr int AVG_CHUNK = 64;         // samples per FP64 partial sum of the knot average
+constexpr int AVG_GROUP = 16;         // chunks per group total (the second level of the sum)
 constexpr int AVG_THREADS = 128;
 
 // Per-iteration weight information (device), written by the weights step.
@@ -26,7 +27,7 @@ struct DevSolve {
     double best_cost;
     int32_t best_index, best_iter, status, pad;
     uint32_t iter_counter;   // Philox counter word 2 of the solve's first iteration
-    uint32_t blocks_done;    // blocks of the running weights launch that finished (last resets)
+    uint32_t blocks_done;    // groups of the running weights launch that finished (the last resets it)
     uint32_t dev_error;      // DEV_ERR_* bits from bounded device waits
     uint32_t pad3;
 };
@@ -88,9 +89,12 @@ cudaError_t launch_average_partial(const float* knots, const double* w, int N, i
                                    cudaStream_t s);
 cudaError_t launch_average_reduce(const double* partial, int nchunks, int E, double* out, cudaStream_t s);
 struct FinalizeArgs {
-    const double* partial;
-    const double* zq;
-    int nchunks, E, iter, iters, warm_from;
+    double* partial;    // [nchunks][E] chunk partial sums
+    double* zq;         // [nchunks][2] chunk (z_c, q_c)
+    double* gpartial;   // [ngroups][E] group totals
+    double* gzq;        // [ngroups][2]
+    uint32_t* gcount;   // [ngroups] chunks of the group finished (zero between iterations)
+    int nchunks, ngroups, E, iter, iters, warm_from;
     const float* knots;
     const float* costs;
     DevIterInfo* info;
@@ -100,13 +104,14 @@ struct FinalizeArgs {
     float* best_out;    // [E]
     mppi_result* result;
 };
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
-// chunk weights + partial sums with the finalize run by the last block to finish (one
-// launch per iteration); zq and partial as in launch_weights_average
-cudaError_t launch_weights_finalize(const FinalizeArgs& a, double* zq, double* partial, int N, double lambda,
-                                    int normalize, cudaStream_t s);
-cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* best_out, int E, cudaStream_t s);
+// chunk weights + partial sums, the group totals by the last chunk of each group and the
+// finalize by the last group to finish (one launch per iteration)
+cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda, int normalize, cudaStream_t s);
+cudaError_t prepare_weights_kernels();   // co-residency of the cooperative finish, per device
+cudaError_t launch_solve_begin(DevSolve* solve, uint32_t* gcount, int ngroups, const float* nominal, float* best_out,
+                               int E, cudaStream_t s);
 cudaError_t launch_fast_math(int n, const float* x, const float* y, float* out, cudaStream_t s);
+cudaError_t launch_widen(int n, const float* x, double* out, cudaStream_t s);
 cudaError_t launch_philox_words(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s);
 cudaError_t launch_dynamics_f32(const DevModel<float>* m, int n, const double* x, const double* tau, double* acc,
                                 cudaStream_t s);
@@ -114,5 +119,6 @@ cudaError_t launch_dynamics_f64(const DevModel<double>* m, int n, const double* 
                                 cudaStream_t s);
 
 __host__ __device__ inline int num_chunks(int N) { return (N + AVG_CHUNK - 1) / AVG_CHUNK; }
+__host__ __device__ inline int num_groups(int N) { return (num_chunks(N) + AVG_GROUP - 1) / AVG_GROUP; }
 
 }  // namespace mppi

@@ -1,7 +1,7 @@
 // Per-iteration kernels around the rollout: knot noise (Alg. 1 sampling + Eq. vel-clamp),
-// chunked weights with FP64 partial knot sums (Eqs. omega-weights / softmax_minmax,
-// Eq. update-nominal) and the iteration's finalize (log-sum-exp, mean, best tracking of
-// Sec. III-D).
+// chunked weights with FP64 partial knot sums and group totals (Eqs. omega-weights /
+// softmax_minmax, Eq. update-nominal) and the iteration's finalize (log-sum-exp, mean,
+// best tracking of Sec. III-D).
 #pragma once
 #include "internal.h"
 #include "noise.cuh"
@@ -49,19 +49,19 @@ cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------
-// K3: weights and partial knot sums per chunk (grid = chunks x element tiles).
+// K3 (standalone weights entry point): weights and (z_c, q_c) per chunk (grid = chunks).
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(AVG_THREADS) weights_average_kernel(const float* __restrict__ costs,
                                                                       const float* __restrict__ knots, int N, int E,
                                                                       double lambda, int normalize, double* e_out,
                                                                       double* zq, double* partial, DevIterInfo* info) {
-    chunk_weights_average(costs, knots, N, E, lambda, normalize, blockIdx.x, blockIdx.y, e_out, zq, partial, info);
+    chunk_partial(costs, knots, N, E, lambda, normalize, blockIdx.x, e_out, zq, partial, info);
 }
 
 cudaError_t launch_weights_average(const float* costs, const float* knots, int N, int E, double lambda, int normalize,
                                    double* e_out, double* zq, double* partial, DevIterInfo* info, cudaStream_t s) {
-    const dim3 grid(num_chunks(N), (E + AVG_THREADS - 1) / AVG_THREADS);
-    if (grid.x == 0) return cudaSuccess;
+    const int grid = num_chunks(N);
+    if (grid == 0) return cudaSuccess;
     weights_average_kernel<<<grid, AVG_THREADS, 0, s>>>(costs, knots, N, E, lambda, normalize, e_out, zq, partial, info);
     return cudaGetLastError();
 }
@@ -127,60 +127,84 @@ cudaError_t launch_average_reduce(const double* partial, int nchunks, int E, dou
 // ------------------------------------------------------------------------------------
 // Iteration bookkeeping.
 // ------------------------------------------------------------------------------------
-// One block; the element sums are spread over 1024 threads (each (sub-sum, element) task
-// sums its chunks in the same order whatever the block size, so the persistent kernel's
-// 256-thread finalize gives the same bits).
-__global__ void __launch_bounds__(1024) finalize_kernel(FinalizeArgs a) { finalize_iteration(a); }
-
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-    finalize_kernel<<<1, 1024, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-// Weights and chunk partial sums, then the iteration's finalize in the block that
-// finishes last (each block fences its writes and counts itself in DevSolve::blocks_done;
-// the last one resets the counter): one launch per iteration instead of two, the same
-// sums in the same order.
+// Weights, chunk partial sums, group totals and the iteration's finalize in one launch per
+// iteration: one block per chunk; the last chunk of each group sums the group, the last
+// group runs the finalize (reduce_chunk). 1024 threads: a chunk's 8 x 128 first-tile
+// (sub-sum, element) tasks take one thread each, and the FP64 work of a chunk is spread
+// over all four schedulers of its SM.
 constexpr int WF_THREADS = 1024;
 
-__global__ void __launch_bounds__(WF_THREADS) weights_finalize_kernel(FinalizeArgs f, double* zq, double* partial,
-                                                                       int N, double lambda, int normalize) {
-    __shared__ int s_last;
-    chunk_weights_average(f.costs, f.knots, N, f.E, lambda, normalize, blockIdx.x, blockIdx.y, nullptr, zq, partial,
-                          f.info);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned total = gridDim.x * gridDim.y;
-        s_last = atomicAdd(&f.solve->blocks_done, 1u) == total - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    finalize_iteration(f);
-    if (threadIdx.x == 0) f.solve->blocks_done = 0;
+__global__ void __launch_bounds__(WF_THREADS) weights_finalize_kernel(FinalizeArgs f, int N, double lambda,
+                                                                       int normalize) {
+    reduce_chunk(f, N, lambda, normalize, blockIdx.x);
 }
 
-cudaError_t launch_weights_finalize(const FinalizeArgs& a, double* zq, double* partial, int N, double lambda,
-                                    int normalize, cudaStream_t s) {
-    const dim3 grid(num_chunks(N), (a.E + WF_THREADS - 1) / WF_THREADS);
-    if (grid.x == 0) return cudaSuccess;
-    weights_finalize_kernel<<<grid, WF_THREADS, 0, s>>>(a, zq, partial, N, lambda, normalize);
+// The single-level finish (reduce_chunk_grid) in a cooperative launch, one chunk per block.
+__global__ void __launch_bounds__(WF_THREADS) weights_grid_kernel(FinalizeArgs f, int N, double lambda,
+                                                                   int normalize) {
+    reduce_chunk_grid(f, N, lambda, normalize);
+}
+
+// Blocks of weights_grid_kernel that can be resident at once on each device (0 where
+// cooperative launches are not supported); filled by prepare_weights_kernels.
+static int g_grid_capacity[64] = {0};
+
+cudaError_t prepare_weights_kernels() {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_grid_kernel, WF_THREADS, 0);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_grid_capacity[dev] = coop ? per_sm * sms : 0;
+    return e;
+}
+
+// One launch per iteration. When all chunks fit on the device at once (and in at most 16
+// groups) the cooperative single-level finish runs, else the two-level one; both give the
+// same bits.
+cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda, int normalize, cudaStream_t s) {
+    const int grid = num_chunks(N);
+    if (grid == 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int cap = dev >= 0 && dev < 64 ? g_grid_capacity[dev] : 0;
+    if (grid <= cap && grid <= 16 * AVG_GROUP) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(WF_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, weights_grid_kernel, a, N, lambda, normalize);
+    }
+    weights_finalize_kernel<<<grid, WF_THREADS, 0, s>>>(a, N, lambda, normalize);
     return cudaGetLastError();
 }
 
-__global__ void solve_begin_kernel(DevSolve* solve, const float* nominal, float* best_out, int E) {
+// Start of a solve: best tracking reset, the best knots start as the nominal, and the
+// reduction's counters are cleared (they are zero after every completed iteration; a
+// launch that gave up part-way could have left them set).
+__global__ void solve_begin_kernel(DevSolve* solve, uint32_t* gcount, int ngroups, const float* nominal,
+                                   float* best_out, int E) {
     if (threadIdx.x == 0) {
         solve->best_cost = INFINITY;
         solve->best_index = -1;
         solve->best_iter = -1;
         solve->status = MPPI_OK;
+        solve->blocks_done = 0;
     }
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) gcount[g] = 0;
     for (int e = threadIdx.x; e < E; e += blockDim.x) best_out[e] = nominal[e];
 }
 
-cudaError_t launch_solve_begin(DevSolve* solve, const float* nominal, float* best_out, int E, cudaStream_t s) {
-    solve_begin_kernel<<<1, 256, 0, s>>>(solve, nominal, best_out, E);
+cudaError_t launch_solve_begin(DevSolve* solve, uint32_t* gcount, int ngroups, const float* nominal, float* best_out,
+                               int E, cudaStream_t s) {
+    solve_begin_kernel<<<1, 256, 0, s>>>(solve, gcount, ngroups, nominal, best_out, E);
     return cudaGetLastError();
 }
 
@@ -244,6 +268,18 @@ __global__ void fast_math_kernel(int n, const float* __restrict__ x, const float
 cudaError_t launch_fast_math(int n, const float* x, const float* y, float* out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     fast_math_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, y, out);
+    return cudaGetLastError();
+}
+
+// The reduction's integer FP32 -> FP64 widening on a list of values (exactness checks).
+__global__ void widen_kernel(int n, const float* __restrict__ x, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = widen(x[i]);
+}
+
+cudaError_t launch_widen(int n, const float* x, double* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    widen_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, out);
     return cudaGetLastError();
 }
 

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("mppi_get_warm_start", C.c_int32, [_P, _fp]),
     ("mppi_model_info", C.c_int32, [_P, _ip]),
     ("mppi_selftest_math", C.c_int32, [C.c_int32, _fp, _fp, _fp]),
+    ("mppi_selftest_widen", C.c_int32, [C.c_int32, _fp, _dp]),
     ("mppi_autotune_cache_file", C.c_int32, [C.c_char_p]),
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
@@ -573,6 +574,14 @@ def selftest_math(x, y):
     ys = _f(y).reshape(-1).copy()
     out = np.zeros((xs.shape[0], 3), np.float32)
     _check(load().mppi_selftest_math(xs.shape[0], _pf(xs), _pf(ys), _pf(out)))
+    return out
+
+
+def selftest_widen(x):
+    """The knot average's integer FP32 -> FP64 widening of x (float32), as float64."""
+    xs = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    out = np.zeros(xs.shape[0], np.float64)
+    _check(load().mppi_selftest_widen(xs.shape[0], _pf(xs), _pd(out)))
     return out
 
 

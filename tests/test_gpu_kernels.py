@@ -352,3 +352,21 @@ def test_rollout_elementary_functions(M):
           f"fast_atan2_pos: max abs error {err_at.max():.2e}")
     assert err_sc.max() < 2.5e-7
     assert err_at.max() < 5e-7
+
+
+def test_widening_is_the_exact_conversion(M):
+    # The knot average converts FP32 knots to FP64 by integer operations only; every float
+    # must come out as (double)x bit for bit: normals, signed zeros, subnormals, extremes,
+    # infinities, and any bit pattern (NaNs compared as NaN).
+    rng = np.random.default_rng(5)
+    x = np.concatenate([
+        rng.normal(size=4096).astype(np.float32),
+        (rng.random(4096) * 1.2e-38).astype(np.float32),          # subnormals and the smallest normals
+        np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, -1e-45, 3.4028235e38, -3.4028235e38,
+                  1.17549435e-38, 1.1754942e-38], dtype=np.float32),
+        rng.integers(0, 2**32, size=65536, dtype=np.uint64).astype(np.uint32).view(np.float32)])
+    got = M.selftest_widen(x)
+    ref = x.astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    np.testing.assert_array_equal(got[~nan].view(np.uint64), ref[~nan].view(np.uint64))
