@@ -502,6 +502,7 @@ __device__ __forceinline__ bool grid_wait(uint32_t* counter, uint32_t target, ui
 // (at most 16 groups), the solve's blocks_done counter reset by the solve's first kernel.
 __device__ __forceinline__ void reduce_chunk_grid(const FinalizeArgs& f, int N, double lambda, int normalize) {
     __shared__ double s_G[1024];       // [element slot][group] group totals of this block's elements
+    __shared__ double s_zq[2 * 16 * AVG_GROUP];   // every chunk's (z_c, q_c), loaded coalesced
     __shared__ double s_zg[2 * 16];    // [z | q][group]
     __shared__ double s_inv_z;
     __shared__ int s_ok, s_upd, s_best, s_best_final;
@@ -538,16 +539,21 @@ __device__ __forceinline__ void reduce_chunk_grid(const FinalizeArgs& f, int N, 
             s_G[k] = tree16n(v, cn);
         }
     } else {
+        // the scalar warp: every chunk's (z_c, q_c) in coalesced loads (each block reads all
+        // of them, so scattered per-lane loads would queue on their few L2 lines), then
+        // the group trees from shared memory
         const int l = t - ts;
+        if (l == 0) inf = *f.info;
+        for (int i = l; i < 2 * f.nchunks; i += 32) s_zq[i] = __ldcg(f.zq + i);
+        __syncwarp();
         if (l < 2 * ng) {
             const int which = l / ng, g = l - which * ng;
             const int c0 = g * AVG_GROUP, cn = min(AVG_GROUP, f.nchunks - c0);
             double v[AVG_GROUP];
 #pragma unroll
-            for (int j = 0; j < AVG_GROUP; ++j) v[j] = j < cn ? __ldcg(f.zq + 2 * (c0 + j) + which) : 0.0;
+            for (int j = 0; j < AVG_GROUP; ++j) v[j] = j < cn ? s_zq[2 * (c0 + j) + which] : 0.0;
             s_zg[which * 16 + g] = tree16n(v, cn);
         }
-        if (t == ts) inf = *f.info;
     }
     __syncthreads();
     double z = 0.0, q = 0.0;

@@ -138,3 +138,30 @@ def test_every_rollout_variant_in_one_batch(M):
         np.testing.assert_array_equal(m, r[0].reshape(-1), err_msg=f"instance {i}")
         np.testing.assert_array_equal(b, r[1].reshape(-1), err_msg=f"instance {i}")
         assert inf["best_cost"] == r[2]["best_cost"]
+
+
+@pytest.mark.parametrize("K", [4000, 12000])
+def test_large_instances_batch_equals_alone_bitwise(M, orc, K):
+    """Several chunk groups and a ragged last chunk, on both single-solve reductions: 4000
+    samples (63 chunks, 4 groups) fit on the device at once and finish cooperatively,
+    12000 (188 chunks, 12 groups) finish group by group. Both must equal the batched
+    kernel's group-by-group reduction bit for bit, and the oracle at 1e-3."""
+    quad = S.quadruped()
+    mq = M.Model(quad)
+    nk, H, it = 6, 40, 2
+    sig = S.linear_sigma(nk, it)
+    x0 = S.standing_state(quad, jitter=0.02, base_vel=0.2, seed=77)
+    warm = S.nominal_knots(quad, nk).astype(np.float32)
+    kw = dict(iters=it, dt=0.005, seed=5, instance=2, mapping=2)
+    alone = M.Controller(mq, K, H, nk, 0.1, sig, **kw)
+    batch = M.Controller(mq, K, H, nk, 0.1, sig, **kw)
+    ref = alone.solve(x0, warm=warm)
+    rc, means, bests, infos = _batch(M, [batch], [x0], [warm])
+    assert rc == 0
+    np.testing.assert_array_equal(means[0], ref[0].reshape(-1))
+    np.testing.assert_array_equal(bests[0], ref[1].reshape(-1))
+    assert infos[0]["ess"] == ref[2]["ess"] and infos[0]["best_cost"] == ref[2]["best_cost"]
+    o = orc.solve(quad, K, nk, H, it, 0.005, 0.1, sig, x0, warm.astype(np.float64), seed=5, inst=2)
+    err = float(np.max(np.abs(ref[0] - o["mean"]) / np.maximum(1.0, np.abs(o["mean"]))))
+    assert err <= 1e-3, err
+    assert ref[2]["best_cost"] == pytest.approx(o["best_cost"], rel=1e-3)
