@@ -35,8 +35,7 @@
 #include "capi_internal.h"
 #include "noise.cuh"
 #include "reduce.cuh"
-#include "rollout_lanes.cuh"
-#include "rollout_split.cuh"
+#include "chain_f32.cuh"
 
 namespace mppi {
 

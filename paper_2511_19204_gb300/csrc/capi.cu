@@ -754,9 +754,14 @@ mppi_status mppi_rollout_explicit(mppi_ctx* c, const double* h_state, const floa
             a.nk = c->nk;
             a.dt = c->dt;
             a.dtk = c->dtk;
-            e = launch_rollout_warp_f64(a, c->mapping == MPPI_MAP_HALFWARP ? 16 : 32,
-                                        c->mapping == MPPI_MAP_WARP || c->mapping == MPPI_MAP_HALFWARP ? c->block : 64,
-                                        c->stream);
+            if (c->mapping == MPPI_MAP_CHAIN)  // the product's chain kernels, in double
+                e = launch_rollout_chain_f64(a, c->model->topology, c->model->host_f.paper_cost != 0,
+                                             c->model->host_f.axis_plan, c->stream);
+            else
+                e = launch_rollout_warp_f64(a, c->mapping == MPPI_MAP_HALFWARP ? 16 : 32,
+                                            c->mapping == MPPI_MAP_WARP || c->mapping == MPPI_MAP_HALFWARP ? c->block
+                                                                                                          : 64,
+                                            c->stream);
         } else {
             RolloutArgs<float> a;
             e = enqueue_rollout(c, d_x, d_k, N, (float*)d_c, d_f, c->stream);

@@ -1,7 +1,6 @@
 // Lanes-per-chain rollout kernels (see rollout_lanes.cuh and rollout_split.cuh).
 #pragma once
-#include "rollout_lanes.cuh"
-#include "rollout_split.cuh"
+#include "chain_f32.cuh"
 
 namespace mppi {
 

@@ -68,6 +68,9 @@ bool thread_mapping_supported(int topology);
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
                                      cudaStream_t s);
 bool chain_mapping_supported(int topology);
+// FP64 check build of the lanes-per-chain kernels (128-thread blocks)
+cudaError_t launch_rollout_chain_f64(const RolloutArgs<double>& a, int topology, bool paper, int axis_plan,
+                                     cudaStream_t s);
 // state after the first nsteps steps of knots [nk][2][nj] from x0 (one warp, Sec. III-E)
 cudaError_t launch_predict_f32(const DevModel<float>* m, const double* x0, const float* knots, int H, int nsteps,
                                int nk, float dt, float dtk, double* out, uint32_t* status, cudaStream_t s);

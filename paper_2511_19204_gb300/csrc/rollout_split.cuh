@@ -22,14 +22,14 @@
 // hold the same bits). Equations as in the other rollout kernels: Sec. III-A Hermite
 // setpoints, Sec. III-C PD tracking, the articulated-body algorithm, semi-implicit Euler,
 // Kahan-summed running cost (Alg. 1).
-#pragma once
-#include "rollout_lanes.cuh"
-
-namespace mppi {
+//
+// A body included after rollout_lanes.cuh by chain_f32.cuh (FP32) and by the FP64 check
+// build's translation unit, with the scalar macros of scalar_macros.h.
+R_NS_BEGIN
 
 constexpr int SPLIT_SPP = 16;                                 // samples per warp pair
-constexpr int SPLIT_REC = 36;                                 // floats per record (16-B aligned, bank-spread)
-constexpr int SPLIT_PAIR_FLOATS = 2 * SPLIT_SPP * SPLIT_REC;  // records A, then records B
+constexpr int SPLIT_REC = 36;                                 // values per record (16-B aligned, bank-spread)
+constexpr int SPLIT_PAIR_FLOATS = 2 * SPLIT_SPP * SPLIT_REC;  // values: records A, then records B
 constexpr int SPLIT_LEG = 6, SPLIT_ARM = 4;
 constexpr int SPLIT_WAIST_AX = 2, SPLIT_WAIST_OF = 2;         // waist: about z, offset along z
 
@@ -50,9 +50,9 @@ __host__ __device__ constexpr int split_offset() {
 // declared __restrict__, since the partner warp writes the same words.
 __device__ __forceinline__ void pair_sync(int id) { asm volatile("barrier.sync %0, 64;" ::"r"(id) : "memory"); }
 
-__device__ __forceinline__ float pair_sum(float v) { return v + __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ R_T pair_sum(R_T v) { return v + __shfl_xor_sync(0xffffffffu, v, 1); }
 
-__device__ __forceinline__ void pair_sum(Art<float>& c, V3<float>& n, V3<float>& f) {
+__device__ __forceinline__ void pair_sum(Art<R_T>& c, V3<R_T>& n, V3<R_T>& f) {
 #pragma unroll
     for (int t = 0; t < 6; ++t) c.A[t] = pair_sum(c.A[t]);
 #pragma unroll
@@ -63,47 +63,58 @@ __device__ __forceinline__ void pair_sum(Art<float>& c, V3<float>& n, V3<float>&
     f = v3(pair_sum(f.x), pair_sum(f.y), pair_sum(f.z));
 }
 
-// N float4 of a record; both lanes of a pair write the same values to the same words
+// N groups of 4 values of a record (one float4 each in FP32); both lanes of a pair write
+// the same values to the same words
 template <int N>
-__device__ __forceinline__ void rec_store(float* rec, const float (&v)[4 * N]) {
-    float4* d = reinterpret_cast<float4*>(rec);
+__device__ __forceinline__ void rec_store(R_T* rec, const R_T (&v)[4 * N]) {
+    if constexpr (std::is_same<R_T, float>::value) {
+        float4* d = reinterpret_cast<float4*>(rec);
 #pragma unroll
-    for (int k = 0; k < N; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        for (int k = 0; k < N; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4 * N; ++k) rec[k] = v[k];
+    }
 }
 template <int N>
-__device__ __forceinline__ void rec_load(const float* rec, float (&v)[4 * N]) {
-    const float4* s = reinterpret_cast<const float4*>(rec);
+__device__ __forceinline__ void rec_load(const R_T* rec, R_T (&v)[4 * N]) {
+    if constexpr (std::is_same<R_T, float>::value) {
+        const float4* s = reinterpret_cast<const float4*>(rec);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const float4 x = s[k];
-        v[4 * k] = x.x;
-        v[4 * k + 1] = x.y;
-        v[4 * k + 2] = x.z;
-        v[4 * k + 3] = x.w;
+        for (int k = 0; k < N; ++k) {
+            const float4 x = s[k];
+            v[4 * k] = x.x;
+            v[4 * k + 1] = x.y;
+            v[4 * k + 2] = x.z;
+            v[4 * k + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4 * N; ++k) v[k] = rec[k];
     }
 }
 
 // record B holds two parts with different writers: the base acceleration (aw, av) at
 // floats [0, 8), written by the leg warp, and the next base pose (R, p, w, v) at [8, 28),
 // written by the arm warp, which integrates the base.
-__device__ __forceinline__ void put_acc(float* rec, V3<float> aw, V3<float> av) {
-    const float v[8] = {aw.x, aw.y, aw.z, av.x, av.y, av.z, 0.f, 0.f};
+__device__ __forceinline__ void put_acc(R_T* rec, V3<R_T> aw, V3<R_T> av) {
+    const R_T v[8] = {aw.x, aw.y, aw.z, av.x, av.y, av.z, R_C(0.), R_C(0.)};
     rec_store<2>(rec, v);
 }
-__device__ __forceinline__ void get_acc(const float* rec, V3<float>& aw, V3<float>& av) {
-    float v[8];
+__device__ __forceinline__ void get_acc(const R_T* rec, V3<R_T>& aw, V3<R_T>& av) {
+    R_T v[8];
     rec_load<2>(rec, v);
     aw = v3(v[0], v[1], v[2]);
     av = v3(v[3], v[4], v[5]);
 }
-__device__ __forceinline__ void put_pose(float* rec, const Pose& B) {
-    const float v[20] = {B.R.m[0], B.R.m[1], B.R.m[2], B.R.m[3], B.R.m[4], B.R.m[5], B.R.m[6],
+__device__ __forceinline__ void put_pose(R_T* rec, const Pose& B) {
+    const R_T v[20] = {B.R.m[0], B.R.m[1], B.R.m[2], B.R.m[3], B.R.m[4], B.R.m[5], B.R.m[6],
                          B.R.m[7], B.R.m[8], B.p.x,    B.p.y,    B.p.z,    B.w.x,    B.w.y,
-                         B.w.z,    B.v.x,    B.v.y,    B.v.z,    0.f,      0.f};
+                         B.w.z,    B.v.x,    B.v.y,    B.v.z,    R_C(0.),      R_C(0.)};
     rec_store<5>(rec + 8, v);
 }
-__device__ __forceinline__ void get_pose(const float* rec, Pose& B) {
-    float v[20];
+__device__ __forceinline__ void get_pose(const R_T* rec, Pose& B) {
+    R_T v[20];
     rec_load<5>(rec + 8, v);
 #pragma unroll
     for (int t = 0; t < 9; ++t) B.R.m[t] = v[t];
@@ -115,20 +126,20 @@ __device__ __forceinline__ void get_pose(const float* rec, Pose& B) {
 // Contact forces of a foot's points, evaluated whether or not a point penetrates (no
 // branch): a point above the ground gets fn = 0, so F = 0 and the sums are unchanged.
 template <bool PAPER>
-__device__ __forceinline__ void foot_contacts(const DevModel<float>& M, int b, const Pose& P, V3<float>& fen,
-                                              V3<float>& fef, float& pcost) {
+__device__ __forceinline__ void foot_contacts(const DevModel<R_T>& M, int b, const Pose& P, V3<R_T>& fen,
+                                              V3<R_T>& fef, R_T& pcost) {
     const int c0 = M.cfirst[b], cn = M.ccount[b];
     for (int c = 0; c < cn; ++c) {
         const int ci = c0 + c;
-        const V3<float> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
-        const V3<float> pc = P.p + mul(P.R, rc);
-        const float depth = -pc.z;
-        const bool touch = depth > 0.f;
-        const V3<float> vw = mul(P.R, P.v + cross(P.w, rc));
-        const float fn = touch ? fmaxf(M.contact_k * depth - M.contact_c * vw.z, 0.f) : 0.f;
-        const float sc = -M.mu * fn * rsqrtf(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
-        const V3<float> F = v3(sc * vw.x, sc * vw.y, fn);
-        const V3<float> fb = mulT(P.R, F);
+        const V3<R_T> rc = v3(M.cpos[0][ci], M.cpos[1][ci], M.cpos[2][ci]);
+        const V3<R_T> pc = P.p + mul(P.R, rc);
+        const R_T depth = -pc.z;
+        const bool touch = depth > R_C(0.);
+        const V3<R_T> vw = mul(P.R, P.v + cross(P.w, rc));
+        const R_T fn = touch ? R_MAX(M.contact_k * depth - M.contact_c * vw.z, R_C(0.)) : R_C(0.);
+        const R_T sc = -M.mu * fn * R_RSQRT(vw.x * vw.x + vw.y * vw.y + M.eps_f * M.eps_f);
+        const V3<R_T> F = v3(sc * vw.x, sc * vw.y, fn);
+        const V3<R_T> fb = mulT(P.R, F);
         fef = fef + fb;
         fen = fen + cross(rc, fb);
         if (PAPER) pcost += touch ? contact_cost(M, vw, F) : M.cf_off;
@@ -138,24 +149,24 @@ __device__ __forceinline__ void foot_contacts(const DevModel<float>& M, int b, c
 // Leg warp: both legs of one sample on lanes side = 0, 1, the base solve, the cost sum.
 // Returns the sample's cost (the same on both lanes).
 template <bool PAPER>
-__device__ __noinline__ float split_legs(const DevModel<float>& M, int side, const float* recA, float* recB, int bar,
+__device__ __noinline__ R_T split_legs(const DevModel<R_T>& M, int side, const R_T* recA, R_T* recB, int bar,
                                          const double* __restrict__ x0,
-                                         const float* __restrict__ knots, int H, int nk, float dt, float dtk,
+                                         const float* __restrict__ knots, int H, int nk, R_T dt, R_T dtk,
                                          double* __restrict__ xf) {
     constexpr int LEN = SPLIT_LEG;
     // the plan fixes the numbering: legs from bodies 1 and 7, the waist 13, arms from 14
     // and 18, 21 joints (compile-time, which shortens the launch)
     constexpr int nj = 21, nq = 7 + nj;
     const int b0 = 1 + 6 * side;
-    const V3<float> p_start = v3((float)x0[0], (float)x0[1], (float)x0[2]);
-    float q[LEN], qd[LEN];
+    const V3<R_T> p_start = v3((R_T)x0[0], (R_T)x0[1], (R_T)x0[2]);
+    R_T q[LEN], qd[LEN];
 #pragma unroll
     for (int j = 0; j < LEN; ++j) {
-        q[j] = (float)x0[7 + b0 - 1 + j];
-        qd[j] = (float)x0[nq + 6 + b0 - 1 + j];
+        q[j] = (R_T)x0[7 + b0 - 1 + j];
+        qd[j] = (R_T)x0[nq + 6 + b0 - 1 + j];
     }
-    const float inv_dtk = 1.0f / dtk;
-    float sum = 0.f, comp = 0.f;
+    const R_T inv_dtk = R_C(1.0) / dtk;
+    R_T sum = R_C(0.), comp = R_C(0.);
     // the plan keeps the cost body off the legs (model creation checks it): no cost terms here
     const ArtProj leafp = leaf_projection<split_axis<0, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     SegPoly kc[LEN];
@@ -163,7 +174,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
     Pose B;
     pair_sync(bar);
     get_pose(recB, B);  // the first base pose, from the arm warp
-    const float inv_H = 1.0f / (float)H;
+    const R_T inv_H = R_C(1.0) / (R_T)H;
     int k = 0, rem = -(nk - 1);
     for (int h = 0; h < H; ++h) {
         rem += nk - 1;
@@ -171,7 +182,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             rem -= H;
             ++k;
         }
-        const float s = (float)rem * inv_H;
+        const R_T s = (R_T)rem * inv_H;
         // power-basis setpoints, formed once per segment (the registers they hold became
         // free once the base's integration moved to the arm warp)
         if (k != kcur) {
@@ -179,11 +190,11 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
 #pragma unroll
             for (int j = 0; j < LEN; ++j) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
         }
-        float tau[LEN];
+        R_T tau[LEN];
 #pragma unroll
         for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
         // ---- pass 1: base, then the leg ----
-        float pc = 0.f;  // this lane's share of the modular running cost
+        R_T pc = R_C(0.);  // this lane's share of the modular running cost
         BodyMem mem[LEN];
         {
             Pose Pp = B;
@@ -193,7 +204,7 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
                 body_pass1<false, PAPER, split_axis<0, j>(), split_offset<0, j>(), false>(
                     M, load_body(M, b0 + j), q[j], qd[j], Pp, P, mem[j], pc, true);
                 if constexpr (j == LEN - 1) {  // the foot: its contact forces enter its bias
-                    V3<float> fen = v3(0.f, 0.f, 0.f), fef = fen;
+                    V3<R_T> fen = v3(R_C(0.), R_C(0.), R_C(0.)), fef = fen;
                     foot_contacts<PAPER>(M, b0 + j, P, fen, fef, pc);
                     mem[j].x0 = mem[j].x0 - fen;
                     mem[j].x1 = mem[j].x1 - fef;
@@ -202,8 +213,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
             });
         }
         // ---- pass 2: the leg inward, both legs summed at the base ----
-        Art<float> carry;
-        V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
+        Art<R_T> carry;
+        V3<R_T> cpn = v3(R_C(0.), R_C(0.), R_C(0.)), cpf = cpn;
         static_for<0, LEN>([&](auto ic) {
             constexpr int j = LEN - 1 - decltype(ic)::value;
             if constexpr (j == LEN - 1)
@@ -214,49 +225,49 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
                                                                           carry, cpn, cpf);
         });
         pair_sum(carry, cpn, cpf);
-        float te = 0.f;
+        R_T te = R_C(0.);
 #pragma unroll
         for (int j = 0; j < LEN; ++j) te += tau[j] * tau[j];
-        float lc = M.w_tau * te;
+        R_T lc = M.w_tau * te;
         if (PAPER) lc += pc;
-        const float c_legs = pair_sum(lc);
+        const R_T c_legs = pair_sum(lc);
         // ---- A: the waist subtree from the arm warp; base solve ----
         pair_sync(bar);
-        float a[28];
+        R_T a[28];
         rec_load<7>(recA, a);
         // record A holds the waist subtree plus the base's own inertia and bias force
-        Art<float> IA0;
+        Art<R_T> IA0;
 #pragma unroll
         for (int t = 0; t < 6; ++t) IA0.A[t] = carry.A[t] + a[t];
 #pragma unroll
         for (int t = 0; t < 9; ++t) IA0.B[t] = carry.B[t] + a[6 + t];
 #pragma unroll
         for (int t = 0; t < 6; ++t) IA0.C[t] = carry.C[t] + a[15 + t];
-        const V3<float> p0n = cpn + v3(a[21], a[22], a[23]);
-        const V3<float> p0f = cpf + v3(a[24], a[25], a[26]);
-        const float c_arms = a[27];
-        V3<float> aw, av;
+        const V3<R_T> p0n = cpn + v3(a[21], a[22], a[23]);
+        const V3<R_T> p0f = cpf + v3(a[24], a[25], a[26]);
+        const R_T c_arms = a[27];
+        V3<R_T> aw, av;
         {
-            const float rhs[6] = {-p0n.x, -p0n.y, -p0n.z, -p0f.x, -p0f.y, -p0f.z};
-            float x[6];
+            const R_T rhs[6] = {-p0n.x, -p0n.y, -p0n.z, -p0f.x, -p0f.y, -p0f.z};
+            R_T x[6];
             art_solve(IA0, rhs, x);
             aw = v3(x[0], x[1], x[2]);
             av = v3(x[3], x[4], x[5]);
         }
         // ---- running cost on the pre-step state (the base terms came with record A) ----
         {
-            const float c = c_legs + c_arms;
-            const float y = c - comp;
-            const float t = sum + y;
+            const R_T c = c_legs + c_arms;
+            const R_T y = c - comp;
+            const R_T t = sum + y;
             comp = (t - sum) - y;
             sum = t;
         }
         put_acc(recB, aw, av);
         pair_sync(bar);  // B: the arm warp integrates the base meanwhile
         // ---- pass 3 and the legs' joints ----
-        float qdd[LEN];
+        R_T qdd[LEN];
         {
-            V3<float> apw = aw, apv = av;
+            V3<R_T> apw = aw, apv = av;
             static_for<0, LEN>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
                 qdd[j] = body_pass3<false, split_axis<0, j>(), split_offset<0, j>()>(load_body(M, b0 + j), mem[j], apw,
@@ -272,8 +283,8 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
         get_pose(recB, B);
     }
     if (PAPER) {  // terminal cost (B holds the final base pose)
-        const float y = terminal_cost(M, B.p, p_start, H, dt) - comp;
-        const float t = sum + y;
+        const R_T y = terminal_cost(M, B.p, p_start, H, dt) - comp;
+        const R_T t = sum + y;
         comp = (t - sum) - y;
         sum = t;
     }
@@ -291,32 +302,32 @@ __device__ __noinline__ float split_legs(const DevModel<float>& M, int side, con
 // the floating base (replicated on both lanes). Returns 0; the sample's cost is the leg
 // warp's.
 template <bool PAPER>
-__device__ __noinline__ float split_arms(const DevModel<float>& M, int side, float* recA, float* recB, int bar,
+__device__ __noinline__ R_T split_arms(const DevModel<R_T>& M, int side, R_T* recA, R_T* recB, int bar,
                                          const double* __restrict__ x0,
-                                         const float* __restrict__ knots, int H, int nk, float dt, float dtk,
+                                         const float* __restrict__ knots, int H, int nk, R_T dt, R_T dtk,
                                          double* __restrict__ xf) {
     constexpr int LEN = SPLIT_ARM;
     constexpr int nj = 21, nq = 7 + nj;
     const int b0 = 14 + 4 * side;
     constexpr int bb = 13;
     const bool lead = side == 0;
-    float qb = (float)x0[7 + bb - 1], qdb = (float)x0[nq + 6 + bb - 1];
-    float q[LEN], qd[LEN];
+    R_T qb = (R_T)x0[7 + bb - 1], qdb = (R_T)x0[nq + 6 + bb - 1];
+    R_T q[LEN], qd[LEN];
 #pragma unroll
     for (int j = 0; j < LEN; ++j) {
-        q[j] = (float)x0[7 + b0 - 1 + j];
-        qd[j] = (float)x0[nq + 6 + b0 - 1 + j];
+        q[j] = (R_T)x0[7 + b0 - 1 + j];
+        qd[j] = (R_T)x0[nq + 6 + b0 - 1 + j];
     }
-    const float inv_dtk = 1.0f / dtk;
+    const R_T inv_dtk = R_C(1.0) / dtk;
     const int cb = M.cost_body;
     const ArtProj leafp = leaf_projection<split_axis<1, LEN - 1>(), false>(load_body(M, b0 + LEN - 1));
     SegPoly kc[LEN], kb;
     int kcur = -1;
     // the floating base: integrated here, its pose handed to the leg warp each step
-    V3<float> p = v3((float)x0[0], (float)x0[1], (float)x0[2]);
-    float qw = (float)x0[3], qx = (float)x0[4], qy = (float)x0[5], qz = (float)x0[6];
-    V3<float> vl = v3((float)x0[nq], (float)x0[nq + 1], (float)x0[nq + 2]);
-    V3<float> w = v3((float)x0[nq + 3], (float)x0[nq + 4], (float)x0[nq + 5]);
+    V3<R_T> p = v3((R_T)x0[0], (R_T)x0[1], (R_T)x0[2]);
+    R_T qw = (R_T)x0[3], qx = (R_T)x0[4], qy = (R_T)x0[5], qz = (R_T)x0[6];
+    V3<R_T> vl = v3((R_T)x0[nq], (R_T)x0[nq + 1], (R_T)x0[nq + 2]);
+    V3<R_T> w = v3((R_T)x0[nq + 3], (R_T)x0[nq + 4], (R_T)x0[nq + 5]);
     Pose B;
     B.R = quat_to_R(qw, qx, qy, qz);
     B.p = p;
@@ -324,8 +335,8 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
     B.v = vl;
     put_pose(recB, B);
     pair_sync(bar);
-    V3<float> aw, av;
-    const float inv_H = 1.0f / (float)H;
+    V3<R_T> aw, av;
+    const R_T inv_H = R_C(1.0) / (R_T)H;
     int k = 0, rem = -(nk - 1);
     for (int h = 0; h < H; ++h) {
         rem += nk - 1;
@@ -333,19 +344,19 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             rem -= H;
             ++k;
         }
-        const float s = (float)rem * inv_H;
+        const R_T s = (R_T)rem * inv_H;
         if (k != kcur) {
             kcur = k;
 #pragma unroll
             for (int j = 0; j < LEN; ++j) kc[j] = seg_poly(seg_knots(knots, nj, k, b0 + j), dtk);
             kb = seg_poly(seg_knots(knots, nj, k, bb), dtk);
         }
-        float tau[LEN];
+        R_T tau[LEN];
 #pragma unroll
         for (int j = 0; j < LEN; ++j) tau[j] = poly_pd(load_body(M, b0 + j), kc[j], s, inv_dtk, q[j], qd[j]);
-        const float taub = poly_pd(load_body(M, bb), kb, s, inv_dtk, qb, qdb);
+        const R_T taub = poly_pd(load_body(M, bb), kb, s, inv_dtk, qb, qdb);
         // ---- pass 1: waist, then the arm ----
-        float pc = 0.f, tz = 0.f, tt = 0.f;
+        R_T pc = R_C(0.), tz = R_C(0.), tt = R_C(0.);
         BodyMem mb;
         Pose PB;
         body_pass1<false, PAPER, SPLIT_WAIST_AX, SPLIT_WAIST_OF, false>(M, load_body(M, bb), qb, qdb, B, PB, mb, pc,
@@ -364,8 +375,8 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             });
         }
         // ---- pass 2: the arm inward, both arms summed at the waist, the waist ----
-        Art<float> carry;
-        V3<float> cpn = v3(0.f, 0.f, 0.f), cpf = cpn;
+        Art<R_T> carry;
+        V3<R_T> cpn = v3(R_C(0.), R_C(0.), R_C(0.)), cpf = cpn;
         static_for<0, LEN>([&](auto ic) {
             constexpr int j = LEN - 1 - decltype(ic)::value;
             if constexpr (j == LEN - 1)
@@ -379,7 +390,7 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
         body_pass2<false, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(load_body(M, bb), taub, mb, true, carry, cpn, cpf);
         // the base's own inertia and bias force, and its cost terms, off the leg warp's path
         {
-            Art<float> IB;
+            Art<R_T> IB;
             body_inertia(load_body(M, 0), IB);
 #pragma unroll
             for (int t = 0; t < 6; ++t) carry.A[t] += IB.A[t];
@@ -387,27 +398,27 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             for (int t = 0; t < 9; ++t) carry.B[t] += IB.B[t];
 #pragma unroll
             for (int t = 0; t < 6; ++t) carry.C[t] += IB.C[t];
-            V3<float> bn, bf;
-            const V3<float> z0 = v3(0.f, 0.f, 0.f);
+            V3<R_T> bn, bf;
+            const V3<R_T> z0 = v3(R_C(0.), R_C(0.), R_C(0.));
             body_bias(load_body(M, 0), B, z0, z0, bn, bf);
             cpn = cpn + bn;
             cpf = cpf + bf;
         }
         if (PAPER && lead) pc += base_cost(M, B.R, B.p);
         if (cb == 0 && lead) cost_terms(M, B, tz, tt);
-        float te = 0.f;
+        R_T te = R_C(0.);
 #pragma unroll
         for (int j = 0; j < LEN; ++j) te += tau[j] * tau[j];
         if (lead) te += taub * taub;
-        float lc = (tz + tt) + M.w_tau * te;
+        R_T lc = (tz + tt) + M.w_tau * te;
         if (PAPER) lc += pc;
         if (lead) {
-            const float vx = B.R.m[0] * B.v.x + B.R.m[1] * B.v.y + B.R.m[2] * B.v.z;
-            const float dv = vx - M.vx_des;
+            const R_T vx = B.R.m[0] * B.v.x + B.R.m[1] * B.v.y + B.R.m[2] * B.v.z;
+            const R_T dv = vx - M.vx_des;
             lc += M.w_vx * dv * dv;
         }
         {
-            const float v[28] = {carry.A[0], carry.A[1], carry.A[2], carry.A[3], carry.A[4], carry.A[5], carry.B[0],
+            const R_T v[28] = {carry.A[0], carry.A[1], carry.A[2], carry.A[3], carry.A[4], carry.A[5], carry.B[0],
                                  carry.B[1], carry.B[2], carry.B[3], carry.B[4], carry.B[5], carry.B[6], carry.B[7],
                                  carry.B[8], carry.C[0], carry.C[1], carry.C[2], carry.C[3], carry.C[4], carry.C[5],
                                  cpn.x,      cpn.y,      cpn.z,      cpf.x,      cpf.y,      cpf.z,      pair_sum(lc)};
@@ -418,23 +429,23 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
         get_acc(recB, aw, av);
         // ---- base: semi-implicit Euler, quaternion exponential; the next pose to the leg warp ----
         {
-            const V3<float> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
+            const V3<R_T> g_b = v3(-M.gravity * B.R.m[6], -M.gravity * B.R.m[7], -M.gravity * B.R.m[8]);
             w = w + dt * aw;
             vl = vl + dt * (av + g_b);
             p = p + dt * mul(B.R, vl);
-            const float wn = sqrtf(dot(w, w));
+            const R_T wn = R_SQRT(dot(w, w));
             // both branches evaluated, one selected (no branch in the step)
-            const bool tiny = wn * dt < 1e-12f;
-            float sh, ch;
-            fast_sincos(0.5f * wn * dt, &sh, &ch);
-            const float dq0 = tiny ? 1.f : ch;
-            const float dqs = tiny ? 0.5f * dt : __fdividef(sh, wn);
-            const float dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
-            const float nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
-            const float nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
-            const float ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
-            const float nz = qw * dz + qx * dy - qy * dx + qz * dq0;
-            const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
+            const bool tiny = wn * dt < R_C(1e-12);
+            R_T sh, ch;
+            R_SINCOS(R_C(0.5) * wn * dt, &sh, &ch);
+            const R_T dq0 = tiny ? R_C(1.) : ch;
+            const R_T dqs = tiny ? R_C(0.5) * dt : R_FDIV(sh, wn);
+            const R_T dx = dqs * w.x, dy = dqs * w.y, dz = dqs * w.z;
+            const R_T nw = qw * dq0 - qx * dx - qy * dy - qz * dz;
+            const R_T nx = qw * dx + qx * dq0 + qy * dz - qz * dy;
+            const R_T ny = qw * dy - qx * dz + qy * dq0 + qz * dx;
+            const R_T nz = qw * dz + qx * dy - qy * dx + qz * dq0;
+            const R_T inv = R_RSQRT(nw * nw + nx * nx + ny * ny + nz * nz);
             qw = nw * inv;
             qx = nx * inv;
             qy = ny * inv;
@@ -447,9 +458,9 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
         Bn.v = vl;
         put_pose(recB, Bn);
         // ---- pass 3 and the waist's and arm's joints ----
-        float qdd[LEN], qddb;
+        R_T qdd[LEN], qddb;
         {
-            V3<float> apw = aw, apv = av;
+            V3<R_T> apw = aw, apv = av;
             qddb = body_pass3<false, SPLIT_WAIST_AX, SPLIT_WAIST_OF>(load_body(M, bb), mb, apw, apv);
             static_for<0, LEN>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
@@ -491,21 +502,21 @@ __device__ __noinline__ float split_arms(const DevModel<float>& M, int side, flo
             xf[nq + 6 + b0 - 1 + j] = qd[j];
         }
     }
-    return 0.f;
+    return R_C(0.);
 }
 
 // One warp pair's rollout of 16 samples: warp 2p + 0 the legs, 2p + 1 the waist and arms.
 // rec = this pair's exchange area (SPLIT_PAIR_FLOATS floats of shared memory), bar its
 // named barrier; every lane of both warps must call it the same number of times.
 template <bool PAPER>
-__device__ __forceinline__ float split_rollout(const DevModel<float>& M, int role, int lane, float* rec, int bar,
+__device__ __forceinline__ R_T split_rollout(const DevModel<R_T>& M, int role, int lane, R_T* rec, int bar,
                                                const double* __restrict__ x0, const float* __restrict__ knots, int H,
-                                               int nk, float dt, float dtk, double* __restrict__ xf) {
+                                               int nk, R_T dt, R_T dtk, double* __restrict__ xf) {
     const int i = lane >> 1, side = lane & 1;
-    float* recA = rec + i * SPLIT_REC;
-    float* recB = rec + (SPLIT_SPP + i) * SPLIT_REC;
+    R_T* recA = rec + i * SPLIT_REC;
+    R_T* recB = rec + (SPLIT_SPP + i) * SPLIT_REC;
     return role == 0 ? split_legs<PAPER>(M, side, recA, recB, bar, x0, knots, H, nk, dt, dtk, xf)
                      : split_arms<PAPER>(M, side, recA, recB, bar, x0, knots, H, nk, dt, dtk, xf);
 }
 
-}  // namespace mppi
+R_NS_END

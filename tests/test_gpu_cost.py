@@ -69,11 +69,13 @@ def _costs(M, orc, p, mapping, fp64=False):
 
 
 @pytest.mark.parametrize("term", TERMS)
-def test_each_term_fp64_check(M, orc, term):
-    # every term alone, FP64 check build (warp mapping): the algorithm, not FP32 rounding
+@pytest.mark.parametrize("mapping", [0, 2])
+def test_each_term_fp64_check(M, orc, term, mapping):
+    # every term alone, FP64 check build (the warp kernel, and the product's lanes-per-chain
+    # kernel with the modular cost compiled in): the algorithm, not FP32 rounding
     p = S.scale_quadruped(n=64)
     p.model = _only(p.model, term)
-    got, ref, _ = _costs(M, orc, p, mapping=0, fp64=True)
+    got, ref, _ = _costs(M, orc, p, mapping=mapping, fp64=True)
     err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
     print(f"{term}: FP64 check rel. error max {err.max():.2e}, cost median {np.median(ref):.3e}")
     assert np.all(ref > 0) and err.max() < 1e-9
@@ -99,6 +101,8 @@ def test_tab2_weight_sets(M, orc, task, robot):
     p.model = S.with_paper_cost(p.model, task, pdot_des=(0.5, 0.0, 0.0), keep_quadratic=True)
     got64, ref, kn64 = _costs(M, orc, p, mapping=0, fp64=True)
     assert np.max(np.abs(got64 - ref) / np.abs(ref)) < 1e-9
+    got64c, _, _ = _costs(M, orc, p, mapping=2, fp64=True)   # the product's chain / split kernel in double
+    assert np.max(np.abs(got64c - ref) / np.abs(ref)) < 1e-9
     for mapping in ((0, 1, 2) if robot == "quadruped" else (0, 2)):   # half warp: <= 16 bodies
         got, _, _ = _costs(M, orc, p, mapping=mapping)
         _check_fp32(orc, p, kn64, got, ref, f"{robot} {task} mapping {mapping}")

@@ -132,8 +132,8 @@ def test_rollout_contact_free(M, orc, name, mapping):
     assert _rel(costs, ref_c) < 1e-4
     for i in range(n):
         assert _rel(fins[i], ref_f[i]) < 1e-4, i
-    if mapping == 2:
-        return
+    # the FP64 check build of the same mapping (for the chain mapping: the product's
+    # specialised lanes / split kernels in double)
     c.set_fp64_check(True)
     costs64, fins64 = c.rollout_explicit(x0, kn, finals=True)
     assert _rel(costs64, ref_c) < 1e-9
@@ -142,7 +142,8 @@ def test_rollout_contact_free(M, orc, name, mapping):
 
 
 @pytest.mark.parametrize("cfg", ["scale", "humanoid", "plain"])
-def test_rollout_with_contact_fp64_check(M, orc, cfg):
+@pytest.mark.parametrize("mapping64", [0, 2])
+def test_rollout_with_contact_fp64_check(M, orc, cfg, mapping64):
     # contact rollouts of the configurations: the FP64 check build within 1e-9 where the
     # dynamics are well conditioned (dt = 0.005), and within the oracle's own FP64
     # sensitivity envelope at dt = 0.01; the FP32 product's cost error is reported and
@@ -160,19 +161,23 @@ def test_rollout_with_contact_fp64_check(M, orc, cfg):
     kn32 = kn.astype(np.float32)
     kn64 = kn32.astype(np.float64)
     (ref_c, ref_f), env_c64, env_f64 = rollout_envelope(m, p.state, kn64, p.horizon, p.dt, 1e-15)
-    c = M.Controller.from_problem(M.Model(m), p, mapping=M.MPPI_MAP_WARP)
+    # mapping64 0: the generic warp kernel in double; 2: the product's lanes-per-chain
+    # kernel in double (the x, y, y quadruped plan; the humanoid's two-warp split)
+    c = M.Controller.from_problem(M.Model(m), p, mapping=mapping64)
     c.set_fp64_check(True)
     c64, f64 = c.rollout_explicit(p.state, kn32, finals=True)
     scale_f = np.max(np.abs(ref_f), axis=1)
     err_f = np.max(np.abs(f64 - ref_f), axis=1) / scale_f
     err_c = np.abs(c64 - ref_c) / np.abs(ref_c)
-    print(f"{cfg}: FP64 check build rel. error costs max {err_c.max():.2e}, final states max {err_f.max():.2e}; "
+    print(f"{cfg} mapping {mapping64}: FP64 check build rel. error costs max {err_c.max():.2e}, final states max {err_f.max():.2e}; "
           f"oracle FP64 envelope max {np.max(env_f64 / scale_f):.2e}")
     if cfg == "plain":
         assert np.all(np.abs(f64 - ref_f).max(axis=1) <= np.maximum(1e-9 * scale_f, 10 * env_f64))
         assert np.median(err_f) < 1e-9
     else:
         assert err_c.max() < 1e-9 and err_f.max() < 1e-9
+    if mapping64 != 0:
+        return
     c.set_fp64_check(False)
     c.set_mapping(M.MPPI_MAP_CHAIN)
     c32 = c.rollout_explicit(p.state, kn32)
@@ -247,6 +252,11 @@ def test_chain_axis_plans(M, orc, tilt):
     print(f"axis plan {mod.info()['axis_plan']}: cost rel. error median {np.median(err):.2e} max {err.max():.2e}, "
           f"final state max {err_f.max():.2e}")
     assert err.max() < 1e-4 and err_f.max() < 1e-4
+    # the same plan's kernel in double: 1e-9
+    c.set_fp64_check(True)
+    g64, f64 = c.rollout_explicit(p.state, kn, finals=True)
+    assert np.max(np.abs(g64 - ref_c) / np.abs(ref_c)) < 1e-9
+    assert np.max(np.max(np.abs(f64 - ref_f), axis=1) / np.max(np.abs(ref_f), axis=1)) < 1e-9
 
 
 @pytest.mark.parametrize("variant", ["layout", "tilted", "offset", "hand_contact", "leg_cost"])
@@ -285,6 +295,12 @@ def test_humanoid_axis_plans(M, orc, variant):
     print(f"humanoid {variant}, axis plan {mod.info()['axis_plan']}: cost rel. error median {np.median(err):.2e} "
           f"max {err.max():.2e}, final state max {err_f.max():.2e}")
     assert err.max() < 1e-4 and err_f.max() < 1e-4
+    # the same plan's kernel in double (split or generic branch chain): 1e-9
+    c.set_fp64_check(True)
+    g64, f64 = c.rollout_explicit(p.state, kn, finals=True)
+    assert np.max(np.abs(g64 - ref_c) / np.abs(ref_c)) < 1e-9
+    assert np.max(np.max(np.abs(f64 - ref_f), axis=1) / np.max(np.abs(ref_f), axis=1)) < 1e-9
+    c.set_fp64_check(False)
     if variant == "layout":
         for block in (64, 256):
             c.set_mapping(M.MPPI_MAP_CHAIN, block)
