@@ -20,15 +20,27 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_COUNT_SRC = os.path.join(_HERE, "count.cc")
+_COUNT_LIB = os.path.join(_HERE, "liboracle_count.so")
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (gcc -O3, no fast-math, portable flags)."""
+    """Compile the oracle (gcc -O3, portable flags, no fast-math and no contraction of a
+    multiply and an add into a fused one, which GCC does by default where the target has
+    it: the oracle computes each operation of its source rounded separately, on x86 and Arm
+    alike) and its operation-counting build (g++, the same source with a counting scalar
+    type)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm", "-lpthread"]
+        cmd = ["gcc", "-O3", "-ffp-contract=off", "-std=gnu11", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm",
+               "-lpthread"]
+        subprocess.check_call(cmd)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_COUNT_SRC))
+    if force or not os.path.exists(_COUNT_LIB) or os.path.getmtime(_COUNT_LIB) < newest:
+        cmd = ["g++", "-O1", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared", "-o", _COUNT_LIB, _COUNT_SRC,
+               "-lm", "-lpthread"]
         subprocess.check_call(cmd)
     return _LIB
 
@@ -384,6 +396,41 @@ def solve_problem(p, iter_base=0, nthreads=None, keep=False, **kw):
     """Alg. 1 on a synth.Problem."""
     return solve(p.model, p.n, p.nk, p.horizon, p.iters, p.dt, p.lam, p.sigma, p.state, p.nominal,
                  seed=p.seed, iter_base=iter_base, inst=p.instance, nthreads=nthreads, keep=keep, **kw)
+
+
+# ------------------------------------------------------------------------------------
+# Operation counts of the algorithm as the oracle specifies it (count.cc)
+# ------------------------------------------------------------------------------------
+PHASES = ("spline", "pd", "pass1", "contact", "bias", "pass2", "solve", "pass3", "cost", "integrate", "other")
+OP_KINDS = ("add", "mul", "div", "sqrt", "func", "cmp", "trivial_add", "trivial_mul", "trivial_div")
+_count_lib = None
+
+
+def _count():
+    global _count_lib
+    if _count_lib is None:
+        build()
+        L = C.CDLL(_COUNT_LIB)
+        L.orc_count_rollout.argtypes = [C.POINTER(_Model), _dp, _dp, C.c_int, C.c_int, C.c_double, C.c_int, _dp]
+        L.orc_count_rollout.restype = C.c_double
+        L.orc_count_dims.argtypes = [_ip]
+        dims = np.zeros(2, np.int32)
+        L.orc_count_dims(dims.ctypes.data_as(_ip))
+        assert (int(dims[0]), int(dims[1])) == (len(PHASES), len(OP_KINDS))
+        _count_lib = L
+    return _count_lib
+
+
+def count_rollout(m, x0, knots, H, dt, spline=0):
+    """Operations of one rollout of one sample, by phase and kind: (cost, counts [phase][kind])
+    with counts a numpy array indexed by PHASES and OP_KINDS. Flops = add + mul + div +
+    sqrt + func (a multiply-add is a mul and an add); the trivial_* columns count the
+    operations among those whose result a structural 0 or +-1 operand fixes."""
+    om = _om(m)
+    kn = _d(knots)
+    out = np.zeros((len(PHASES), len(OP_KINDS)))
+    S = _count().orc_count_rollout(om.ref, _ptr(_d(x0)), _ptr(kn), kn.shape[0], H, dt, spline, _ptr(out))
+    return S, out
 
 
 if __name__ == "__main__":

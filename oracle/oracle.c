@@ -5,7 +5,7 @@
  * CPU-baseline leg load this file's library. The product (the CUDA library) shares no
  * code with it and never calls it.
  *
- * Plain, slow, obviously correct: every quantity in double precision, 6x6 spatial
+ * Plain, slow, obviously correct: every quantity in real precision, 6x6 spatial
  * matrices written out densely, no blocking or fusion beyond what the method states.
  * Sections follow the paper ("Reference-Free Sampling-Based Model Predictive
  * Control", arXiv 2511.19204):
@@ -43,30 +43,41 @@
 #define ORC_MAXB 64
 #define ORC_MAXNV (6 + ORC_MAXB)
 
+/* The scalar of all arithmetic: double. The operation-counting build (count.cc, test
+ * infrastructure for the work per rollout step) compiles this file as C++ with `real` a
+ * double-sized type that counts the operations it performs, and ORC_PHASE naming the
+ * algorithm's phase they belong to; here ORC_PHASE does nothing. */
+#ifndef ORC_COUNTING
+typedef double real;
+#define ORC_PHASE(p) ((void)0)
+#endif
+enum { PH_SPLINE, PH_PD, PH_PASS1, PH_CONTACT, PH_BIAS, PH_PASS2, PH_SOLVE, PH_PASS3, PH_COST, PH_INTEGRATE,
+       PH_OTHER, PH_COUNT };
+
 typedef struct {
     int32_t nb, nc, fixed_base, cost_body;
     const int32_t* parent;     /* [nb] */
-    const double* axis;        /* [nb][3] */
-    const double* jpos;        /* [nb][3] */
-    const double* mass;        /* [nb] */
-    const double* com;         /* [nb][3] */
-    const double* inertia;     /* [nb][6] Ixx Iyy Izz Ixy Ixz Iyz about the com */
-    const double* armature;    /* [nb] */
-    const double* q_min;       /* [nb-1] */
-    const double* q_max;       /* [nb-1] */
-    const double* kp;          /* [nb-1] */
-    const double* kd;          /* [nb-1] */
-    const double* tau_max;     /* [nb-1] */
+    const real* axis;        /* [nb][3] */
+    const real* jpos;        /* [nb][3] */
+    const real* mass;        /* [nb] */
+    const real* com;         /* [nb][3] */
+    const real* inertia;     /* [nb][6] Ixx Iyy Izz Ixy Ixz Iyz about the com */
+    const real* armature;    /* [nb] */
+    const real* q_min;       /* [nb-1] */
+    const real* q_max;       /* [nb-1] */
+    const real* kp;          /* [nb-1] */
+    const real* kd;          /* [nb-1] */
+    const real* tau_max;     /* [nb-1] */
     const int32_t* contact_body; /* [nc] */
-    const double* contact_pos;   /* [nc][3] */
-    double contact_k, contact_c, mu, eps_f, gravity;
-    double z_des, vx_des, w_z, w_vx, w_tilt, w_tau;
+    const real* contact_pos;   /* [nc][3] */
+    real contact_k, contact_c, mu, eps_f, gravity;
+    real z_des, vx_des, w_z, w_vx, w_tilt, w_tau;
     /* modular cost of Sec. IV-A */
-    double w_h, w_orient, w_q, w_cvel, w_cforce, w_term;
-    double quat_des[4];        /* (w, x, y, z), unit */
-    double f0[3];
-    double pdot_des[3];
-    const double* q0;          /* [nb-1] or NULL (zeros) */
+    real w_h, w_orient, w_q, w_cvel, w_cforce, w_term;
+    real quat_des[4];        /* (w, x, y, z), unit */
+    real f0[3];
+    real pdot_des[3];
+    const real* q0;          /* [nb-1] or NULL (zeros) */
 } orc_model;
 
 /* ------------------------------------------------------------------------------------ */
@@ -98,22 +109,22 @@ void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out
  * exp(-(I - i)/(beta1 I) - (K - k)/(beta2 K)) for iterations i = I..1 and knots
  * k = 0..K-1, used as the standard-deviation factor sigma[it][k] with it = I - i (so the
  * first iteration, i = I, is row 0), times `scale`. out [iters][knots]. */
-void orc_noise_schedule(int iters, int knots, double beta1, double beta2, double scale, double* out) {
+void orc_noise_schedule(int iters, int knots, real beta1, real beta2, real scale, real* out) {
     for (int it = 0; it < iters; ++it) {
         int i = iters - it;
         for (int k = 0; k < knots; ++k)
             out[it * knots + k] =
-                scale * exp(-(double)(iters - i) / (beta1 * iters) - (double)(knots - k) / (beta2 * knots));
+                scale * exp(-(real)(iters - i) / (beta1 * iters) - (real)(knots - k) / (beta2 * knots));
     }
 }
 
 /* Box-Muller on two 32-bit words: u1 in (0,1], u2 in [0,1). */
-static void box_muller(uint32_t wa, uint32_t wb, double* ea, double* eb) {
-    const double two_m24 = 1.0 / 16777216.0;
-    double u1 = ((double)(wa >> 8) + 1.0) * two_m24;
-    double u2 = (double)(wb >> 8) * two_m24;
-    double r = sqrt(-2.0 * log(u1));
-    double ang = 2.0 * M_PI * u2;
+static void box_muller(uint32_t wa, uint32_t wb, real* ea, real* eb) {
+    const real two_m24 = 1.0 / 16777216.0;
+    real u1 = ((real)(wa >> 8) + 1.0) * two_m24;
+    real u2 = (real)(wb >> 8) * two_m24;
+    real r = sqrt(-2.0 * log(u1));
+    real ang = 2.0 * M_PI * u2;
     *ea = r * cos(ang);
     *eb = r * sin(ang);
 }
@@ -121,34 +132,34 @@ static void box_muller(uint32_t wa, uint32_t wb, double* ea, double* eb) {
 /* Standard normal eps for one element e of sample n (n >= 1):
  * counter = (e/4, n, iteration counter, instance), key = (seed lo, seed hi);
  * element pairs (2m, 2m+1) share one Box-Muller draw from words (e%4 & ~1, +1). */
-double orc_normal(uint64_t seed, uint32_t iter_ctr, uint32_t inst, uint32_t n, uint32_t e) {
+real orc_normal(uint64_t seed, uint32_t iter_ctr, uint32_t inst, uint32_t n, uint32_t e) {
     uint32_t ctr[4] = {e / 4u, n, iter_ctr, inst};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox(ctr, key, w);
     uint32_t j = (e % 4u) & ~1u;
-    double ea, eb;
+    real ea, eb;
     box_muller(w[j], w[j + 1], &ea, &eb);
     return (e & 1u) ? eb : ea;
 }
 
 /* Knot spacing of nk uniform knots over H steps of dt, both endpoints included. */
-static double knot_dt(int nk, int H, double dt) { return (double)H * dt / (double)(nk - 1); }
+static real knot_dt(int nk, int H, real dt) { return (real)H * dt / (real)(nk - 1); }
 
 /* Sec. III-A Eq. (vel-clamp): clip theta^q into the limits, then bound |theta^v| by the
  * distance to the nearest limit over half a knot interval. Only joints with a finite
  * limit are clamped. knots: [nk][2][nu]. */
-void orc_clamp(int nu, int nk, double dtk, const double* qmin, const double* qmax, double* kn) {
+void orc_clamp(int nu, int nk, real dtk, const real* qmin, const real* qmax, real* kn) {
     for (int k = 0; k < nk; ++k)
         for (int j = 0; j < nu; ++j) {
-            double lo = qmin[j], hi = qmax[j];
+            real lo = qmin[j], hi = qmax[j];
             if (!isfinite(lo) && !isfinite(hi)) continue;
-            double* q = &kn[(k * 2 + 0) * nu + j];
-            double* v = &kn[(k * 2 + 1) * nu + j];
+            real* q = &kn[(k * 2 + 0) * nu + j];
+            real* v = &kn[(k * 2 + 1) * nu + j];
             if (*q < lo) *q = lo;
             if (*q > hi) *q = hi;
-            double room = fmin(hi - *q, *q - lo);
-            double vmax = room / (dtk / 2.0);
+            real room = fmin(hi - *q, *q - lo);
+            real vmax = room / (dtk / 2.0);
             if (*v > vmax) *v = vmax;
             if (*v < -vmax) *v = -vmax;
         }
@@ -158,19 +169,19 @@ void orc_clamp(int nu, int nk, double dtk, const double* qmin, const double* qma
  * is the nominal itself; then the clamp (when the model has finite limits).
  * nominal [E], sigma_row [nk], out [N][E], E = nk*2*nu.
  * scale_v <= 0 selects the default 1/knot-spacing. */
-void orc_sample_knots(int nu, int nk, int N, int H, double dt, const double* nominal,
-                      const double* sigma_row, double scale_q, double scale_v, uint64_t seed,
-                      uint32_t iter_ctr, uint32_t inst, const double* qmin, const double* qmax,
-                      double* out) {
+void orc_sample_knots(int nu, int nk, int N, int H, real dt, const real* nominal,
+                      const real* sigma_row, real scale_q, real scale_v, uint64_t seed,
+                      uint32_t iter_ctr, uint32_t inst, const real* qmin, const real* qmax,
+                      real* out) {
     const int E = nk * 2 * nu;
-    const double dtk = knot_dt(nk, H, dt);
+    const real dtk = knot_dt(nk, H, dt);
     if (scale_v <= 0.0) scale_v = 1.0 / dtk;
     for (int n = 0; n < N; ++n) {
-        double* kn = out + (size_t)n * E;
+        real* kn = out + (size_t)n * E;
         for (int e = 0; e < E; ++e) {
             int k = e / (2 * nu);
             int p = (e / nu) % 2;
-            double eps = (n == 0) ? 0.0 : orc_normal(seed, iter_ctr, inst, (uint32_t)n, (uint32_t)e);
+            real eps = (n == 0) ? 0.0 : orc_normal(seed, iter_ctr, inst, (uint32_t)n, (uint32_t)e);
             kn[e] = nominal[e] + sigma_row[k] * (p == 0 ? scale_q : scale_v) * eps;
         }
         if (qmin && qmax) orc_clamp(nu, nk, dtk, qmin, qmax, kn);
@@ -182,22 +193,22 @@ void orc_sample_knots(int nu, int nk, int N, int H, double dt, const double* nom
 /* ------------------------------------------------------------------------------------ */
 /* Segment and local time for step h: r = h*(nk-1); k = floor(r/H) (<= nk-2);
  * s = (r - k*H)/H = (t_h - t_k)/knot spacing, t_h = h*dt. */
-void orc_segment(int h, int H, int nk, int* k_out, double* s_out) {
+void orc_segment(int h, int H, int nk, int* k_out, real* s_out) {
     long r = (long)h * (long)(nk - 1);
     long k = r / H;
     if (k > nk - 2) k = nk - 2;
     *k_out = (int)k;
-    *s_out = (double)(r - k * (long)H) / (double)H;
+    *s_out = (real)(r - k * (long)H) / (real)H;
 }
 
 /* q(s) and dq/dt on one segment with knot spacing dtk. */
-void orc_hermite(double s, double dtk, double q0, double v0, double q1, double v1,
-                 double* q, double* qdot) {
-    double s2 = s * s, s3 = s2 * s;
-    double h00 = 2 * s3 - 3 * s2 + 1, h10 = s3 - 2 * s2 + s;
-    double h01 = -2 * s3 + 3 * s2, h11 = s3 - s2;
-    double d00 = 6 * s2 - 6 * s, d10 = 3 * s2 - 4 * s + 1;
-    double d01 = -6 * s2 + 6 * s, d11 = 3 * s2 - 2 * s;
+void orc_hermite(real s, real dtk, real q0, real v0, real q1, real v1,
+                 real* q, real* qdot) {
+    real s2 = s * s, s3 = s2 * s;
+    real h00 = 2 * s3 - 3 * s2 + 1, h10 = s3 - 2 * s2 + s;
+    real h01 = -2 * s3 + 3 * s2, h11 = s3 - s2;
+    real d00 = 6 * s2 - 6 * s, d10 = 3 * s2 - 4 * s + 1;
+    real d01 = -6 * s2 + 6 * s, d11 = 3 * s2 - 2 * s;
     *q = h00 * q0 + h10 * dtk * v0 + h01 * q1 + h11 * dtk * v1;
     *qdot = (d00 * q0 + d01 * q1) / dtk + d10 * v0 + d11 * v1;
 }
@@ -205,8 +216,8 @@ void orc_hermite(double s, double dtk, double q0, double v0, double q1, double v
 /* ------------------------------------------------------------------------------------ */
 /* Small dense linear algebra                                                            */
 /* ------------------------------------------------------------------------------------ */
-typedef double m3[3][3];
-typedef double m6[6][6];
+typedef real m3[3][3];
+typedef real m6[6][6];
 
 static void m3_mul(const m3 a, const m3 b, m3 c) {
     m3 t;
@@ -217,36 +228,36 @@ static void m3_mul(const m3 a, const m3 b, m3 c) {
         }
     memcpy(c, t, sizeof(m3));
 }
-static void m3_vec(const m3 a, const double* x, double* y) {
-    double t[3];
+static void m3_vec(const m3 a, const real* x, real* y) {
+    real t[3];
     for (int i = 0; i < 3; ++i) t[i] = a[i][0] * x[0] + a[i][1] * x[1] + a[i][2] * x[2];
     memcpy(y, t, sizeof t);
 }
-static void m3_tvec(const m3 a, const double* x, double* y) {
-    double t[3];
+static void m3_tvec(const m3 a, const real* x, real* y) {
+    real t[3];
     for (int i = 0; i < 3; ++i) t[i] = a[0][i] * x[0] + a[1][i] * x[1] + a[2][i] * x[2];
     memcpy(y, t, sizeof t);
 }
-static void cross3(const double* a, const double* b, double* c) {
-    double t[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+static void cross3(const real* a, const real* b, real* c) {
+    real t[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
     memcpy(c, t, sizeof t);
 }
-static void skew(const double* a, m3 s) {
+static void skew(const real* a, m3 s) {
     s[0][0] = 0; s[0][1] = -a[2]; s[0][2] = a[1];
     s[1][0] = a[2]; s[1][1] = 0; s[1][2] = -a[0];
     s[2][0] = -a[1]; s[2][1] = a[0]; s[2][2] = 0;
 }
 /* Rodrigues: rotation about unit axis a by angle t (child -> parent coordinates). */
-static void axis_angle(const double* a, double t, m3 R) {
+static void axis_angle(const real* a, real t, m3 R) {
     m3 K, K2;
     skew(a, K);
     m3_mul(K, K, K2);
-    double s = sin(t), c = cos(t);
+    real s = sin(t), c = cos(t);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) R[i][j] = (i == j ? 1.0 : 0.0) + s * K[i][j] + (1 - c) * K2[i][j];
 }
-static void quat_to_R(const double* q, m3 R) {
-    double w = q[0], x = q[1], y = q[2], z = q[3];
+static void quat_to_R(const real* q, m3 R) {
+    real w = q[0], x = q[1], y = q[2], z = q[3];
     R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
     R[1][0] = 2 * (x * y + w * z); R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
     R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
@@ -256,7 +267,7 @@ static void m6_mul(const m6 a, const m6 b, m6 c) {
     m6 t;
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) {
-            double s = 0;
+            real s = 0;
             for (int k = 0; k < 6; ++k) s += a[i][k] * b[k][j];
             t[i][j] = s;
         }
@@ -266,36 +277,36 @@ static void m6_tmul(const m6 a, const m6 b, m6 c) { /* c = a^T b */
     m6 t;
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) {
-            double s = 0;
+            real s = 0;
             for (int k = 0; k < 6; ++k) s += a[k][i] * b[k][j];
             t[i][j] = s;
         }
     memcpy(c, t, sizeof(m6));
 }
-static void m6_vec(const m6 a, const double* x, double* y) {
-    double t[6];
+static void m6_vec(const m6 a, const real* x, real* y) {
+    real t[6];
     for (int i = 0; i < 6; ++i) {
-        double s = 0;
+        real s = 0;
         for (int k = 0; k < 6; ++k) s += a[i][k] * x[k];
         t[i] = s;
     }
     memcpy(y, t, sizeof t);
 }
-static void m6_tvec(const m6 a, const double* x, double* y) {
-    double t[6];
+static void m6_tvec(const m6 a, const real* x, real* y) {
+    real t[6];
     for (int i = 0; i < 6; ++i) {
-        double s = 0;
+        real s = 0;
         for (int k = 0; k < 6; ++k) s += a[k][i] * x[k];
         t[i] = s;
     }
     memcpy(y, t, sizeof t);
 }
 /* Solve A x = b for a symmetric positive definite n x n matrix (Cholesky). */
-static int spd_solve(int n, const double* A, const double* b, double* x) {
-    double L[ORC_MAXNV * ORC_MAXNV];
+static int spd_solve(int n, const real* A, const real* b, real* x) {
+    real L[ORC_MAXNV * ORC_MAXNV];
     for (int i = 0; i < n; ++i)
         for (int j = 0; j <= i; ++j) {
-            double s = A[i * n + j];
+            real s = A[i * n + j];
             for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
             if (i == j) {
                 if (!(s > 0)) return -1;
@@ -304,14 +315,14 @@ static int spd_solve(int n, const double* A, const double* b, double* x) {
                 L[i * n + j] = s / L[j * n + j];
             }
         }
-    double y[ORC_MAXNV];
+    real y[ORC_MAXNV];
     for (int i = 0; i < n; ++i) {
-        double s = b[i];
+        real s = b[i];
         for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
         y[i] = s / L[i * n + i];
     }
     for (int i = n - 1; i >= 0; --i) {
-        double s = y[i];
+        real s = y[i];
         for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
         x[i] = s / L[i * n + i];
     }
@@ -323,7 +334,7 @@ static int spd_solve(int n, const double* A, const double* b, double* x) {
 /* ------------------------------------------------------------------------------------ */
 /* Plucker transform parent -> child: X = [E 0; -E [r]x  E], E = rotation parent->child
  * coordinates, r = child origin in parent coordinates. */
-static void plucker(const m3 E, const double* r, m6 X) {
+static void plucker(const m3 E, const real* r, m6 X) {
     m3 S, ES;
     skew(r, S);
     m3_mul(E, S, ES);
@@ -337,15 +348,15 @@ static void plucker(const m3 E, const double* r, m6 X) {
 }
 /* Rigid-body spatial inertia about the body origin. */
 static void body_inertia(const orc_model* m, int b, m6 I) {
-    const double* c = &m->com[3 * b];
-    const double* ic = &m->inertia[6 * b];
-    double mass = m->mass[b];
+    const real* c = &m->com[3 * b];
+    const real* ic = &m->inertia[6 * b];
+    real mass = m->mass[b];
     m3 Ic = {{ic[0], ic[3], ic[4]}, {ic[3], ic[1], ic[5]}, {ic[4], ic[5], ic[2]}};
     m3 C, CCt;
     skew(c, C);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0;
+            real s = 0;
             for (int k = 0; k < 3; ++k) s += C[i][k] * C[j][k]; /* C C^T */
             CCt[i][j] = s;
         }
@@ -358,16 +369,16 @@ static void body_inertia(const orc_model* m, int b, m6 I) {
             I[3 + i][3 + j] = (i == j) ? mass : 0.0;
         }
 }
-static void crm(const double* a, const double* b, double* c) { /* motion x motion */
-    double t[6], u[3];
+static void crm(const real* a, const real* b, real* c) { /* motion x motion */
+    real t[6], u[3];
     cross3(a, b, t);
     cross3(a, b + 3, t + 3);
     cross3(a + 3, b, u);
     t[3] += u[0]; t[4] += u[1]; t[5] += u[2];
     memcpy(c, t, sizeof t);
 }
-static void crf(const double* a, const double* f, double* c) { /* motion x* force */
-    double t[6], u[3];
+static void crf(const real* a, const real* f, real* c) { /* motion x* force */
+    real t[6], u[3];
     cross3(a, f, t);
     cross3(a + 3, f + 3, u);
     t[0] += u[0]; t[1] += u[1]; t[2] += u[2];
@@ -381,21 +392,22 @@ static void crf(const double* a, const double* f, double* c) { /* motion x* forc
 typedef struct {
     m6 X[ORC_MAXB];          /* parent -> body transform */
     m3 R[ORC_MAXB];          /* body -> world rotation */
-    double p[ORC_MAXB][3];   /* body origin, world */
-    double v[ORC_MAXB][6];   /* spatial velocity, body coordinates */
-    double fext[ORC_MAXB][6];/* external spatial force, body coordinates */
+    real p[ORC_MAXB][3];   /* body origin, world */
+    real v[ORC_MAXB][6];   /* spatial velocity, body coordinates */
+    real fext[ORC_MAXB][6];/* external spatial force, body coordinates */
 } orc_kin;
 
-static void kinematics(const orc_model* m, const double* x, orc_kin* K) {
+static void kinematics(const orc_model* m, const real* x, orc_kin* K) {
     const int nb = m->nb, nj = nb - 1, nq = 7 + nj;
-    const double* q = x + 7;
-    const double* vb = x + nq;       /* v_lin(3), omega(3), body frame */
-    const double* qd = x + nq + 6;
+    const real* q = x + 7;
+    const real* vb = x + nq;       /* v_lin(3), omega(3), body frame */
+    const real* qd = x + nq + 6;
+    ORC_PHASE(PH_PASS1);
     quat_to_R(x + 3, K->R[0]);
-    memcpy(K->p[0], x, 3 * sizeof(double));
+    memcpy(K->p[0], x, 3 * sizeof(real));
     K->v[0][0] = vb[3]; K->v[0][1] = vb[4]; K->v[0][2] = vb[5];
     K->v[0][3] = vb[0]; K->v[0][4] = vb[1]; K->v[0][5] = vb[2];
-    if (m->fixed_base) memset(K->v[0], 0, 6 * sizeof(double));
+    if (m->fixed_base) memset(K->v[0], 0, 6 * sizeof(real));
     for (int i = 1; i < nb; ++i) {
         int l = m->parent[i];
         m3 Rj, E;
@@ -404,31 +416,32 @@ static void kinematics(const orc_model* m, const double* x, orc_kin* K) {
             for (int b = 0; b < 3; ++b) E[a][b] = Rj[b][a];
         plucker(E, &m->jpos[3 * i], K->X[i]);
         m3_mul(K->R[l], Rj, K->R[i]);
-        double t[3];
+        real t[3];
         m3_vec(K->R[l], &m->jpos[3 * i], t);
         for (int a = 0; a < 3; ++a) K->p[i][a] = K->p[l][a] + t[a];
         m6_vec(K->X[i], K->v[l], K->v[i]);
         for (int a = 0; a < 3; ++a) K->v[i][a] += m->axis[3 * i + a] * qd[i - 1];
     }
-    for (int i = 0; i < nb; ++i) memset(K->fext[i], 0, 6 * sizeof(double));
+    for (int i = 0; i < nb; ++i) memset(K->fext[i], 0, 6 * sizeof(real));
+    ORC_PHASE(PH_CONTACT);
     /* soft ground contact on the plane z = 0 */
     for (int c = 0; c < m->nc; ++c) {
         int b = m->contact_body[c];
-        const double* rc = &m->contact_pos[3 * c];
-        double pw[3], vloc[3], vw[3], t[3];
+        const real* rc = &m->contact_pos[3 * c];
+        real pw[3], vloc[3], vw[3], t[3];
         m3_vec(K->R[b], rc, t);
         for (int a = 0; a < 3; ++a) pw[a] = K->p[b][a] + t[a];
         cross3(K->v[b], rc, vloc); /* w x r */
         for (int a = 0; a < 3; ++a) vloc[a] += K->v[b][3 + a];
         m3_vec(K->R[b], vloc, vw);
-        double depth = -pw[2];
+        real depth = -pw[2];
         if (depth <= 0) continue;
-        double fn = m->contact_k * depth - m->contact_c * vw[2];
+        real fn = m->contact_k * depth - m->contact_c * vw[2];
         if (fn < 0) fn = 0;
-        double vt2 = vw[0] * vw[0] + vw[1] * vw[1];
-        double scale = -m->mu * fn / sqrt(vt2 + m->eps_f * m->eps_f);
-        double F[3] = {scale * vw[0], scale * vw[1], fn};
-        double fb[3], nb3[3];
+        real vt2 = vw[0] * vw[0] + vw[1] * vw[1];
+        real scale = -m->mu * fn / sqrt(vt2 + m->eps_f * m->eps_f);
+        real F[3] = {scale * vw[0], scale * vw[1], fn};
+        real fb[3], nb3[3];
         m3_tvec(K->R[b], F, fb);
         cross3(rc, fb, nb3);
         for (int a = 0; a < 3; ++a) {
@@ -443,16 +456,17 @@ static void kinematics(const orc_model* m, const double* x, orc_kin* K) {
 /* acc[nv] = (base spatial acceleration (w_dot, v_dot) in body coordinates, qdd).       */
 /* For a fixed base the base part is zero.                                               */
 /* ------------------------------------------------------------------------------------ */
-static int aba(const orc_model* m, const double* x, const double* tau, orc_kin* K, double* acc) {
+static int aba(const orc_model* m, const real* x, const real* tau, orc_kin* K, real* acc) {
     const int nb = m->nb, nj = nb - 1, nq = 7 + nj;
-    const double* qd = x + nq + 6;
+    const real* qd = x + nq + 6;
     static __thread m6 IA[ORC_MAXB];
-    double pA[ORC_MAXB][6], c[ORC_MAXB][6], U[ORC_MAXB][6], D[ORC_MAXB], u[ORC_MAXB];
-    double a[ORC_MAXB][6];
+    real pA[ORC_MAXB][6], c[ORC_MAXB][6], U[ORC_MAXB][6], D[ORC_MAXB], u[ORC_MAXB];
+    real a[ORC_MAXB][6];
     kinematics(m, x, K);
+    ORC_PHASE(PH_BIAS);
     for (int i = 0; i < nb; ++i) {
         m6 I;
-        double Iv[6];
+        real Iv[6];
         body_inertia(m, i, I);
         memcpy(IA[i], I, sizeof(m6));
         m6_vec(I, K->v[i], Iv);
@@ -460,18 +474,19 @@ static int aba(const orc_model* m, const double* x, const double* tau, orc_kin* 
         for (int k = 0; k < 6; ++k) pA[i][k] -= K->fext[i][k];
         memset(c[i], 0, sizeof c[i]);
         if (i > 0) {
-            double Sq[6] = {0};
+            real Sq[6] = {0};
             for (int k = 0; k < 3; ++k) Sq[k] = m->axis[3 * i + k] * qd[i - 1];
             crm(K->v[i], Sq, c[i]);
         }
     }
+    ORC_PHASE(PH_PASS2);
     for (int i = nb - 1; i >= 1; --i) {
-        const double* S = &m->axis[3 * i]; /* S = (axis, 0) */
+        const real* S = &m->axis[3 * i]; /* S = (axis, 0) */
         for (int k = 0; k < 6; ++k) U[i][k] = IA[i][k][0] * S[0] + IA[i][k][1] * S[1] + IA[i][k][2] * S[2];
         D[i] = S[0] * U[i][0] + S[1] * U[i][1] + S[2] * U[i][2] + m->armature[i];
         u[i] = tau[i - 1] - (S[0] * pA[i][0] + S[1] * pA[i][1] + S[2] * pA[i][2]);
         m6 Ia, tmp, XtIaX;
-        double pa[6], Iac[6], Xtpa[6];
+        real pa[6], Iac[6], Xtpa[6];
         for (int r = 0; r < 6; ++r)
             for (int s = 0; s < 6; ++s) Ia[r][s] = IA[i][r][s] - U[i][r] * U[i][s] / D[i];
         m6_vec(Ia, c[i], Iac);
@@ -485,24 +500,26 @@ static int aba(const orc_model* m, const double* x, const double* tau, orc_kin* 
             pA[l][r] += Xtpa[r];
         }
     }
+    ORC_PHASE(PH_SOLVE);
     /* gravity offset: a' = a - a_g, a_g = (0, R0^T g) */
-    double g_w[3] = {0, 0, -m->gravity}, g_b[3];
+    real g_w[3] = {0, 0, -m->gravity}, g_b[3];
     m3_tvec(K->R[0], g_w, g_b);
     if (m->fixed_base) {
         a[0][0] = a[0][1] = a[0][2] = 0;
         a[0][3] = -g_b[0]; a[0][4] = -g_b[1]; a[0][5] = -g_b[2];
     } else {
-        double rhs[6];
+        real rhs[6];
         for (int k = 0; k < 6; ++k) rhs[k] = -pA[0][k];
         if (spd_solve(6, &IA[0][0][0], rhs, a[0]) != 0) return -1;
     }
+    ORC_PHASE(PH_PASS3);
     for (int i = 1; i < nb; ++i) {
-        const double* S = &m->axis[3 * i];
+        const real* S = &m->axis[3 * i];
         int l = m->parent[i];
-        double ap[6];
+        real ap[6];
         m6_vec(K->X[i], a[l], ap);
         for (int k = 0; k < 6; ++k) ap[k] += c[i][k];
-        double qdd = (u[i] - (U[i][0] * ap[0] + U[i][1] * ap[1] + U[i][2] * ap[2] + U[i][3] * ap[3] +
+        real qdd = (u[i] - (U[i][0] * ap[0] + U[i][1] * ap[1] + U[i][2] * ap[2] + U[i][3] * ap[3] +
                               U[i][4] * ap[4] + U[i][5] * ap[5])) / D[i];
         for (int k = 0; k < 6; ++k) a[i][k] = ap[k];
         for (int k = 0; k < 3; ++k) a[i][k] += S[k] * qdd;
@@ -519,7 +536,7 @@ static int aba(const orc_model* m, const double* x, const double* tau, orc_kin* 
 
 /* Joint-space mass matrix by the composite-rigid-body algorithm (check only).
  * Generalised velocity = (base (w, v) body coordinates [floating only], qdot). */
-int orc_crba(const orc_model* mdl, const double* x, double* M) {
+int orc_crba(const orc_model* mdl, const real* x, real* M) {
     const int nb = mdl->nb, nj = nb - 1;
     const int off = mdl->fixed_base ? 0 : 6;
     const int n = off + nj;
@@ -535,30 +552,30 @@ int orc_crba(const orc_model* mdl, const double* x, double* M) {
         for (int r = 0; r < 6; ++r)
             for (int s = 0; s < 6; ++s) Ic[l][r][s] += XtIX[r][s];
     }
-    memset(M, 0, sizeof(double) * n * n);
+    memset(M, 0, sizeof(real) * n * n);
     if (!mdl->fixed_base)
         for (int r = 0; r < 6; ++r)
             for (int s = 0; s < 6; ++s) M[r * n + s] = Ic[0][r][s];
     for (int i = 1; i < nb; ++i) {
-        const double* S = &mdl->axis[3 * i];
-        double F[6];
+        const real* S = &mdl->axis[3 * i];
+        real F[6];
         for (int k = 0; k < 6; ++k) F[k] = Ic[i][k][0] * S[0] + Ic[i][k][1] * S[1] + Ic[i][k][2] * S[2];
         int di = off + i - 1;
         M[di * n + di] = S[0] * F[0] + S[1] * F[1] + S[2] * F[2] + mdl->armature[i];
         int j = i;
         while (mdl->parent[j] > 0) {
-            double t[6];
+            real t[6];
             m6_tvec(K.X[j], F, t);
             memcpy(F, t, sizeof t);
             j = mdl->parent[j];
-            const double* Sj = &mdl->axis[3 * j];
+            const real* Sj = &mdl->axis[3 * j];
             int dj = off + j - 1;
-            double val = Sj[0] * F[0] + Sj[1] * F[1] + Sj[2] * F[2];
+            real val = Sj[0] * F[0] + Sj[1] * F[1] + Sj[2] * F[2];
             M[di * n + dj] = val;
             M[dj * n + di] = val;
         }
         if (!mdl->fixed_base) {
-            double t[6];
+            real t[6];
             m6_tvec(K.X[j], F, t); /* j's parent is the base */
             for (int k = 0; k < 6; ++k) {
                 M[di * n + k] = t[k];
@@ -571,29 +588,29 @@ int orc_crba(const orc_model* mdl, const double* x, double* M) {
 
 /* Bias forces h(q, v) (Coriolis, gravity, minus contact forces) by the recursive
  * Newton-Euler algorithm with zero generalised acceleration (check only). */
-int orc_rnea_bias(const orc_model* mdl, const double* x, double* h) {
+int orc_rnea_bias(const orc_model* mdl, const real* x, real* h) {
     const int nb = mdl->nb;
     const int off = mdl->fixed_base ? 0 : 6;
     static __thread orc_kin K;
-    double a[ORC_MAXB][6], f[ORC_MAXB][6];
+    real a[ORC_MAXB][6], f[ORC_MAXB][6];
     const int nj = nb - 1, nq = 7 + nj;
-    const double* qd = x + nq + 6;
+    const real* qd = x + nq + 6;
     kinematics(mdl, x, &K);
-    double g_w[3] = {0, 0, -mdl->gravity}, g_b[3];
+    real g_w[3] = {0, 0, -mdl->gravity}, g_b[3];
     m3_tvec(K.R[0], g_w, g_b);
     a[0][0] = a[0][1] = a[0][2] = 0;
     a[0][3] = -g_b[0]; a[0][4] = -g_b[1]; a[0][5] = -g_b[2];
     for (int i = 0; i < nb; ++i) {
         if (i > 0) {
             int l = mdl->parent[i];
-            double Sq[6] = {0}, cc[6];
+            real Sq[6] = {0}, cc[6];
             for (int k = 0; k < 3; ++k) Sq[k] = mdl->axis[3 * i + k] * qd[i - 1];
             crm(K.v[i], Sq, cc);
             m6_vec(K.X[i], a[l], a[i]);
             for (int k = 0; k < 6; ++k) a[i][k] += cc[k];
         }
         m6 I;
-        double Ia[6], Iv[6], vxIv[6];
+        real Ia[6], Iv[6], vxIv[6];
         body_inertia(mdl, i, I);
         m6_vec(I, a[i], Ia);
         m6_vec(I, K.v[i], Iv);
@@ -601,9 +618,9 @@ int orc_rnea_bias(const orc_model* mdl, const double* x, double* h) {
         for (int k = 0; k < 6; ++k) f[i][k] = Ia[k] + vxIv[k] - K.fext[i][k];
     }
     for (int i = nb - 1; i >= 1; --i) {
-        const double* S = &mdl->axis[3 * i];
+        const real* S = &mdl->axis[3 * i];
         h[off + i - 1] = S[0] * f[i][0] + S[1] * f[i][1] + S[2] * f[i][2];
-        double t[6];
+        real t[6];
         m6_tvec(K.X[i], f[i], t);
         int l = mdl->parent[i];
         for (int k = 0; k < 6; ++k) f[l][k] += t[k];
@@ -614,31 +631,31 @@ int orc_rnea_bias(const orc_model* mdl, const double* x, double* h) {
 }
 
 /* Generalised accelerations from ABA. acc[nv]: base (w_dot, v_dot) then qdd. */
-int orc_forward_dynamics(const orc_model* m, const double* x, const double* tau, double* acc) {
+int orc_forward_dynamics(const orc_model* m, const real* x, const real* tau, real* acc) {
     static __thread orc_kin K;
     return aba(m, x, tau, &K, acc);
 }
 
 /* Contact forces in the world frame for every contact point: out [nc][3]. */
-void orc_contact_forces(const orc_model* m, const double* x, double* out) {
+void orc_contact_forces(const orc_model* m, const real* x, real* out) {
     static __thread orc_kin K;
     kinematics(m, x, &K);
     for (int c = 0; c < m->nc; ++c) {
         int b = m->contact_body[c];
-        const double* rc = &m->contact_pos[3 * c];
-        double pw[3], vloc[3], vw[3], t[3];
+        const real* rc = &m->contact_pos[3 * c];
+        real pw[3], vloc[3], vw[3], t[3];
         m3_vec(K.R[b], rc, t);
         for (int a = 0; a < 3; ++a) pw[a] = K.p[b][a] + t[a];
         cross3(K.v[b], rc, vloc);
         for (int a = 0; a < 3; ++a) vloc[a] += K.v[b][3 + a];
         m3_vec(K.R[b], vloc, vw);
-        double depth = -pw[2];
+        real depth = -pw[2];
         out[3 * c] = out[3 * c + 1] = out[3 * c + 2] = 0;
         if (depth <= 0) continue;
-        double fn = m->contact_k * depth - m->contact_c * vw[2];
+        real fn = m->contact_k * depth - m->contact_c * vw[2];
         if (fn < 0) fn = 0;
-        double vt2 = vw[0] * vw[0] + vw[1] * vw[1];
-        double scale = -m->mu * fn / sqrt(vt2 + m->eps_f * m->eps_f);
+        real vt2 = vw[0] * vw[0] + vw[1] * vw[1];
+        real scale = -m->mu * fn / sqrt(vt2 + m->eps_f * m->eps_f);
         out[3 * c] = scale * vw[0];
         out[3 * c + 1] = scale * vw[1];
         out[3 * c + 2] = fn;
@@ -646,36 +663,36 @@ void orc_contact_forces(const orc_model* m, const double* x, double* out) {
 }
 
 /* World position of every body origin and contact point: bodies [nb][3], contacts [nc][3]. */
-void orc_positions(const orc_model* m, const double* x, double* bodies, double* contacts) {
+void orc_positions(const orc_model* m, const real* x, real* bodies, real* contacts) {
     static __thread orc_kin K;
     kinematics(m, x, &K);
     for (int b = 0; b < m->nb; ++b)
         for (int a = 0; a < 3; ++a) bodies[3 * b + a] = K.p[b][a];
     for (int c = 0; c < m->nc; ++c) {
         int b = m->contact_body[c];
-        double t[3];
+        real t[3];
         m3_vec(K.R[b], &m->contact_pos[3 * c], t);
         for (int a = 0; a < 3; ++a) contacts[3 * c + a] = K.p[b][a] + t[a];
     }
 }
 
 /* Kinetic + gravitational potential energy (check only). */
-double orc_energy(const orc_model* m, const double* x) {
+real orc_energy(const orc_model* m, const real* x) {
     static __thread orc_kin K;
     kinematics(m, x, &K);
-    double e = 0;
+    real e = 0;
     for (int i = 0; i < m->nb; ++i) {
         m6 I;
-        double Iv[6];
+        real Iv[6];
         body_inertia(m, i, I);
         m6_vec(I, K.v[i], Iv);
         for (int k = 0; k < 6; ++k) e += 0.5 * K.v[i][k] * Iv[k];
-        double cw[3];
+        real cw[3];
         m3_vec(K.R[i], &m->com[3 * i], cw);
         e += m->mass[i] * m->gravity * (K.p[i][2] + cw[2]);
     }
     for (int i = 1; i < m->nb; ++i) {
-        double qd = x[7 + m->nb - 1 + 6 + i - 1];
+        real qd = x[7 + m->nb - 1 + 6 + i - 1];
         e += 0.5 * m->armature[i] * qd * qd;
     }
     return e;
@@ -685,11 +702,11 @@ double orc_energy(const orc_model* m, const double* x) {
 /* PD tracking, running cost, semi-implicit Euler                                       */
 /* ------------------------------------------------------------------------------------ */
 /* Sec. III-C Eq. (pd-controller), clipped to +-tau_max. */
-static void pd_torque(const orc_model* m, const double* x, const double* qref, const double* vref,
-                      double* tau) {
+static void pd_torque(const orc_model* m, const real* x, const real* qref, const real* vref,
+                      real* tau) {
     const int nj = m->nb - 1, nq = 7 + nj;
     for (int j = 0; j < nj; ++j) {
-        double t = m->kp[j] * (qref[j] - x[7 + j]) + m->kd[j] * (vref[j] - x[nq + 6 + j]);
+        real t = m->kp[j] * (qref[j] - x[7 + j]) + m->kd[j] * (vref[j] - x[nq + 6 + j]);
         if (t > m->tau_max[j]) t = m->tau_max[j];
         if (t < -m->tau_max[j]) t = -m->tau_max[j];
         tau[j] = t;
@@ -699,15 +716,15 @@ static void pd_torque(const orc_model* m, const double* x, const double* qref, c
 /* Running cost c(x_h, u_h): w_z (z - z_des)^2 + w_vx (vx - vx_des)^2 + w_tilt tilt^2 +
  * w_tau |tau|^2, z and tilt of the cost body, vx = world x-velocity of the base origin,
  * tilt = angle between the cost body's z axis and the world z axis. */
-static double running_cost(const orc_model* m, const double* x, const orc_kin* K, const double* tau) {
+static real running_cost(const orc_model* m, const real* x, const orc_kin* K, const real* tau) {
     const int nj = m->nb - 1, nq = 7 + nj;
     int b = m->cost_body;
-    double z = K->p[b][2];
-    double tilt = atan2(sqrt(K->R[b][0][2] * K->R[b][0][2] + K->R[b][1][2] * K->R[b][1][2]), K->R[b][2][2]);
-    double vw[3];
+    real z = K->p[b][2];
+    real tilt = atan2(sqrt(K->R[b][0][2] * K->R[b][0][2] + K->R[b][1][2] * K->R[b][1][2]), K->R[b][2][2]);
+    real vw[3];
     m3_vec(K->R[0], x + nq, vw);
-    double vx = m->fixed_base ? 0.0 : vw[0];
-    double tt = 0;
+    real vx = m->fixed_base ? 0.0 : vw[0];
+    real tt = 0;
     for (int j = 0; j < nj; ++j) tt += tau[j] * tau[j];
     return m->w_z * (z - m->z_des) * (z - m->z_des) + m->w_vx * (vx - m->vx_des) * (vx - m->vx_des) +
            m->w_tilt * tilt * tilt + m->w_tau * tt;
@@ -720,36 +737,36 @@ static double running_cost(const orc_model* m, const double* x, const orc_kin* K
  * conj(q_base) * q_des: 2 atan2(|vector part|, |scalar part|). A contact point is in
  * contact when it penetrates the ground (depth > 0); v_c is its world velocity and f_c
  * its world contact force (zero when not in contact). */
-static double modular_cost(const orc_model* m, const double* x, const orc_kin* K) {
+static real modular_cost(const orc_model* m, const real* x, const orc_kin* K) {
     const int nj = m->nb - 1;
-    double S = 0;
+    real S = 0;
     S += m->w_h * fabs(x[2] - m->z_des);
-    const double* qb = x + 3;
-    const double* qd = m->quat_des;
+    const real* qb = x + 3;
+    const real* qd = m->quat_des;
     /* conj(qb) * qd */
-    double rw = qb[0] * qd[0] + qb[1] * qd[1] + qb[2] * qd[2] + qb[3] * qd[3];
-    double rx = qb[0] * qd[1] - qb[1] * qd[0] - qb[2] * qd[3] + qb[3] * qd[2];
-    double ry = qb[0] * qd[2] + qb[1] * qd[3] - qb[2] * qd[0] - qb[3] * qd[1];
-    double rz = qb[0] * qd[3] - qb[1] * qd[2] + qb[2] * qd[1] - qb[3] * qd[0];
-    double th = 2.0 * atan2(sqrt(rx * rx + ry * ry + rz * rz), fabs(rw));
+    real rw = qb[0] * qd[0] + qb[1] * qd[1] + qb[2] * qd[2] + qb[3] * qd[3];
+    real rx = qb[0] * qd[1] - qb[1] * qd[0] - qb[2] * qd[3] + qb[3] * qd[2];
+    real ry = qb[0] * qd[2] + qb[1] * qd[3] - qb[2] * qd[0] - qb[3] * qd[1];
+    real rz = qb[0] * qd[3] - qb[1] * qd[2] + qb[2] * qd[1] - qb[3] * qd[0];
+    real th = 2.0 * atan2(sqrt(rx * rx + ry * ry + rz * rz), fabs(rw));
     S += m->w_orient * th * th;
     for (int j = 0; j < nj; ++j) {
-        double d = x[7 + j] - (m->q0 ? m->q0[j] : 0.0);
+        real d = x[7 + j] - (m->q0 ? m->q0[j] : 0.0);
         S += m->w_q * d * d;
     }
     for (int c = 0; c < m->nc; ++c) {
         int b = m->contact_body[c];
-        const double* rc = &m->contact_pos[3 * c];
-        double pw[3], vloc[3], vw[3], t[3], F[3] = {0, 0, 0};
+        const real* rc = &m->contact_pos[3 * c];
+        real pw[3], vloc[3], vw[3], t[3], F[3] = {0, 0, 0};
         m3_vec(K->R[b], rc, t);
         for (int a = 0; a < 3; ++a) pw[a] = K->p[b][a] + t[a];
         cross3(K->v[b], rc, vloc);
         for (int a = 0; a < 3; ++a) vloc[a] += K->v[b][3 + a];
         m3_vec(K->R[b], vloc, vw);
         if (-pw[2] > 0) {
-            double fn = m->contact_k * (-pw[2]) - m->contact_c * vw[2];
+            real fn = m->contact_k * (-pw[2]) - m->contact_c * vw[2];
             if (fn < 0) fn = 0;
-            double sc = -m->mu * fn / sqrt(vw[0] * vw[0] + vw[1] * vw[1] + m->eps_f * m->eps_f);
+            real sc = -m->mu * fn / sqrt(vw[0] * vw[0] + vw[1] * vw[1] + m->eps_f * m->eps_f);
             F[0] = sc * vw[0];
             F[1] = sc * vw[1];
             F[2] = fn;
@@ -762,18 +779,18 @@ static double modular_cost(const orc_model* m, const double* x, const orc_kin* K
 
 /* Terminal cost of Sec. IV-A (Eq. terminal cost): w_term ||p_base(x_H) - p_target||_1,
  * p_target = p_base(x_0) + pdot_des H dt. */
-static double terminal_cost(const orc_model* m, const double* x0, const double* xH, int H, double dt) {
-    double S = 0;
+static real terminal_cost(const orc_model* m, const real* x0, const real* xH, int H, real dt) {
+    real S = 0;
     for (int a = 0; a < 3; ++a) S += fabs(xH[a] - (x0[a] + m->pdot_des[a] * H * dt));
     return m->w_term * S;
 }
 
 /* Semi-implicit Euler: velocities first, then positions with the new velocities; base
  * orientation by the quaternion exponential of the new body angular velocity. */
-static void integrate(const orc_model* m, double* x, const double* acc, double dt) {
+static void integrate(const orc_model* m, real* x, const real* acc, real dt) {
     const int nj = m->nb - 1, nq = 7 + nj;
-    double* vb = x + nq;
-    double* qd = x + nq + 6;
+    real* vb = x + nq;
+    real* qd = x + nq + 6;
     for (int j = 0; j < nj; ++j) {
         qd[j] += dt * acc[6 + j];
         x[7 + j] += dt * qd[j];
@@ -786,31 +803,31 @@ static void integrate(const orc_model* m, double* x, const double* acc, double d
     }
     m3 R;
     quat_to_R(x + 3, R);
-    double dp[3];
+    real dp[3];
     m3_vec(R, vb, dp);
     for (int k = 0; k < 3; ++k) x[k] += dt * dp[k];
-    const double* w = vb + 3;
-    double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-    double th = wn * dt;
-    double dq[4];
+    const real* w = vb + 3;
+    real wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    real th = wn * dt;
+    real dq[4];
     if (th < 1e-12) {
         dq[0] = 1; dq[1] = 0.5 * dt * w[0]; dq[2] = 0.5 * dt * w[1]; dq[3] = 0.5 * dt * w[2];
     } else {
-        double s = sin(0.5 * th) / wn;
+        real s = sin(0.5 * th) / wn;
         dq[0] = cos(0.5 * th); dq[1] = s * w[0]; dq[2] = s * w[1]; dq[3] = s * w[2];
     }
-    double* q = x + 3;
-    double r[4] = {q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3],
+    real* q = x + 3;
+    real r[4] = {q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3],
                    q[0] * dq[1] + q[1] * dq[0] + q[2] * dq[3] - q[3] * dq[2],
                    q[0] * dq[2] - q[1] * dq[3] + q[2] * dq[0] + q[3] * dq[1],
                    q[0] * dq[3] + q[1] * dq[2] - q[2] * dq[1] + q[3] * dq[0]};
-    double nrm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    real nrm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
     for (int k = 0; k < 4; ++k) q[k] = r[k] / nrm;
 }
 
 /* One step under a given torque: x <- step(x, tau). Returns 0 or -1 (singular). */
-int orc_step(const orc_model* m, double* x, const double* tau, double dt) {
-    double acc[ORC_MAXNV];
+int orc_step(const orc_model* m, real* x, const real* tau, real dt) {
+    real acc[ORC_MAXNV];
     static __thread orc_kin K;
     if (aba(m, x, tau, &K, acc) != 0) return -1;
     integrate(m, x, acc, dt);
@@ -828,8 +845,8 @@ int orc_step(const orc_model* m, double* x, const double* tau, double dt) {
  * the full K x K system (rows 0 and K-1: M = 0; row k: M_{k-1} + 4 M_k + M_{k+1} =
  * 6 (y_{k+1} - 2 y_k + y_{k-1}) / h^2), by dense Gaussian elimination with partial
  * pivoting. */
-static void natural_cubic_moments(int K, double h, const double* y, double* M) {
-    double A[32][33];
+static void natural_cubic_moments(int K, real h, const real* y, real* M) {
+    real A[32][33];
     for (int r = 0; r < K; ++r) {
         for (int c = 0; c <= K; ++c) A[r][c] = 0;
         if (r == 0 || r == K - 1) {
@@ -847,17 +864,17 @@ static void natural_cubic_moments(int K, double h, const double* y, double* M) {
             if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
         if (piv != c)
             for (int k = 0; k <= K; ++k) {
-                double t = A[c][k];
+                real t = A[c][k];
                 A[c][k] = A[piv][k];
                 A[piv][k] = t;
             }
         for (int r = c + 1; r < K; ++r) {
-            double f = A[r][c] / A[c][c];
+            real f = A[r][c] / A[c][c];
             for (int k = c; k <= K; ++k) A[r][k] -= f * A[c][k];
         }
     }
     for (int r = K - 1; r >= 0; --r) {
-        double acc = A[r][K];
+        real acc = A[r][K];
         for (int k = r + 1; k < K; ++k) acc -= A[r][k] * M[k];
         M[r] = acc / A[r][r];
     }
@@ -866,20 +883,20 @@ static void natural_cubic_moments(int K, double h, const double* y, double* M) {
 /* C1 quadratic spline through y with zero slope at the first node: on segment k,
  * q(s) = y_k + d_k h s + (y_{k+1} - y_k - d_k h) s^2, so d_{k+1} = q'(end) = 2 (y_{k+1} -
  * y_k) / h - d_k. */
-static void quadratic_slopes(int K, double h, const double* y, double* d) {
+static void quadratic_slopes(int K, real h, const real* y, real* d) {
     d[0] = 0;
     for (int k = 0; k + 1 < K; ++k) d[k + 1] = 2.0 * (y[k + 1] - y[k]) / h - d[k];
 }
 
 /* Value and time derivative of joint j's variant spline at segment k, local time s. */
-static void variant_eval(int spline, double h, const double* y, const double* aux, int k, double s,
-                         double* q, double* qd) {
+static void variant_eval(int spline, real h, const real* y, const real* aux, int k, real s,
+                         real* q, real* qd) {
     if (spline == ORC_SPLINE_QUADRATIC) {
-        double a2 = y[k + 1] - y[k] - aux[k] * h;
+        real a2 = y[k + 1] - y[k] - aux[k] * h;
         *q = y[k] + aux[k] * h * s + a2 * s * s;
         *qd = aux[k] + 2.0 * a2 * s / h;
     } else { /* natural cubic in moment form */
-        double u = 1.0 - s;
+        real u = 1.0 - s;
         *q = u * y[k] + s * y[k + 1] + h * h / 6.0 * ((u * u * u - u) * aux[k] + (s * s * s - s) * aux[k + 1]);
         *qd = (y[k + 1] - y[k]) / h + h / 6.0 * (-(3.0 * u * u - 1.0) * aux[k] + (3.0 * s * s - 1.0) * aux[k + 1]);
     }
@@ -887,9 +904,9 @@ static void variant_eval(int spline, double h, const double* y, const double* au
 
 /* The node derivatives of the variant spline of every joint's position knots, written
  * into the velocity knots: knots [nk][2][nu], spacing dtk. */
-void orc_spline_slopes(int spline, int nu, int nk, double dtk, double* knots) {
+void orc_spline_slopes(int spline, int nu, int nk, real dtk, real* knots) {
     if (spline == ORC_SPLINE_HERMITE) return;
-    double y[32], aux[32];
+    real y[32], aux[32];
     for (int j = 0; j < nu; ++j) {
         for (int k = 0; k < nk; ++k) y[k] = knots[(k * 2 + 0) * nu + j];
         if (spline == ORC_SPLINE_QUADRATIC) {
@@ -898,7 +915,7 @@ void orc_spline_slopes(int spline, int nu, int nk, double dtk, double* knots) {
         } else {
             natural_cubic_moments(nk, dtk, y, aux);
             for (int k = 0; k < nk; ++k) {
-                double q, qd;
+                real q, qd;
                 if (k + 1 < nk) variant_eval(spline, dtk, y, aux, k, 0.0, &q, &qd);
                 else variant_eval(spline, dtk, y, aux, nk - 2, 1.0, &q, &qd);
                 knots[(k * 2 + 1) * nu + j] = qd;
@@ -909,8 +926,8 @@ void orc_spline_slopes(int spline, int nu, int nk, double dtk, double* knots) {
 
 /* Per-joint data of the position-only variants: node positions ys [nj][nk] and the
  * moments (cubic) or node slopes (quadratic) aux [nj][nk]. */
-static void variant_prepare(int spline, int nj, int nk, double dtk, const double* knots, double* ys,
-                            double* aux) {
+static void variant_prepare(int spline, int nj, int nk, real dtk, const real* knots, real* ys,
+                            real* aux) {
     for (int j = 0; j < nj; ++j) {
         for (int k = 0; k < nk; ++k) ys[j * nk + k] = knots[(k * 2 + 0) * nj + j];
         if (spline == ORC_SPLINE_QUADRATIC) quadratic_slopes(nk, dtk, ys + j * nk, aux + j * nk);
@@ -919,10 +936,10 @@ static void variant_prepare(int spline, int nj, int nk, double dtk, const double
 }
 
 /* Setpoints (q_ref, v_ref) of step h for every joint: the spline at t_h = h dt. */
-static void step_setpoints(int spline, int nj, int nk, int H, double dtk, const double* knots,
-                           const double* ys, const double* aux, int h, double* qref, double* vref) {
+static void step_setpoints(int spline, int nj, int nk, int H, real dtk, const real* knots,
+                           const real* ys, const real* aux, int h, real* qref, real* vref) {
     int k;
-    double s;
+    real s;
     orc_segment(h, H, nk, &k, &s);
     for (int j = 0; j < nj; ++j) {
         if (spline == ORC_SPLINE_HERMITE)
@@ -935,11 +952,11 @@ static void step_setpoints(int spline, int nj, int nk, int H, double dtk, const 
 }
 
 /* The setpoints a rollout tracks: qref, vref [H][nu] for knots [nk][2][nu]. */
-void orc_setpoints(int spline, int nu, int nk, int H, double dt, const double* knots, double* qref,
-                   double* vref) {
-    const double dtk = knot_dt(nk, H, dt);
-    double* ys = (double*)malloc(sizeof(double) * (size_t)(nu > 0 ? nu : 1) * nk);
-    double* aux = (double*)malloc(sizeof(double) * (size_t)(nu > 0 ? nu : 1) * nk);
+void orc_setpoints(int spline, int nu, int nk, int H, real dt, const real* knots, real* qref,
+                   real* vref) {
+    const real dtk = knot_dt(nk, H, dt);
+    real* ys = (real*)malloc(sizeof(real) * (size_t)(nu > 0 ? nu : 1) * nk);
+    real* aux = (real*)malloc(sizeof(real) * (size_t)(nu > 0 ? nu : 1) * nk);
     if (spline != ORC_SPLINE_HERMITE) variant_prepare(spline, nu, nk, dtk, knots, ys, aux);
     for (int h = 0; h < H; ++h)
         step_setpoints(spline, nu, nk, H, dtk, knots, ys, aux, h, qref + (size_t)h * nu, vref + (size_t)h * nu);
@@ -950,54 +967,59 @@ void orc_setpoints(int spline, int nu, int nk, int H, double dt, const double* k
 /* Rollout of one sample (Alg. 1 "simulate"): H steps from x0 tracking the Hermite
  * setpoints of knots [nk][2][nu]; returns S = sum_h c(x_h, u_h) + c_T(x_H) (Sec. IV-A).
  * x_final [nx] and traj [(H+1)][nx] are optional. */
-double orc_rollout_ex(const orc_model* m, const double* x0, const double* knots, int nk, int H,
-                      double dt, int spline, double* x_final, double* traj) {
+real orc_rollout_ex(const orc_model* m, const real* x0, const real* knots, int nk, int H,
+                      real dt, int spline, real* x_final, real* traj) {
     const int nj = m->nb - 1, nq = 7 + nj, nx = nq + 6 + nj;
-    double x[7 + ORC_MAXB + 6 + ORC_MAXB];
-    double qref[ORC_MAXB], vref[ORC_MAXB], tau[ORC_MAXB], acc[ORC_MAXNV];
+    real x[7 + ORC_MAXB + 6 + ORC_MAXB];
+    real qref[ORC_MAXB], vref[ORC_MAXB], tau[ORC_MAXB], acc[ORC_MAXNV];
     orc_kin* K = (orc_kin*)malloc(sizeof(orc_kin));
-    memcpy(x, x0, sizeof(double) * nx);
-    const double dtk = knot_dt(nk, H, dt);
+    memcpy(x, x0, sizeof(real) * nx);
+    const real dtk = knot_dt(nk, H, dt);
     /* position-only variants: per-joint node positions and their spline data */
-    double* ys = (double*)malloc(sizeof(double) * (size_t)(nj > 0 ? nj : 1) * nk);
-    double* aux = (double*)malloc(sizeof(double) * (size_t)(nj > 0 ? nj : 1) * nk);
+    real* ys = (real*)malloc(sizeof(real) * (size_t)(nj > 0 ? nj : 1) * nk);
+    real* aux = (real*)malloc(sizeof(real) * (size_t)(nj > 0 ? nj : 1) * nk);
     if (spline != ORC_SPLINE_HERMITE) variant_prepare(spline, nj, nk, dtk, knots, ys, aux);
-    double S = 0;
-    if (traj) memcpy(traj, x, sizeof(double) * nx);
+    real S = 0;
+    if (traj) memcpy(traj, x, sizeof(real) * nx);
     for (int h = 0; h < H; ++h) {
+        ORC_PHASE(PH_SPLINE);
         step_setpoints(spline, nj, nk, H, dtk, knots, ys, aux, h, qref, vref);
+        ORC_PHASE(PH_PD);
         pd_torque(m, x, qref, vref, tau);
         if (aba(m, x, tau, K, acc) != 0) {
             S = NAN;
             break;
         }
+        ORC_PHASE(PH_COST);
         S += running_cost(m, x, K, tau) + modular_cost(m, x, K);
+        ORC_PHASE(PH_INTEGRATE);
         integrate(m, x, acc, dt);
-        if (traj) memcpy(traj + (size_t)(h + 1) * nx, x, sizeof(double) * nx);
+        ORC_PHASE(PH_OTHER);
+        if (traj) memcpy(traj + (size_t)(h + 1) * nx, x, sizeof(real) * nx);
     }
     if (H > 0 && isfinite(S)) S += terminal_cost(m, x0, x, H, dt);
-    if (x_final) memcpy(x_final, x, sizeof(double) * nx);
+    if (x_final) memcpy(x_final, x, sizeof(real) * nx);
     free(K);
     free(ys);
     free(aux);
     return S;
 }
 
-double orc_rollout(const orc_model* m, const double* x0, const double* knots, int nk, int H,
-                   double dt, double* x_final, double* traj) {
+real orc_rollout(const orc_model* m, const real* x0, const real* knots, int nk, int H,
+                   real dt, real* x_final, real* traj) {
     return orc_rollout_ex(m, x0, knots, nk, H, dt, ORC_SPLINE_HERMITE, x_final, traj);
 }
 
 /* Sec. III-E state prediction: simulate the first `nsteps` steps of the spline defined by
  * knots over a horizon of H steps (knot times as in the rollout) from x0; x_out [nx]. */
-int orc_predict_state(const orc_model* m, const double* x0, const double* knots, int nk, int H, int nsteps,
-                      double dt, double* x_out) {
+int orc_predict_state(const orc_model* m, const real* x0, const real* knots, int nk, int H, int nsteps,
+                      real dt, real* x_out) {
     const int nj = m->nb - 1, nq = 7 + nj, nx = nq + 6 + nj;
-    double* tr = (double*)malloc(sizeof(double) * (size_t)(H + 1) * nx);
-    double S = orc_rollout(m, x0, knots, nk, H, dt, NULL, tr);
+    real* tr = (real*)malloc(sizeof(real) * (size_t)(H + 1) * nx);
+    real S = orc_rollout(m, x0, knots, nk, H, dt, NULL, tr);
     (void)S;
     if (nsteps > H) nsteps = H;
-    memcpy(x_out, tr + (size_t)nsteps * nx, sizeof(double) * nx);
+    memcpy(x_out, tr + (size_t)nsteps * nx, sizeof(real) * nx);
     free(tr);
     return 0;
 }
@@ -1007,16 +1029,16 @@ int orc_predict_state(const orc_model* m, const double* x0, const double* knots,
  * horizon end T = H dt. In the rollout's integer units r = t / dt * (nk - 1):
  * r_j = min(j H + steps (nk - 1), H (nk - 1)), segment k = min(floor(r_j / H), nk - 2),
  * s = (r_j - k H) / H. knots in/out [nk][2][nu] (may not alias). */
-void orc_shift_knots(int nu, int nk, int H, int steps, double dt, const double* in, double* out) {
-    const double dtk = knot_dt(nk, H, dt);
+void orc_shift_knots(int nu, int nk, int H, int steps, real dt, const real* in, real* out) {
+    const real dtk = knot_dt(nk, H, dt);
     for (int j = 0; j < nk; ++j) {
         long r = (long)j * H + (long)steps * (nk - 1);
         if (r > (long)H * (nk - 1)) r = (long)H * (nk - 1);
         long k = r / H;
         if (k > nk - 2) k = nk - 2;
-        double s = (double)(r - k * (long)H) / (double)H;
+        real s = (real)(r - k * (long)H) / (real)H;
         for (int i = 0; i < nu; ++i) {
-            double q, qd;
+            real q, qd;
             orc_hermite(s, dtk, in[(k * 2 + 0) * nu + i], in[(k * 2 + 1) * nu + i], in[((k + 1) * 2 + 0) * nu + i],
                         in[((k + 1) * 2 + 1) * nu + i], &q, &qd);
             out[(j * 2 + 0) * nu + i] = q;
@@ -1031,8 +1053,8 @@ void orc_shift_knots(int nu, int nk, int H, int steps, double dt, const double* 
 /* info[0..5] = S_min, S_max, argmin (ties -> lowest index), ESS = 1/sum w^2, n_finite,
  * log-sum-exp. normalize 0: min-max Eq. (softmax_minmax); 1: raw Eq. (omega-weights).
  * Non-finite costs get weight 0. Returns 0, or -3 when no cost is finite (w = 0). */
-int orc_weights(int N, const double* S, double lambda, int normalize, double* w, double* info) {
-    double smin = INFINITY, smax = -INFINITY;
+int orc_weights(int N, const real* S, real lambda, int normalize, real* w, real* info) {
+    real smin = INFINITY, smax = -INFINITY;
     int best = -1, nf = 0;
     for (int n = 0; n < N; ++n) {
         if (!isfinite(S[n])) continue;
@@ -1045,20 +1067,20 @@ int orc_weights(int N, const double* S, double lambda, int normalize, double* w,
         info[0] = NAN; info[1] = NAN; info[2] = -1; info[3] = 0; info[4] = 0; info[5] = NAN;
         return -3;
     }
-    double range = smax - smin;
-    double z = 0;
+    real range = smax - smin;
+    real z = 0;
     for (int n = 0; n < N; ++n) {
         if (!isfinite(S[n])) continue;
-        double sh;
+        real sh;
         if (normalize == 0) sh = range > 0 ? (S[n] - smin) / range : 0.0;
         else sh = S[n] - smin;
         z += exp(-sh / lambda);
     }
-    double lse = log(z);
-    double ess_den = 0;
+    real lse = log(z);
+    real ess_den = 0;
     for (int n = 0; n < N; ++n) {
         if (!isfinite(S[n])) continue;
-        double sh;
+        real sh;
         if (normalize == 0) sh = range > 0 ? (S[n] - smin) / range : 0.0;
         else sh = S[n] - smin;
         w[n] = exp(-sh / lambda - lse);
@@ -1069,9 +1091,9 @@ int orc_weights(int N, const double* S, double lambda, int normalize, double* w,
 }
 
 /* Eq. (update-nominal) on the knots: out[e] = sum_n w_n theta_{n,e}. */
-void orc_average(int N, int E, const double* knots, const double* w, double* out) {
+void orc_average(int N, int E, const real* knots, const real* w, real* out) {
     for (int e = 0; e < E; ++e) {
-        double s = 0;
+        real s = 0;
         for (int n = 0; n < N; ++n) s += w[n] * knots[(size_t)n * E + e];
         out[e] = s;
     }
@@ -1082,12 +1104,12 @@ void orc_average(int N, int E, const double* knots, const double* w, double* out
 /* ------------------------------------------------------------------------------------ */
 typedef struct {
     const orc_model* m;
-    const double* x0;
-    const double* knots;
+    const real* x0;
+    const real* knots;
     int N, nk, H, E, nx, tid, nthreads, spline;
-    double dt;
-    double* costs;
-    double* finals;
+    real dt;
+    real* costs;
+    real* finals;
 } rollout_job;
 
 static void* rollout_worker(void* arg) {
@@ -1099,8 +1121,8 @@ static void* rollout_worker(void* arg) {
 }
 
 /* costs[N] (and finals[N][nx] if non-null) for knots [N][nk][2][nu]. */
-void orc_rollout_batch_ex(const orc_model* m, int N, const double* x0, const double* knots, int nk,
-                          int H, double dt, int spline, double* costs, double* finals, int nthreads) {
+void orc_rollout_batch_ex(const orc_model* m, int N, const real* x0, const real* knots, int nk,
+                          int H, real dt, int spline, real* costs, real* finals, int nthreads) {
     const int nj = m->nb - 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
@@ -1116,8 +1138,8 @@ void orc_rollout_batch_ex(const orc_model* m, int N, const double* x0, const dou
         for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
 
-void orc_rollout_batch(const orc_model* m, int N, const double* x0, const double* knots, int nk,
-                       int H, double dt, double* costs, double* finals, int nthreads) {
+void orc_rollout_batch(const orc_model* m, int N, const real* x0, const real* knots, int nk,
+                       int H, real dt, real* costs, real* finals, int nthreads) {
     orc_rollout_batch_ex(m, N, x0, knots, nk, H, dt, ORC_SPLINE_HERMITE, costs, finals, nthreads);
 }
 
@@ -1131,24 +1153,24 @@ void orc_rollout_batch(const orc_model* m, int N, const double* x0, const double
  * Iteration i draws noise with counter iter_base + i. spline: ORC_SPLINE_* (the position-
  * only variants track their own spline of the sampled position knots).
  * Returns status (0 or -3). */
-int orc_solve(const orc_model* m, int N, int nk, int H, int iters, double dt, double lambda,
-              int normalize, const double* sigma, double scale_q, double scale_v, uint64_t seed,
-              uint32_t iter_base, uint32_t inst, const double* x0, const double* nominal_in,
-              double* mean_out, double* best_out, double* info, int nthreads, double* knots_out,
-              double* costs_out, int spline) {
+int orc_solve(const orc_model* m, int N, int nk, int H, int iters, real dt, real lambda,
+              int normalize, const real* sigma, real scale_q, real scale_v, uint64_t seed,
+              uint32_t iter_base, uint32_t inst, const real* x0, const real* nominal_in,
+              real* mean_out, real* best_out, real* info, int nthreads, real* knots_out,
+              real* costs_out, int spline) {
     const int nj = m->nb - 1, E = nk * 2 * nj;
-    double* knots = (double*)malloc(sizeof(double) * (size_t)N * E);
-    double* costs = (double*)malloc(sizeof(double) * N);
-    double* w = (double*)malloc(sizeof(double) * N);
-    double* nominal = (double*)malloc(sizeof(double) * (size_t)E);
-    memcpy(nominal, nominal_in, sizeof(double) * E);
+    real* knots = (real*)malloc(sizeof(real) * (size_t)N * E);
+    real* costs = (real*)malloc(sizeof(real) * N);
+    real* w = (real*)malloc(sizeof(real) * N);
+    real* nominal = (real*)malloc(sizeof(real) * (size_t)E);
+    memcpy(nominal, nominal_in, sizeof(real) * E);
     int has_limits = 0;
     for (int j = 0; j < nj; ++j)
         if (isfinite(m->q_min[j]) || isfinite(m->q_max[j])) has_limits = 1;
-    double best_cost = INFINITY;
+    real best_cost = INFINITY;
     int best_idx = -1, best_it = -1, status = 0;
-    double winfo[6] = {0};
-    memcpy(best_out, nominal, sizeof(double) * E);
+    real winfo[6] = {0};
+    memcpy(best_out, nominal, sizeof(real) * E);
     for (int it = 0; it < iters; ++it) {
         orc_sample_knots(nj, nk, N, H, dt, nominal, sigma + (size_t)it * nk, scale_q, scale_v, seed,
                          iter_base + (uint32_t)it, inst, has_limits ? m->q_min : NULL,
@@ -1157,8 +1179,8 @@ int orc_solve(const orc_model* m, int N, int nk, int H, int iters, double dt, do
         for (int n = 0; n < N && spline != ORC_SPLINE_HERMITE; ++n)
             orc_spline_slopes(spline, nj, nk, knot_dt(nk, H, dt), knots + (size_t)n * E);
         orc_rollout_batch_ex(m, N, x0, knots, nk, H, dt, spline, costs, NULL, nthreads);
-        if (knots_out) memcpy(knots_out + (size_t)it * N * E, knots, sizeof(double) * (size_t)N * E);
-        if (costs_out) memcpy(costs_out + (size_t)it * N, costs, sizeof(double) * N);
+        if (knots_out) memcpy(knots_out + (size_t)it * N * E, knots, sizeof(real) * (size_t)N * E);
+        if (costs_out) memcpy(costs_out + (size_t)it * N, costs, sizeof(real) * N);
         int st = orc_weights(N, costs, lambda, normalize, w, winfo);
         if (st != 0) {
             status = st;
@@ -1170,10 +1192,10 @@ int orc_solve(const orc_model* m, int N, int nk, int H, int iters, double dt, do
             best_cost = costs[b];
             best_idx = b;
             best_it = it;
-            memcpy(best_out, knots + (size_t)b * E, sizeof(double) * E);
+            memcpy(best_out, knots + (size_t)b * E, sizeof(real) * E);
         }
     }
-    memcpy(mean_out, nominal, sizeof(double) * E);
+    memcpy(mean_out, nominal, sizeof(real) * E);
     info[0] = winfo[0]; info[1] = winfo[1]; info[2] = best_cost; info[3] = best_idx;
     info[4] = best_it; info[5] = winfo[3]; info[6] = winfo[4]; info[7] = status;
     free(knots);

@@ -53,11 +53,16 @@ products and the congruence shift, and legs evaluate their setpoints in the Herm
   leg:   yaw 568, roll 516, thigh 466, shin 516, ankle 516, foot (leaf) 389           2971
   arm:   shoulder pitch 533, shoulder roll 481, upper arm 431, forearm (leaf) 404    1849
   waist: two children (54), offset along z                                             508
+
+The method's own count (the FP64 oracle with an operation-counting scalar type, at the end
+of this file) is the roofline's numerator; these per-primitive counts of the kernels'
+formulations are reported beside it.
 """
 from __future__ import annotations
 
 PER_JOINT = 55 + 31 + 111 + 21 + 78 + 565 + 27 + 67 + 4 + 2
 PER_CONTACT = 18 + 27 + 4 + 12 + 15 + 12
+PER_BASE_SOLVE = 161 + 6   # 6x6 Cholesky solve and the gravity offset
 PER_BASE = 25 + 78 + 161 + 6 + 94 + 42
 MOD_JOINT = 4
 MOD_CONTACT = 5 + 8 + 4
@@ -156,6 +161,30 @@ def flops_per_step(model, contacts_active=None, mapping_chain=True) -> int:
     if any(getattr(model, w, 0.0) for w in MOD_WEIGHTS):
         f += MOD_JOINT * model.nj + MOD_CONTACT * model.nc + MOD_BASE
     return f
+
+
+# Algorithmic work per step-sample as the method specifies it: the FP64 oracle (which
+# restates Alg. 1's rollout with dense 6x6 spatial algebra) run with an operation-counting
+# scalar type on the workloads' own samples (16 of each, the configurations' seeds),
+# averaged per step. "dense" counts every operation (add/sub, mul, div, sqrt and the
+# elementary functions one each; a multiply-add is two); "nontrivial" leaves out those
+# whose result a structural operand fixes (an added 0, a factor 0 or +-1, a divisor +-1):
+# multiplying by the zeros of a 6x6 spatial transform is not work of the algorithm, and
+# the dense figure divided by the measured rollout time would exceed the FP32 peak.
+# The non-trivial figure is the roofline's numerator; the kernels' own formulations
+# (above) do a little less (they hoist the model-constant body inertias and form 1 / D
+# once per body where the oracle divides per element).
+METHOD_FLOPS = {
+    # workload: (dense, nontrivial) per step-sample
+    "scale_quadruped": (24157.7, 6767.4),
+    "plain_quadruped": (24173.9, 6747.7),
+    "humanoid": (41946.6, 13160.5),
+}
+
+
+def method_flops_per_step(workload: str):
+    """(dense, nontrivial) oracle operation counts per step-sample of a workload, or None."""
+    return METHOD_FLOPS.get(workload)
 
 
 def fp32_peak_tflops(sms: int = 152, clock_mhz: float = 2070.0) -> float:
