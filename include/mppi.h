@@ -53,7 +53,7 @@ typedef int32_t mppi_status;
 #define MPPI_MAP_HALFWARP 1   /* one sample per 16 lanes, one lane per body (nb<=16) */
 #define MPPI_MAP_CHAIN 2      /* one sample per 4 lanes, one lane per leg chain (a
                                  floating base with 4 equal 3-body chains)           */
-#define MPPI_MAP_THREAD 3     /* one sample per thread (specialised robot trees)    */
+#define MPPI_MAP_THREAD 3     /* reserved: no kernel; contexts reject it (INVALID_ARG) */
 
 /* Weight normalisation. */
 #define MPPI_NORM_MINMAX 0    /* Eq. (softmax_minmax): costs min-max normalised first */
@@ -323,6 +323,15 @@ mppi_status mppi_average(int32_t K, int32_t E, const float* h_knots, const doubl
 mppi_status mppi_average_noalloc(int32_t K, int32_t E, const float* d_knots, const double* d_w, double* d_out,
                                  void* stream);
 
+/* Bounds-check word of a check build of the library (compiled with -DMPPI_CHECK; no
+ * counterpart in the paper): every index check on the path (noise, segment, split
+ * records, persistent queue items, chunk sums, best sample) that failed since the last
+ * reset set its bit here (1 noise, 2 segment, 4 queue, 8 chunk, 16 split record, 32 best
+ * sample); the kernel skipped or clamped that access instead of trapping. reset != 0
+ * clears the word after reading it. Returns MPPI_ERR_UNSUPPORTED (word 0) in the product
+ * build, which has no checks. */
+mppi_status mppi_check_word(uint32_t* h_word, int32_t reset);
+
 /* Single-step state derivative: generalised accelerations h_acc [n][nv] (base spatial
  * acceleration (w_dot, v_dot) in body coordinates, then qdd) of n states under
  * torques h_tau [n][nj], contact forces included, by the warp-per-sample articulated-
@@ -420,8 +429,9 @@ mppi_status mppi_server_stats_ex(mppi_server* server, int64_t* h_out, int32_t n)
 
 /* Time every supported rollout mapping and block size for this context's model and
  * sizes (a few timed launches each) and switch the context to the fastest. h_ms (nullable,
- * [4*4]) receives the timings in ms per rollout launch (mapping-major, block sizes 32, 64,
- * 128, 256; negative = not supported). Writes the choice to *mapping / *block_size. */
+ * [4*4]) receives the timings in ms per rollout launch (mapping-major: warp, half-warp,
+ * lanes-per-chain and the reserved mapping 3, whose row is always negative; block sizes 32,
+ * 64, 128, 256; negative = not supported). Writes the choice to *mapping / *block_size. */
 mppi_status mppi_autotune(mppi_ctx* ctx, int32_t* mapping, int32_t* block_size, float* h_ms);
 
 /* Persist the autotuner's choices in a JSON file (an array with one object per tuned
@@ -432,7 +442,7 @@ mppi_status mppi_autotune(mppi_ctx* ctx, int32_t* mapping, int32_t* block_size, 
  * only. Errors: INVALID_ARG (the file exists but is not in this format). */
 mppi_status mppi_autotune_cache_file(const char* path);
 
-/* Switch a context's rollout mapping and block size (MPPI_MAP_WARP/HALFWARP/CHAIN/THREAD). */
+/* Switch a context's rollout mapping and block size (MPPI_MAP_WARP/HALFWARP/CHAIN). */
 mppi_status mppi_ctx_set_mapping(mppi_ctx* ctx, int32_t mapping, int32_t block_size);
 
 /* FP64 check build: when on, mppi_rollout_explicit runs the same rollout source in double

@@ -13,6 +13,7 @@
 #include <tuple>
 
 #include "capi_internal.h"
+#include "nvtx.h"
 
 namespace mppi {
 
@@ -244,6 +245,7 @@ mppi_status autotune_ctx(mppi_ctx* c, int reps, TuneVal* out) {
 using namespace mppi;
 
 extern "C" mppi_status mppi_autotune(mppi_ctx* c, int32_t* mapping, int32_t* block, float* h_ms) {
+    MPPI_NVTX("mppi_autotune");
     if (!c) return MPPI_ERR_INVALID_ARG;
     // the timed rollouts start from the context's last state if a solve ran, else from
     // the model's rest pose half a metre above the ground

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "nvtx.h"
 #include "capi_internal.h"
 #include "noise.cuh"
 #include "reduce.cuh"
@@ -79,7 +80,9 @@ struct QueueItem {
 
 struct BatchQueue {
     int head, append, total, nprefill;
-    uint32_t error, pad0, pad1, pad2;
+    uint32_t error;
+    int count;   // instances of the batch (bounds of the items' instance index)
+    uint32_t pad1, pad2;
 };
 
 // Where a group's queue, items and prefill list sit in the device block (byte offsets).
@@ -271,7 +274,15 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
             break;
         }
         const int ii = s_inst;
+        if (!MPPI_CHECK_OK(ii >= 0 && ii < q->count, CHECK_QUEUE)) {
+            if (threadIdx.x == 0) atomicOr(&q->error, DEV_ERR_BAD_ITEM);
+            break;
+        }
         const BatchInst& I = insts[ii];
+        if (!MPPI_CHECK_OK(s_item >= 0 && s_item < (type == ITEM_ROLLOUT ? I.ntiles : I.nchunks), CHECK_QUEUE)) {
+            if (threadIdx.x == 0) atomicOr(&q->error, DEV_ERR_BAD_ITEM);
+            break;
+        }
         const int it = *reinterpret_cast<volatile int*>(&ctr[ii].it);
         if (type == ITEM_ROLLOUT) {
             if (s_loaded != (const void*)I.model) {
@@ -563,6 +574,7 @@ void fill_batch_image(mppi_ctx* const* ctxs, const BatchLayout& L, const double*
         memset(q, 0, sizeof *q);
         q->total = (int)g.total;
         q->nprefill = (int)g.nprefill;
+        q->count = L.count;
         gd[k].q = (long long)g.o_q;
         gd[k].items = (long long)g.o_items;
         gd[k].pre = (long long)g.o_pre;
@@ -926,6 +938,7 @@ mppi_status check_batchable(const mppi_ctx* c, int dev) {
 extern "C" mppi_status mppi_solve_batch(mppi_ctx* const* ctxs, int32_t count, const double* const* h_states,
                                         const float* const* h_warm, float* const* h_out_mean,
                                         float* const* h_out_best, mppi_result* h_info) {
+    MPPI_NVTX("mppi_solve_batch");
     if (!ctxs || count < 1 || !h_states || !h_out_mean) return MPPI_ERR_INVALID_ARG;
     int dev;
     cudaError_t e = cudaGetDevice(&dev);

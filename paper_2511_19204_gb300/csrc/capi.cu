@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "capi_internal.h"
+#include "nvtx.h"
 
 namespace mppi {
 
@@ -286,6 +287,7 @@ const char* mppi_last_error(const mppi_ctx* ctx) {
 }
 
 mppi_status mppi_model_create(const mppi_model_desc* d, mppi_model** out) {
+    MPPI_NVTX("mppi_model_create");
     if (!d || !out) return MPPI_ERR_INVALID_ARG;
     *out = nullptr;
     auto bad = [&](const char* why) {
@@ -426,7 +428,6 @@ cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knot
         case MPPI_MAP_CHAIN:
             return launch_rollout_chain_f32(a, c->model->topology, c->model->host_f.paper_cost != 0,
                                             c->model->host_f.axis_plan, c->block, s);
-        case MPPI_MAP_THREAD: return launch_rollout_thread_f32(a, c->model->topology, c->block, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -530,7 +531,6 @@ cudaError_t prepare_kernels() {
     cudaError_t e = prepare_weights_kernels();
     if (e == cudaSuccess) e = prepare_warp_f32();
     if (e == cudaSuccess) e = prepare_warp_f64();
-    if (e == cudaSuccess) e = prepare_thread_f32();
     return e;
 }
 
@@ -545,9 +545,8 @@ bool mapping_valid(const mppi_model* m, int mapping, int block) {
             if (m->host_f.axis_plan == AXP_HUM)  // warp pairs
                 return block == 0 || (block % 64 == 0 && block >= 64 && block <= 256);
             return chain_mapping_supported(m->topology) && (block == 0 || (block % 32 == 0 && block >= 32 && block <= 256));
-        case MPPI_MAP_THREAD:
-            return m->topology != TOPO_GENERIC && thread_mapping_supported(m->topology) &&
-                   (block == 0 || (block % 32 == 0 && block >= 32 && block <= 512));
+        case MPPI_MAP_THREAD:   // reserved: no kernel
+            return false;
         default: return false;
     }
 }
@@ -558,6 +557,7 @@ extern "C" {
 
 mppi_status mppi_create(const mppi_model* model, int32_t K, int32_t H, int32_t knots, double lambda,
                         const float* h_sigma, int32_t iters, const mppi_params* p, mppi_ctx** out) {
+    MPPI_NVTX("mppi_create");
     if (!out) return MPPI_ERR_INVALID_ARG;
     *out = nullptr;
     auto bad = [&](const char* why) {
@@ -667,6 +667,7 @@ void mppi_destroy(mppi_ctx* c) {
 
 mppi_status mppi_solve(mppi_ctx* c, const double* h_state, const float* h_warm, float* h_out_mean,
                        float* h_out_best, mppi_result* h_info) {
+    MPPI_NVTX("mppi_solve");
     if (!c || !h_state || !h_out_mean) return MPPI_ERR_INVALID_ARG;
     for (int i = 0; i < c->nx; ++i)
         if (!isfinite(h_state[i])) {
@@ -694,6 +695,7 @@ mppi_status mppi_solve(mppi_ctx* c, const double* h_state, const float* h_warm, 
 
 mppi_status mppi_solve_device(mppi_ctx* c, const double* d_state, const float* d_warm, float* d_out_mean,
                               float* d_out_best, mppi_result* d_info) {
+    MPPI_NVTX("mppi_solve_device");
     if (!c || !d_state || !d_out_mean) return MPPI_ERR_INVALID_ARG;
     CK(c, cudaMemcpyAsync(c->d_x0, d_state, sizeof(double) * c->nx, cudaMemcpyDeviceToDevice, c->stream));
     c->has_state = true;
@@ -723,6 +725,7 @@ mppi_status mppi_sync(mppi_ctx* c) {
 
 mppi_status mppi_rollout_explicit(mppi_ctx* c, const double* h_state, const float* h_knots, double* h_costs,
                                   double* h_finals) {
+    MPPI_NVTX("mppi_rollout_explicit");
     if (!c || !h_state || !h_knots || !h_costs) return MPPI_ERR_INVALID_ARG;
     const int N = c->N, E = c->E, nx = c->nx;
     double* d_x = nullptr;
@@ -799,6 +802,7 @@ mppi_status mppi_rollout_explicit(mppi_ctx* c, const double* h_state, const floa
 
 mppi_status mppi_sample_knots(mppi_ctx* c, int32_t iter, uint32_t iter_counter, const float* h_nominal,
                               float* h_out) {
+    MPPI_NVTX("mppi_sample_knots");
     if (!c || !h_nominal || !h_out || iter < 0 || iter >= c->iters) return MPPI_ERR_INVALID_ARG;
     float *d_nom = nullptr, *d_out = nullptr;
     const size_t NE = (size_t)c->N * c->E;
@@ -905,6 +909,7 @@ static mppi_status enqueue_predict(mppi_ctx* c, const double* d_state, int32_t s
 }
 
 mppi_status mppi_predict_state_device(mppi_ctx* c, const double* d_state, int32_t steps, double* d_out) {
+    MPPI_NVTX("mppi_predict_state_device");
     if (!c) return MPPI_ERR_INVALID_ARG;
     if (!d_state || !d_out || steps < 0 || steps > c->H) {
         set_error(c, "mppi_predict_state_device: needs device state and output and 0 <= steps <= H");
@@ -914,6 +919,7 @@ mppi_status mppi_predict_state_device(mppi_ctx* c, const double* d_state, int32_
 }
 
 mppi_status mppi_predict_state(mppi_ctx* c, const double* h_state, int32_t steps, double* h_out) {
+    MPPI_NVTX("mppi_predict_state");
     if (!c) return MPPI_ERR_INVALID_ARG;
     if (!h_state || !h_out || steps < 0 || steps > c->H) {
         set_error(c, "mppi_predict_state: needs state and output and 0 <= steps <= H");
@@ -940,6 +946,7 @@ mppi_status mppi_predict_state(mppi_ctx* c, const double* h_state, int32_t steps
 }
 
 mppi_status mppi_shift_warm_start(mppi_ctx* c, int32_t steps) {
+    MPPI_NVTX("mppi_shift_warm_start");
     if (!c) return MPPI_ERR_INVALID_ARG;
     if (steps < 0) {
         set_error(c, "mppi_shift_warm_start: steps must be >= 0");
@@ -1010,6 +1017,7 @@ mppi_status mppi_philox_words(int32_t n, const uint32_t* h_ctr, const uint32_t* 
 
 mppi_status mppi_weights(int32_t K, const float* h_costs, double lambda, int32_t normalize, double* h_w,
                          mppi_result* h_info) {
+    MPPI_NVTX("mppi_weights");
     if (K < 1 || !h_costs || !h_w || !(lambda > 0)) return MPPI_ERR_INVALID_ARG;
     if (normalize != MPPI_NORM_MINMAX && normalize != MPPI_NORM_RAW) return MPPI_ERR_INVALID_ARG;
     float *d_c = nullptr, *d_k = nullptr;
@@ -1049,6 +1057,7 @@ mppi_status mppi_weights(int32_t K, const float* h_costs, double lambda, int32_t
 }
 
 mppi_status mppi_average(int32_t K, int32_t E, const float* h_knots, const double* h_w, double* h_out) {
+    MPPI_NVTX("mppi_average");
     if (K < 1 || E < 1 || !h_knots || !h_w || !h_out) return MPPI_ERR_INVALID_ARG;
     float* d_k = nullptr;
     double *d_w = nullptr, *d_p = nullptr, *d_o = nullptr;
@@ -1077,6 +1086,7 @@ mppi_status mppi_forward_dynamics(const mppi_model* m, int32_t n, const double* 
 
 mppi_status mppi_forward_dynamics_ex(const mppi_model* m, int32_t n, const double* h_x, const double* h_tau,
                                      double* h_acc, int32_t fp64) {
+    MPPI_NVTX("mppi_forward_dynamics");
     if (!m || n < 0 || (n > 0 && (!h_x || !h_acc || (m->nj > 0 && !h_tau)))) return MPPI_ERR_INVALID_ARG;
     if (n == 0) return MPPI_OK;
     const int nx = 13 + 2 * m->nj, nv = 6 + m->nj;

@@ -36,7 +36,9 @@ __global__ void __launch_bounds__(256) rollout_split_kernel(RolloutArgs<float> a
         if (threadIdx.x == 0 && a.status) atomicOr(a.status, DEV_ERR_TMA_TIMEOUT);
         return;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pair = warp >> 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int pair = warp >> 1;
+    if (!MPPI_CHECK_OK(pair < 4, CHECK_SPLIT)) pair = 3;   // xch holds 4 pairs (launches allow <= 256 threads)
     const int n = blockIdx.x * (blockDim.x / LANES) + pair * SPLIT_SPP + (lane >> 1);
     const bool active = n < a.N;
     const int ne = active ? n : a.N - 1;

@@ -507,6 +507,25 @@ __device__ __forceinline__ bool bulk_load_to_smem(void* smem_dst, const void* gm
     return false;
 }
 
+// Bounds checks of the check build (compiled with -DMPPI_CHECK, in place of a memory
+// checker): MPPI_CHECK_OK(cond, bit) is cond, and when cond fails it also
+// sets `bit` in the translation unit's check word (mppi_check_word reads the word of the
+// unit that holds every FP32 kernel); the caller then skips or clamps the access, so a
+// failed check never traps. In the product build it is the constant true and the
+// compiler removes the check.
+#ifdef MPPI_CHECK
+static __device__ uint32_t g_check_word;
+#define MPPI_CHECK_OK(cond, bit) ((cond) ? true : (atomicOr(&::mppi::g_check_word, (uint32_t)(bit)), false))
+#else
+#define MPPI_CHECK_OK(cond, bit) true
+#endif
+constexpr uint32_t CHECK_NOISE = 1u;    // noise: a sample or element outside the knots
+constexpr uint32_t CHECK_KNOT = 2u;     // rollout: a segment past the last knot pair
+constexpr uint32_t CHECK_QUEUE = 4u;    // persistent kernel: an item outside its instance
+constexpr uint32_t CHECK_CHUNK = 8u;    // reduction: a chunk or element outside the sums
+constexpr uint32_t CHECK_SPLIT = 16u;   // split rollout: a record outside the pair's area
+constexpr uint32_t CHECK_BEST = 32u;    // finalize: a best sample outside the knots
+
 // Status word written by kernels whose bounded waits gave up.
 constexpr uint32_t DEV_ERR_TMA_TIMEOUT = 1u;
 constexpr uint32_t DEV_ERR_QUEUE_TIMEOUT = 2u;

@@ -63,8 +63,6 @@ struct RolloutArgs {
 cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s);
 cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s);
 cudaError_t launch_rollout_warp_f64(const RolloutArgs<double>& a, int G, int block, cudaStream_t s);
-cudaError_t launch_rollout_thread_f32(const RolloutArgs<float>& a, int topology, int block, cudaStream_t s);
-bool thread_mapping_supported(int topology);
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
                                      cudaStream_t s);
 bool chain_mapping_supported(int topology);
@@ -80,7 +78,6 @@ cudaError_t launch_predict_f64(const DevModel<double>* m, const double* x0, cons
 cudaError_t launch_shift_knots(float* knots, int nj, int nk, int H, int steps, double dtk, cudaStream_t s);
 cudaError_t prepare_warp_f32();
 cudaError_t prepare_warp_f64();
-cudaError_t prepare_thread_f32();
 // weights of each chunk of AVG_CHUNK samples and their partial knot sums (reduce.cuh)
 cudaError_t launch_weights_average(const float* costs, const float* knots, int N, int E, double lambda, int normalize,
                                    double* e_out, double* zq, double* partial, DevIterInfo* info, cudaStream_t s);

@@ -82,6 +82,7 @@ __device__ __noinline__ void block_sample_knots(const NoiseParams& a, int n0, in
         if (n >= a.N) continue;
         const int k = rem / a.nj, j = rem - k * a.nj;
         const int eq = (2 * k) * a.nj + j, ev = eq + a.nj;
+        if (!MPPI_CHECK_OK(nl < NOISE_SPB && ev < E, CHECK_NOISE)) continue;
         const float sg = a.sigma_row[k];
         float q = __fmaf_rn(__fmul_rn(sg, a.scale_q), eps[nl * E + eq], a.nominal[eq]);
         float v = __fmaf_rn(__fmul_rn(sg, a.scale_v), eps[nl * E + ev], a.nominal[ev]);

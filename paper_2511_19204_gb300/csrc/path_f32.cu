@@ -24,3 +24,21 @@ cudaError_t launch_predict_f32(const DevModel<float>* m, const double* x0, const
 }
 cudaError_t prepare_warp_f32() { return prepare_warp_kernels<float>(); }
 }  // namespace mppi
+
+// The check word of this translation unit, which holds every FP32 kernel of the path
+// (check builds only; see MPPI_CHECK_OK in common.cuh).
+extern "C" mppi_status mppi_check_word(uint32_t* h_word, int32_t reset) {
+    if (!h_word) return MPPI_ERR_INVALID_ARG;
+    *h_word = 0;
+#ifdef MPPI_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(h_word, mppi::g_check_word, sizeof(uint32_t));
+    if (e == cudaSuccess && reset) {
+        const uint32_t zero = 0;
+        e = cudaMemcpyToSymbol(mppi::g_check_word, &zero, sizeof(uint32_t));
+    }
+    return e == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+#else
+    (void)reset;
+    return MPPI_ERR_UNSUPPORTED;
+#endif
+}

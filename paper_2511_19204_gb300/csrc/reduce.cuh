@@ -221,6 +221,7 @@ __device__ __noinline__ void chunk_partial(const float* __restrict__ costs, cons
     const int t = threadIdx.x, B = blockDim.x;
     const int n0 = c * AVG_CHUNK;
     const int cn = min(AVG_CHUNK, N - n0);
+    if (!MPPI_CHECK_OK(n0 < N && n0 >= 0, CHECK_CHUNK)) return;
     const MinMax mm = block_minmax(costs, N, lambda, normalize);
     // the first pair of tasks of the first tile: loads in flight while the weights form
     const int ne0 = min(SUB_TILE, E), nt0 = SUB_SPLIT * ne0;
@@ -392,8 +393,11 @@ __device__ __noinline__ void finalize_iteration(const FinalizeArgs& a) {
         }
         asm volatile("bar.sync %0, %1;" ::"r"(FIN_BARRIER), "r"(B) : "memory");
         const double inv_z = s_inv_z;
-        const bool ok = s_ok, upd = s_update;
+        const bool ok = s_ok;
         const int best = s_best;
+        // (the check build skips the copy of an out-of-range best sample; no early return,
+        // the block's last barrier is still ahead)
+        const bool upd = s_update && MPPI_CHECK_OK(best >= 0 && best < a.nchunks * AVG_CHUNK, CHECK_BEST);
         const bool keep_best = last && a.warm_from == MPPI_WARM_BEST && s_best_final >= 0;
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
@@ -581,7 +585,8 @@ __device__ __forceinline__ void reduce_chunk_grid(const FinalizeArgs& f, int N, 
 #pragma unroll
         for (int g = 0; g < 16; ++g) v[g] = g < ng ? s_G[t * ng + g] : 0.0;
         const double tot = tree16n(v, ng);
-        const bool ok = s_ok, upd = s_upd;
+        const bool ok = s_ok;
+        const bool upd = s_upd && MPPI_CHECK_OK(s_best >= 0 && s_best < N, CHECK_BEST);
         const bool keep_best = last && f.warm_from == MPPI_WARM_BEST && s_best_final >= 0;
         const float m = ok ? (float)(tot * s_inv_z) : f.nominal[e];
         float bv = 0.f;

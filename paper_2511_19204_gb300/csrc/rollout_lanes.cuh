@@ -740,6 +740,7 @@ __device__ __noinline__ R_T lanes_rollout(const DevModel<R_T>& M, int g, const d
             rem -= H;
             ++k;
         }
+        if (!MPPI_CHECK_OK(k + 1 < nk, CHECK_KNOT)) k = nk - 2;
         const R_T s = (R_T)rem * inv_H;
         if (KEEP && k != kcur) {
             kcur = k;

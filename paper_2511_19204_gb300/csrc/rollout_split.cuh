@@ -182,6 +182,7 @@ __device__ __noinline__ R_T split_legs(const DevModel<R_T>& M, int side, const R
             rem -= H;
             ++k;
         }
+        if (!MPPI_CHECK_OK(k + 1 < nk, CHECK_KNOT)) k = nk - 2;
         const R_T s = (R_T)rem * inv_H;
         // power-basis setpoints, formed once per segment (the registers they hold became
         // free once the base's integration moved to the arm warp)
@@ -344,6 +345,7 @@ __device__ __noinline__ R_T split_arms(const DevModel<R_T>& M, int side, R_T* re
             rem -= H;
             ++k;
         }
+        if (!MPPI_CHECK_OK(k + 1 < nk, CHECK_KNOT)) k = nk - 2;
         const R_T s = (R_T)rem * inv_H;
         if (k != kcur) {
             kcur = k;

@@ -40,6 +40,7 @@
 
 #include "batch.h"
 #include "capi_internal.h"
+#include "nvtx.h"
 
 namespace mppi {
 
@@ -166,6 +167,7 @@ static std::vector<Request*> take_requests(mppi_server* S, size_t* bytes_out) {
 // Builds and enqueues one slot's launch (no lock: the slot and its requests belong to the
 // worker until they are published).
 static cudaError_t launch_slot(mppi_server* S, Slot& s) {
+    MPPI_NVTX("mppi_server_launch");
     std::vector<mppi_ctx*> ctxs;
     std::vector<const double*> states;
     std::vector<const float*> warms;
@@ -187,6 +189,7 @@ static cudaError_t launch_slot(mppi_server* S, Slot& s) {
 
 // Results of a finished slot into its request records (no lock).
 static mppi_status unpack_slot(Slot& s, cudaError_t q, std::vector<mppi_result>& infos) {
+    MPPI_NVTX("mppi_server_retire");
     std::vector<mppi_ctx*> ctxs;
     std::vector<float*> means, bests;
     infos.assign(s.reqs.size(), mppi_result{});

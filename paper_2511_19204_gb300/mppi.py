@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmppi.so")
+# the library to load: MPPI_LIBRARY (e.g. the bounds-check build) or the in-tree build
+LIB_PATH = os.environ.get("MPPI_LIBRARY") or os.path.join(_HERE, "libmppi.so")
 
 MPPI_OK = 0
 MPPI_PENDING = 1
@@ -37,7 +38,7 @@ MPPI_MAP_HALFWARP = 1
 MPPI_MAP_CHAIN = 2
 MPPI_MAP_THREAD = 3
 MAPPING_NAMES = {MPPI_MAP_WARP: "warp-per-sample", MPPI_MAP_HALFWARP: "halfwarp-per-sample",
-                 MPPI_MAP_CHAIN: "lanes-per-chain", MPPI_MAP_THREAD: "thread-per-sample"}
+                 MPPI_MAP_CHAIN: "lanes-per-chain", MPPI_MAP_THREAD: "reserved"}
 MPPI_NORM_MINMAX = 0
 MPPI_NORM_RAW = 1
 MPPI_WARM_BEST = 0
@@ -116,6 +117,7 @@ SIGNATURES = [
     ("mppi_model_info", C.c_int32, [_P, _ip]),
     ("mppi_selftest_math", C.c_int32, [C.c_int32, _fp, _fp, _fp]),
     ("mppi_selftest_widen", C.c_int32, [C.c_int32, _fp, _dp]),
+    ("mppi_check_word", C.c_int32, [_u32p, C.c_int32]),
     ("mppi_autotune_cache_file", C.c_int32, [C.c_char_p]),
     ("mppi_philox_words", C.c_int32, [C.c_int32, _u32p, _u32p, _u32p]),
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
