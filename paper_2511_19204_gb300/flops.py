@@ -48,9 +48,9 @@ setpoint from a power-basis form of its segment (formed once per segment). Per s
 Humanoids of the usual layout (legs turning about z, x, y, y, y, x; a waist about z; arms
 about y, x, z, y; offsets in the yz-plane, on one axis or zero) run the two-warp split
 kernel with the same specialisations; a zero offset drops the origin, the offset cross
-products and the congruence shift, and legs evaluate their setpoints in the Hermite form
-(55) where arms and waist use the power-basis form (20). Per step:
-  leg:   yaw 568, roll 516, thigh 466, shin 516, ankle 516, foot (leaf) 389           2971
+products and the congruence shift, and every body evaluates its setpoint from the
+power-basis form of its segment (20). Per step:
+  leg:   yaw 533, roll 481, thigh 431, shin 481, ankle 481, foot (leaf) 354           2761
   arm:   shoulder pitch 533, shoulder roll 481, upper arm 431, forearm (leaf) 404    1849
   waist: two children (54), offset along z                                             508
 
@@ -75,8 +75,8 @@ PER_JOINT_XYY_CALF = 20 + 1 + 41 + 4 + 78 + 0 + (1 + 0 + 61 + 140 + 16) + 36 + 4
 # split humanoid kernel: (setpoint, pass 1, child accumulation, pass 2, pass 3) per body,
 # each plus sincos 1, velocity product 4, bias 78, Euler 4, effort 2
 _SPLIT_FIXED = 1 + 4 + 78 + 4 + 2
-PER_JOINT_HUM_LEG = [55 + 51 + 27 + 306 + 40, 55 + 41 + 27 + 268 + 36, 55 + 31 + 27 + 232 + 32,
-                     55 + 41 + 27 + 268 + 36, 55 + 41 + 27 + 268 + 36, 55 + 31 + 0 + 182 + 32]
+PER_JOINT_HUM_LEG = [20 + 51 + 27 + 306 + 40, 20 + 41 + 27 + 268 + 36, 20 + 31 + 27 + 232 + 32,
+                     20 + 41 + 27 + 268 + 36, 20 + 41 + 27 + 268 + 36, 20 + 31 + 0 + 182 + 32]
 PER_JOINT_HUM_ARM = [20 + 51 + 27 + 306 + 40, 20 + 41 + 27 + 268 + 36, 20 + 31 + 27 + 232 + 32,
                      20 + 41 + 0 + 218 + 36]
 PER_JOINT_HUM_WAIST = 20 + 41 + 54 + 268 + 36

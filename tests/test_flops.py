@@ -19,10 +19,10 @@ def test_humanoid_counts():
     h = S.humanoid()
     assert F.axis_plan_hum(h) and not F.axis_plan_xyy(h)
     fixed = F._SPLIT_FIXED
-    assert [c + fixed for c in F.PER_JOINT_HUM_LEG] == [568, 516, 466, 516, 516, 389]
+    assert [c + fixed for c in F.PER_JOINT_HUM_LEG] == [533, 481, 431, 481, 481, 354]
     assert [c + fixed for c in F.PER_JOINT_HUM_ARM] == [533, 481, 431, 404]
     assert F.PER_JOINT_HUM_WAIST + fixed == 508
-    assert F.flops_per_step(h) == 2 * 2971 + 2 * 1849 + 508 + 8 * F.PER_CONTACT + F.PER_BASE == 11258
+    assert F.flops_per_step(h) == 2 * 2761 + 2 * 1849 + 508 + 8 * F.PER_CONTACT + F.PER_BASE == 10838
     assert F.flops_per_step(h, mapping_chain=False) == 21 * F.PER_JOINT + 8 * F.PER_CONTACT + F.PER_BASE
 
 
@@ -111,13 +111,13 @@ def test_kernel_counts_against_the_method(orc):
     # against the oracle's non-trivial operations: the kernels do less where they hoist
     # model constants (body inertias, a body's 1 / D instead of a division per element of
     # the rank-one update) and evaluate setpoints from a power basis; they never do less
-    # than half, and the totals agree within 20 % (quadruped 5 %, humanoid 17 %)
+    # than half, and the totals agree within 25 % (quadruped 5 %, humanoid 21 %)
     for name, p, kernel in (("scale_quadruped", S.scale_quadruped(n=64), 6430),
-                            ("humanoid", S.humanoid_problem(n=64), 11258)):
+                            ("humanoid", S.humanoid_problem(n=64), 10838)):
         dense, nontrivial, per = _workload_counts(orc, p)
         assert F.flops_per_step(p.model) == kernel
         assert kernel <= nontrivial <= dense / 3
-        assert nontrivial / kernel < 1.2
+        assert nontrivial / kernel < 1.25
         # the base's 6x6 solve: the same Cholesky work (the kernel counts 161 with gravity)
         solve = per[orc.PHASES.index("solve"), :5].sum() - per[orc.PHASES.index("solve"), 6:9].sum()
         assert abs(solve - F.PER_BASE_SOLVE) < 0.1 * F.PER_BASE_SOLVE
