@@ -163,7 +163,8 @@ def device_fp32_peak(torch, index: int, flops):
 # ------------------------------------------------------------------------------------
 # DRAM traffic of the dominant kernel, from a committed ncu summary
 # ------------------------------------------------------------------------------------
-TRAFFIC_SOURCES = ["rollout_lanes.cuh", "chain_kernel.cuh", "common.cuh", "rollout_warp.cuh", "internal.h"]
+TRAFFIC_SOURCES = ["rollout_lanes.cuh", "chain_kernel.cuh", "chain_f32.cuh", "scalar_macros.h", "common.cuh",
+                   "rollout_warp.cuh", "internal.h"]
 
 
 def sources_sha256(names=TRAFFIC_SOURCES) -> str:
