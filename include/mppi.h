@@ -332,6 +332,62 @@ mppi_status mppi_average_noalloc(int32_t K, int32_t E, const float* d_knots, con
  * build, which has no checks. */
 mppi_status mppi_check_word(uint32_t* h_word, int32_t reset);
 
+/* ---------------------------------------------------------------------------------- */
+/* Sample shards: one iteration's weights and knot average over samples split into     */
+/* shards (on several devices, or several launches of one)                              */
+/* ---------------------------------------------------------------------------------- */
+/* The weights of Sec. III-C (Eq. (softmax_minmax)) need the global S_min and S_max of
+ * the iteration's costs before any exponential, so a sharded iteration exchanges twice:
+ * (1) each shard scans its costs (mppi_shard_range_local) and the ranges are merged
+ * (mppi_shard_range_merge); (2) each shard forms, with the merged range, its
+ * unnormalised weight sum and weighted knot sums (mppi_shard_moments), the sums are
+ * merged (mppi_shard_moments_merge) and divided (mppi_shard_mean) into the updated
+ * nominal of Eq. (update-nominal). The sample with the global best_index (Sec. III-D)
+ * belongs to exactly one shard, which supplies its knots. Both merges are associative
+ * and commutative (the second up to FP64 rounding: merge in a fixed shard order for
+ * run-to-run identical results). Costs are FP32, sums FP64. The library itself moves no
+ * data between devices; the exchange is the caller's (an all-gather of 4 doubles, then
+ * of E + 1 doubles). */
+typedef struct {
+    double s_min;       /* smallest finite cost (+inf if the shard has none) */
+    double s_max;       /* largest finite cost (-inf if none) */
+    int64_t best_index; /* global sample index of the first smallest cost (-1 if none) */
+    int64_t n_finite;   /* number of finite costs */
+} mppi_shard_range;
+
+/* Range of a shard's K costs d_costs [K] (device); the shard's sample n is global
+ * sample index_base + n. Ties go to the lowest index, non-finite costs are left out
+ * (as in the single-instance weights). Synchronous on `stream` (NULL = legacy default
+ * stream); allocates and frees a few bytes of device memory. Errors: INVALID_ARG
+ * (K < 1, index_base < 0, null pointers), CUDA. */
+mppi_status mppi_shard_range_local(int32_t K, const float* d_costs, int64_t index_base,
+                                   mppi_shard_range* h_out, void* stream);
+
+/* out = the range of the union of a's and b's samples (host only; out may alias a or
+ * b). Associative and commutative. */
+void mppi_shard_range_merge(const mppi_shard_range* a, const mppi_shard_range* b, mppi_shard_range* out);
+
+/* A shard's moments under the merged range `global`: h_out[0] = sum_n w_n and
+ * h_out[1 + e] = sum_n w_n theta_n[e] for e < E, with w_n = exp(-(S_n - S_min) k),
+ * k = 1 / ((S_max - S_min) lambda) for MPPI_NORM_MINMAX (0 when S_max = S_min, i.e.
+ * uniform weights) or 1 / lambda for MPPI_NORM_RAW, and w_n = 0 for a non-finite cost:
+ * the single-instance weights before their division by the total. d_knots [K][E] and
+ * d_costs [K] are the shard's samples (device), h_out [E + 1] host FP64. Synchronous on
+ * `stream`; allocates its scratch on the device for the call (like mppi_average).
+ * Errors: INVALID_ARG (also when global's s_min is not an FP32 value, as a merge of
+ * mppi_shard_range_local results always gives, or s_max < s_min), ALL_COSTS_NONFINITE
+ * (global->n_finite == 0: the iteration leaves the nominal unchanged), CUDA. */
+mppi_status mppi_shard_moments(int32_t K, int32_t E, const float* d_knots, const float* d_costs,
+                               const mppi_shard_range* global, double lambda, int32_t normalize,
+                               double* h_out, void* stream);
+
+/* out[i] = a[i] + b[i] for i <= E (host only; out may alias a or b). */
+void mppi_shard_moments_merge(int32_t E, const double* a, const double* b, double* out);
+
+/* The updated nominal from merged moments: h_mean[e] = sums[1 + e] / sums[0] (FP32).
+ * Errors: INVALID_ARG (E < 1, null pointers, sums[0] not positive and finite). */
+mppi_status mppi_shard_mean(int32_t E, const double* sums, float* h_mean);
+
 /* Single-step state derivative: generalised accelerations h_acc [n][nv] (base spatial
  * acceleration (w_dot, v_dot) in body coordinates, then qdd) of n states under
  * torques h_tau [n][nj], contact forces included, by the warp-per-sample articulated-

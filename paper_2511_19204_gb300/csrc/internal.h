@@ -110,6 +110,15 @@ cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda,
 cudaError_t prepare_weights_kernels();   // co-residency of the cooperative finish, per device
 cudaError_t launch_solve_begin(DevSolve* solve, uint32_t* gcount, int ngroups, const float* nominal, float* best_out,
                                int E, cudaStream_t s);
+// sample shards (shard_kernels.cuh): one shard's cost range, and its unnormalised weights
+// w [K] and their sum under a merged range (S_min, weight scale k)
+struct ShardScan {
+    float smin, smax;
+    int best, nfinite;
+};
+cudaError_t launch_shard_range(const float* costs, int K, ShardScan* out, cudaStream_t s);
+cudaError_t launch_shard_weights(const float* costs, int K, float smin, double k, double* w, double* wsum,
+                                 cudaStream_t s);
 cudaError_t launch_fast_math(int n, const float* x, const float* y, float* out, cudaStream_t s);
 cudaError_t launch_widen(int n, const float* x, double* out, cudaStream_t s);
 cudaError_t launch_philox_words(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s);

@@ -7,6 +7,7 @@
 #include "iter_kernels.cuh"
 #include "chain_kernel.cuh"
 #include "batch_impl.cuh"
+#include "shard_kernels.cuh"
 
 namespace mppi {
 cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s) {

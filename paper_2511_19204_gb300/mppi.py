@@ -92,7 +92,16 @@ class mppi_result(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class mppi_shard_range(C.Structure):
+    _fields_ = [("s_min", C.c_double), ("s_max", C.c_double), ("best_index", C.c_int64),
+                ("n_finite", C.c_int64)]
+
+    def as_tuple(self):
+        return (self.s_min, self.s_max, self.best_index, self.n_finite)
+
+
 _P = C.c_void_p
+_SRP = C.POINTER(mppi_shard_range)
 # (name, restype, argtypes) of every entry point in include/mppi.h
 SIGNATURES = [
     ("mppi_model_create", C.c_int32, [C.POINTER(mppi_model_desc), C.POINTER(_P)]),
@@ -123,6 +132,11 @@ SIGNATURES = [
     ("mppi_weights", C.c_int32, [C.c_int32, _fp, C.c_double, C.c_int32, _dp, C.POINTER(mppi_result)]),
     ("mppi_average", C.c_int32, [C.c_int32, C.c_int32, _fp, _dp, _dp]),
     ("mppi_average_noalloc", C.c_int32, [C.c_int32, C.c_int32, _P, _P, _P, _P]),
+    ("mppi_shard_range_local", C.c_int32, [C.c_int32, _P, C.c_int64, _SRP, _P]),
+    ("mppi_shard_range_merge", None, [_SRP, _SRP, _SRP]),
+    ("mppi_shard_moments", C.c_int32, [C.c_int32, C.c_int32, _P, _P, _SRP, C.c_double, C.c_int32, _dp, _P]),
+    ("mppi_shard_moments_merge", None, [C.c_int32, _dp, _dp, _dp]),
+    ("mppi_shard_mean", C.c_int32, [C.c_int32, _dp, _fp]),
     ("mppi_forward_dynamics", C.c_int32, [_P, C.c_int32, _dp, _dp, _dp]),
     ("mppi_forward_dynamics_ex", C.c_int32, [_P, C.c_int32, _dp, _dp, _dp, C.c_int32]),
     ("mppi_solve_batch", C.c_int32, [C.POINTER(_P), C.c_int32, C.POINTER(_dp), C.POINTER(_fp),
@@ -455,6 +469,52 @@ def average(knots, w):
     out = np.zeros(E)
     _check(load().mppi_average(K, E, _pf(k.reshape(K, E)), _pd(_d(w)), _pd(out)))
     return out.reshape(k.shape[1:])
+
+
+# ------------------------------------------------------------------------------------
+# Sample shards (one iteration's weights and average over samples split into shards)
+# ------------------------------------------------------------------------------------
+def shard_range(s_min=float("inf"), s_max=float("-inf"), best_index=-1, n_finite=0):
+    """An mppi_shard_range from its four fields (the empty range by default)."""
+    return mppi_shard_range(s_min, s_max, best_index, n_finite)
+
+
+def shard_range_local(d_costs, K, index_base, stream=None):
+    """Round 1 on the device: the range of a shard's K costs (device pointer d_costs)."""
+    r = mppi_shard_range()
+    _check(load().mppi_shard_range_local(K, _P(d_costs), index_base, C.byref(r), _P(stream) if stream else None))
+    return r
+
+
+def shard_range_merge(a, b):
+    """Host merge of two ranges (associative, commutative)."""
+    r = mppi_shard_range()
+    load().mppi_shard_range_merge(C.byref(a), C.byref(b), C.byref(r))
+    return r
+
+
+def shard_moments(d_knots, d_costs, K, E, global_range, lam, normalize=MPPI_NORM_MINMAX, stream=None):
+    """Round 2 on the device: [sum w, sum w theta (E)] of a shard under the merged range."""
+    out = np.zeros(E + 1)
+    _check(load().mppi_shard_moments(K, E, _P(d_knots), _P(d_costs), C.byref(global_range), lam, normalize,
+                                     _pd(out), _P(stream) if stream else None))
+    return out
+
+
+def shard_moments_merge(a, b):
+    """Host merge of two moment vectors of length E + 1."""
+    a, b = _d(a), _d(b)
+    out = np.zeros_like(a)
+    load().mppi_shard_moments_merge(a.shape[0] - 1, _pd(a), _pd(b), _pd(out))
+    return out
+
+
+def shard_mean(sums):
+    """The updated nominal [E] (FP32) from merged moments."""
+    s = _d(sums)
+    out = np.zeros(s.shape[0] - 1, dtype=np.float32)
+    _check(load().mppi_shard_mean(s.shape[0] - 1, _pd(s), _pf(out)))
+    return out
 
 
 def _packed(arrays, sizes, dtype, what):
