@@ -23,7 +23,8 @@ def _case(K=8192, E=144, seed=17):
     costs[rng.random(K) < 0.02] = np.nan
     costs[rng.random(K) < 0.01] = np.inf
     lo = np.float32(np.nanmin(np.where(np.isfinite(costs), costs, np.nan)) - 1.0)
-    costs[4500] = costs[7000] = lo        # the global minimum twice, in different shards
+    i1, i2 = (4500, 7000) if K > 7000 else (K // 3, 2 * K // 3)
+    costs[i1] = costs[i2] = lo            # the global minimum twice, in different shards
     knots = rng.normal(size=(K, E)).astype(np.float32)
     return knots, costs
 
