@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=8192)
-    ap.add_argument("--mapping", type=int, default=-1, help="-1 autotuned, 0 warp, 1 half-warp, 2 thread")
+    ap.add_argument("--mapping", type=int, default=-1, help="-1 autotuned, 0 warp, 1 half-warp, 2 lanes-per-chain")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-samples", type=int, default=1024)
@@ -176,10 +176,9 @@ def sources_sha256(names=TRAFFIC_SOURCES) -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(name: str, samples: int):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch from profiles/<name>.md,
-    scaled to `samples` if the capture used another count; None when the kernel's
-    sources changed since the capture (the summary records their SHA-256)."""
+def profiled_values(name: str):
+    """The `- key: value` lines of profiles/<name>.md, or None when the kernel's sources
+    changed since the capture (the summary records their SHA-256)."""
     path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
         return None
@@ -188,11 +187,26 @@ def profiled_traffic(name: str, samples: int):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source-sha256") != sources_sha256():
-        return None
+    return vals if vals.get("source-sha256") == sources_sha256() else None
+
+
+def profiled_traffic(name: str, samples: int):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from profiles/<name>.md,
+    scaled to `samples` if the capture used another count; None when the kernel's
+    sources changed since the capture."""
+    vals = profiled_values(name)
     try:
         return float(vals["dram-bytes-per-launch"]) * samples / float(vals["samples"])
-    except (KeyError, ValueError):
+    except (TypeError, KeyError, ValueError):
+        return None
+
+
+def profiled_fma_pipe(name: str):
+    """ncu's FP32 (FMA) pipe utilisation of the captured launch, as a fraction, or None."""
+    vals = profiled_values(name)
+    try:
+        return float(vals["fma-pipe-pct"]) / 100.0
+    except (TypeError, KeyError, ValueError):
         return None
 
 
@@ -769,6 +783,8 @@ def run_ours(args, rank, world, local):
                      "frac": achieved / peak,
                      "traffic": (profiled_traffic("rollout_lanes_quadruped", p.n)
                                  if info["mapping"] == mppi.MPPI_MAP_CHAIN else None),
+                     "fp32_pipe_util_ncu": (profiled_fma_pipe("rollout_lanes_quadruped")
+                                            if info["mapping"] == mppi.MPPI_MAP_CHAIN else None),
                      "kernel": "rollout", "launch_ms": roll_ms,
                      "flops_per_step_sample": fl_step,
                      "flops_basis": ("the FP64 oracle's non-trivial operations per step-sample on this workload "

@@ -452,19 +452,21 @@ int batch_variant(const mppi_ctx* c) {
 
 // Estimated duration (us) of one of an instance's tiles: H steps of its variant's step
 // time in the persistent kernel (one 256-thread block per SM), measured on GB300 for the
-// specialised chain variants (quadruped 3.2 us, humanoid split 7.5 us, +10 % with the
-// modular cost) and scaled from the per-instance kernels' ratios for the others. Orders
-// the prefill (longest first) and shares the SMs between groups. Only the ratios matter:
-// later kernels run these steps in 2.6 and 6.8 us, but weights in that ratio gave a
-// slower mixed batch (8.7 against 8.3 ms), so these stay.
+// specialised chain variants (quadruped 3.2 us, +10 % with the modular cost) and scaled
+// from the per-instance kernels' ratios for the others. Orders the prefill (longest
+// first) and shares the SMs between groups, so only the ratios matter. The humanoid
+// split's weight comes from the two groups' kernel times in the 256-instance mix (each
+// alone on its share of the SMs under ncu: the quadruped group 6.58 ms on 73 SMs, the
+// split group 5.17 ms on 79 with a weight of 7.5, i.e. a true ratio of 1.84 to the
+// quadruped's) and a sweep of it (7.5, 6.5, 5.9, 5.3: 7.85, 7.43, 7.22, 7.53 ms per batch).
 static double step_us(const mppi_ctx* c) {
     switch (batch_variant(c)) {
         case BV_XYY: return 3.2;
         case BV_XYY_P: return 3.5;
         case BV_QUAD: return 6.5;
         case BV_QUAD_P: return 7.2;
-        case BV_SPLIT: return 7.5;
-        case BV_SPLIT_P: return 8.2;
+        case BV_SPLIT: return 5.9;
+        case BV_SPLIT_P: return 6.5;
         case BV_HUMG: return 15.0;
         case BV_HUMG_P: return 16.5;
         case BV_HALF: return 0.8 * c->model->nb;
