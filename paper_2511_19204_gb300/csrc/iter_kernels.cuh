@@ -39,8 +39,63 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs
     block_sample_knots(p, blockIdx.x * NOISE_SPB, NOISE_SPB, eps);
 }
 
+// The same knots without the shared-memory stage and its barrier, for joint counts that
+// are multiples of 4 under the Hermite parameterisation (the x, y, y quadruped's 12):
+// thread (n, k, m) draws the two Philox blocks that hold knot k's positions and
+// velocities of joints 4m .. 4m + 3 (each block's 4 words start on a knot's position or
+// velocity half, since 2 k nj and nj are multiples of 4), and writes both halves clamped,
+// 16 bytes each. Same counters, Box-Muller pairs and arithmetic as block_sample_knots,
+// so the knots are identical bit for bit to the batched path's.
+__global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_j4_kernel(SampleArgs a) {
+    const int nj = a.nj, nk = a.nk, E = nk * 2 * nj, G = nj / 4;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)a.N * nk * G) return;
+    const int n = (int)(t / (nk * G));
+    const int r = (int)(t - (long)n * nk * G);
+    const int k = r / G, m = r - k * G;
+    const uint32_t it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
+    const int eq = 2 * k * nj + 4 * m, ev = eq + nj;
+    if (!MPPI_CHECK_OK(ev + 3 < E, CHECK_NOISE)) return;
+    float e_q[4] = {0.f, 0.f, 0.f, 0.f}, e_v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (n > 0) {
+        const U4 wq = philox4x32_10(U4{(uint32_t)(eq / 4), (uint32_t)n, it, a.inst}, a.seed_lo, a.seed_hi);
+        const U4 wv = philox4x32_10(U4{(uint32_t)(ev / 4), (uint32_t)n, it, a.inst}, a.seed_lo, a.seed_hi);
+        box_muller<float>(wq.x, wq.y, &e_q[0], &e_q[1]);
+        box_muller<float>(wq.z, wq.w, &e_q[2], &e_q[3]);
+        box_muller<float>(wv.x, wv.y, &e_v[0], &e_v[1]);
+        box_muller<float>(wv.z, wv.w, &e_v[2], &e_v[3]);
+    }
+    const float sg = a.sigma_row[k];
+    const float sq = __fmul_rn(sg, a.scale_q), sv = __fmul_rn(sg, a.scale_v);
+    float q[4], v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        q[i] = __fmaf_rn(sq, e_q[i], a.nominal[eq + i]);
+        v[i] = __fmaf_rn(sv, e_v[i], a.nominal[ev + i]);
+        if (a.has_limits) {
+            const int j = 4 * m + i;
+            const float lo = a.model->q_min[j + 1], hi = a.model->q_max[j + 1];
+            if (isfinite(lo) || isfinite(hi)) {
+                q[i] = fminf(fmaxf(q[i], lo), hi);
+                const float room = fminf(hi - q[i], q[i] - lo);
+                const float vmax = room / (a.dtk * 0.5f);
+                v[i] = fminf(fmaxf(v[i], -vmax), vmax);
+            }
+        }
+    }
+    float* kn = a.knots + (size_t)n * E;
+    *reinterpret_cast<float4*>(kn + eq) = make_float4(q[0], q[1], q[2], q[3]);
+    *reinterpret_cast<float4*>(kn + ev) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
 cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s) {
     const int E = a.nk * 2 * a.nj;
+    if (a.nj % 4 == 0 && a.spline == MPPI_SPLINE_HERMITE && (reinterpret_cast<uintptr_t>(a.knots) & 15) == 0) {
+        const long threads = (long)a.N * a.nk * (a.nj / 4);
+        if (threads == 0) return cudaSuccess;
+        sample_knots_j4_kernel<<<(int)((threads + SAMPLE_THREADS - 1) / SAMPLE_THREADS), SAMPLE_THREADS, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const int grid = (a.N + NOISE_SPB - 1) / NOISE_SPB;
     if (grid == 0) return cudaSuccess;
     const size_t sm = (size_t)NOISE_SPB * E * sizeof(float);
