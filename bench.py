@@ -522,10 +522,10 @@ def _serving_controllers(mppi, synth, n_ctrl, seed=7):
     return ctrls, states, work, rng
 
 
-def _quantiles(lat):
+def _quantiles(lat, prefix="latency_ms"):
     lat = sorted(lat)
     q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
-    return {"latency_ms_p50": q(0.5), "latency_ms_p99": q(0.99), "latency_ms_p999": q(0.999)}
+    return {f"{prefix}_p50": q(0.5), f"{prefix}_p99": q(0.99), f"{prefix}_p999": q(0.999)}
 
 
 def _plain_under_load(ctrls, states, work, rate_per_ctrl, seconds, warm_s, rng):
@@ -579,8 +579,10 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
     result, and a newer state replaces one still waiting (superseded: a controller acts on
     its latest state). Requests still waiting for admission after the deadline (one 50 Hz
     control period) are shed. Latency = server completion time - arrival time (CLOCK_MONOTONIC)
-    of the served requests arriving in the measurement window; throughput = completions
-    inside it. Beside it, the plain single-instance path (synchronous mppi_solve, first
+    of the served requests arriving in the measurement window (it includes a request's wait
+    behind its controller's previous one and any lateness of this Python generator);
+    submit_to_result = server completion - host submit of the same requests; throughput =
+    completions inside the window. Beside it, the plain single-instance path (synchronous mppi_solve, first
     come first served) under the same arrivals."""
     import heapq
 
@@ -612,7 +614,7 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
         busy = [None] * n_ctrl          # outstanding ticket
         backlog = [None] * n_ctrl       # the latest arrival waiting for the controller's running request
         owner, arrival = {}, {}
-        lat, units, done_in_window, shed_in_window, arrived, superseded = [], 0, 0, 0, 0, 0
+        lat, lat_sub, units, done_in_window, shed_in_window, arrived, superseded = [], [], 0, 0, 0, 0, 0
         t_end = now0 + int((seconds + warm_s) * 1e9)
         t_meas = now0 + int(warm_s * 1e9)
         s0 = srv.stats()
@@ -642,7 +644,7 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
                     backlog[i] = t_arr
             nc = srv.next_completed(timeout_us=200)
             while nc is not None:
-                t, _, t_done = nc
+                t, t_sub, t_done = nc
                 i = owner.pop(t)
                 t_arr = arrival.pop(t)
                 st = srv.poll(t, ctrls[i], timeout_us=0)[0]
@@ -650,6 +652,7 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
                 if st == mppi.MPPI_OK:
                     if t_arr >= t_meas and t_arr < t_end:
                         lat.append((t_done - t_arr) / 1e6)
+                        lat_sub.append((t_done - t_sub) / 1e6)
                     if t_meas <= t_done < t_end:
                         done_in_window += 1
                         units += work[i]
@@ -668,6 +671,7 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
                  "superseded_req_per_s": superseded / seconds,
                  "saturated": done_in_window / seconds < 0.95 * load,
                  "rollout_steps_per_s": units / seconds, **_quantiles(lat),
+                 **_quantiles(lat_sub, "submit_to_result_ms"),
                  "mean_requests_per_launch": completed / max(launches, 1)}
         gc.collect()
         entry["plain_launch"] = _plain_under_load(ctrls, states, work, rate, plain_seconds, plain_warm_s, rng)
