@@ -1,8 +1,8 @@
 // Device side of the sample-shard entry points: one iteration's weights (Sec. III-C,
 // Eq. softmax_minmax) and knot average (Eq. update-nominal) over samples split into
-// shards. Round 1 scans a shard's costs with the weights kernels' own scan; round 2 forms
-// the shard's unnormalised weights under the merged range and their sums. The knot sums
-// reuse the FP64 average kernels of mppi_average.
+// shards. Before the first exchange a shard scans its costs with the weights kernels' own
+// scan; before the second it forms its unnormalised weights under the merged range and
+// their sums. The knot sums reuse the FP64 average kernels of mppi_average.
 #pragma once
 #include "internal.h"
 #include "reduce.cuh"

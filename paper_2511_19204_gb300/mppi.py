@@ -480,7 +480,7 @@ def shard_range(s_min=float("inf"), s_max=float("-inf"), best_index=-1, n_finite
 
 
 def shard_range_local(d_costs, K, index_base, stream=None):
-    """Round 1 on the device: the range of a shard's K costs (device pointer d_costs)."""
+    """First exchange, on the device: the range of a shard's K costs (device pointer d_costs)."""
     r = mppi_shard_range()
     _check(load().mppi_shard_range_local(K, _P(d_costs), index_base, C.byref(r), _P(stream) if stream else None))
     return r
@@ -494,7 +494,7 @@ def shard_range_merge(a, b):
 
 
 def shard_moments(d_knots, d_costs, K, E, global_range, lam, normalize=MPPI_NORM_MINMAX, stream=None):
-    """Round 2 on the device: [sum w, sum w theta (E)] of a shard under the merged range."""
+    """Second exchange, on the device: [sum w, sum w theta (E)] of a shard under the merged range."""
     out = np.zeros(E + 1)
     _check(load().mppi_shard_moments(K, E, _P(d_knots), _P(d_costs), C.byref(global_range), lam, normalize,
                                      _pd(out), _P(stream) if stream else None))
