@@ -309,7 +309,6 @@ def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1,
     stream = torch.cuda.Stream()
     ctrl = mppi.Controller.from_problem(mppi.Model(p.model), p, stream=stream.cuda_stream, mapping=mapping,
                                         spline=spline, block=block)
-    ctrl.profile(True)
     x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
     out = torch.zeros(ctrl.E, dtype=torch.float32, device="cuda")
     w = torch.tensor(p.nominal.reshape(-1), dtype=torch.float32, device="cuda")
@@ -333,7 +332,18 @@ def single_instance(mppi, synth, torch, flops, p, reps=20, warmup=5, mapping=-1,
             e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    # the rollout launches' durations from a profiled copy of the graph (events inside it)
+    ctrl.profile(True)
+    for _ in range(3):
+        ctrl.solve_device(x.data_ptr(), out.data_ptr(), d_warm=w.data_ptr())
+    torch.cuda.synchronize()
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            ctrl.solve_device(x.data_ptr(), out.data_ptr(), d_warm=w.data_ptr())
+        torch.cuda.synchronize()
         roll.extend(float(v) for v in ctrl.rollout_ms())
+    ctrl.profile(False)
     host = []
     for _ in range(reps):
         t0 = time.perf_counter()
@@ -711,7 +721,6 @@ def run_ours(args, rank, world, local):
         except mppi.MppiError:
             tuned = None
     info = ctrl.info()
-    ctrl.profile(True)
     nx, E = p.model.nx, ctrl.E
     x = torch.tensor(p.state, dtype=torch.float64, device="cuda")
     mean = torch.zeros(E, dtype=torch.float32, device="cuda")
@@ -737,10 +746,22 @@ def run_ours(args, rank, world, local):
             ev1.record(stream)
         ev1.synchronize()
         per_solve_ms.append(ev0.elapsed_time(ev1))
-        rollout_ms.extend(float(v) for v in ctrl.rollout_ms())
     torch.cuda.synchronize()
     barrier(dist)
     t_local = sum(per_solve_ms) / 1e3
+    # the rollout launches' own durations: the same solves with CUDA events around each
+    # kernel inside the graph (a separate graph, so the timed solves above carry no events)
+    ctrl.profile(True)
+    for _ in range(3):
+        ctrl.solve_device(x.data_ptr(), mean.data_ptr(), best.data_ptr())
+    torch.cuda.synchronize()
+    for _ in range(max(3, min(args.steps, 20))):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            ctrl.solve_device(x.data_ptr(), mean.data_ptr(), best.data_ptr())
+        torch.cuda.synchronize()
+        rollout_ms.extend(float(v) for v in ctrl.rollout_ms())
+    ctrl.profile(False)
     units = p.n * p.horizon * p.iters
     t_max, units_all = reduce_max_sum(dist, t_local, units * args.steps)
     value = units_all / t_max

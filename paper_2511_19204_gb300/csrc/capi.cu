@@ -409,7 +409,7 @@ size_t ctx_layout(mppi_ctx* c, bool assign) {
 }
 
 cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knots, int N, float* d_costs,
-                            double* d_finals, cudaStream_t s) {
+                            double* d_finals, cudaStream_t s, bool after_noise) {
     RolloutArgs<float> a;
     a.model = (const DevModel<float>*)c->model->d_f;
     a.x0 = d_x0;
@@ -426,8 +426,9 @@ cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knot
         case MPPI_MAP_WARP: return launch_rollout_warp_f32(a, 32, c->block, s);
         case MPPI_MAP_HALFWARP: return launch_rollout_warp_f32(a, 16, c->block, s);
         case MPPI_MAP_CHAIN:
+            // no programmatic launch behind the profiling events (they sit between the kernels)
             return launch_rollout_chain_f32(a, c->model->topology, c->model->host_f.paper_cost != 0,
-                                            c->model->host_f.axis_plan, c->block, s);
+                                            c->model->host_f.axis_plan, c->block, s, after_noise && !c->profile);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -455,7 +456,7 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
     sa.spline = c->spline;
     cudaError_t e = launch_sample_knots(sa, s);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it], s, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s);
+    if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s, true);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it + 1], s, cudaEventRecordExternal);
     if (e == cudaSuccess) {
         FinalizeArgs f;

@@ -71,8 +71,10 @@ namespace mppi {
 void set_error(mppi_ctx* ctx, const std::string& msg);
 mppi_status cuda_fail(mppi_ctx* ctx, cudaError_t e, const char* what);
 size_t ctx_layout(mppi_ctx* c, bool assign);
+// after_noise: the kernel before it in the stream is the solve's knot noise (the rollout
+// may then start as its programmatic dependent)
 cudaError_t enqueue_rollout(mppi_ctx* c, const double* d_x0, const float* d_knots, int N, float* d_costs,
-                            double* d_finals, cudaStream_t s);
+                            double* d_finals, cudaStream_t s, bool after_noise = false);
 cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s);
 cudaError_t enqueue_solve_kernels(mppi_ctx* c, cudaStream_t s);
 mppi_status launch_solve(mppi_ctx* c);

@@ -53,32 +53,46 @@ __global__ void __launch_bounds__(256) rollout_split_kernel(RolloutArgs<float> a
 
 bool chain_mapping_supported(int topology) { return topology == TOPO_QUADRUPED || topology == TOPO_HUMANOID; }
 
+// a plain launch, or with programmatic stream serialisation (see launch_rollout_chain_f32)
+static cudaError_t chain_launch(void (*kernel)(RolloutArgs<float>), int grid, int block, cudaStream_t s, bool pdl,
+                                const RolloutArgs<float>& a) {
+    if (!pdl) {
+        kernel<<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, bool pdl) {
     if (!chain_mapping_supported(topology)) return cudaErrorNotSupported;
     if (block <= 0) block = 128;
     if (block % 32 != 0 || block > 256) return cudaErrorInvalidValue;
     const int spb = block / LANES;
     const int grid = (a.N + spb - 1) / spb;
     if (grid == 0) return cudaSuccess;
+    void (*k)(RolloutArgs<float>);
     if (topology == TOPO_QUADRUPED) {
         const bool xyy = axis_plan == AXP_XYY;
-        if (paper) {
-            if (xyy) rollout_lanes_kernel<3, false, true, AXP_XYY><<<grid, block, 0, s>>>(a);
-            else rollout_lanes_kernel<3, false, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
-        } else {
-            if (xyy) rollout_lanes_kernel<3, false, false, AXP_XYY><<<grid, block, 0, s>>>(a);
-            else rollout_lanes_kernel<3, false, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
-        }
+        if (paper) k = xyy ? rollout_lanes_kernel<3, false, true, AXP_XYY> : rollout_lanes_kernel<3, false, true, AXP_GENERIC>;
+        else k = xyy ? rollout_lanes_kernel<3, false, false, AXP_XYY> : rollout_lanes_kernel<3, false, false, AXP_GENERIC>;
     } else if (axis_plan == AXP_HUM) {
         if (block % 64 != 0) return cudaErrorInvalidValue;
-        if (paper) rollout_split_kernel<true><<<grid, block, 0, s>>>(a);
-        else rollout_split_kernel<false><<<grid, block, 0, s>>>(a);
+        k = paper ? rollout_split_kernel<true> : rollout_split_kernel<false>;
     } else {
-        if (paper) rollout_lanes_kernel<6, true, true, AXP_GENERIC><<<grid, block, 0, s>>>(a);
-        else rollout_lanes_kernel<6, true, false, AXP_GENERIC><<<grid, block, 0, s>>>(a);
+        k = paper ? rollout_lanes_kernel<6, true, true, AXP_GENERIC> : rollout_lanes_kernel<6, true, false, AXP_GENERIC>;
     }
-    return cudaGetLastError();
+    return chain_launch(k, grid, block, s, pdl, a);
 }
 
 }  // namespace mppi

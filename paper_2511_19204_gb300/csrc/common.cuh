@@ -464,6 +464,14 @@ __device__ __forceinline__ void art_solve(const Art<T>& I, const T* b, T* x) {
     }
 }
 
+// Programmatic dependent launch: a kernel launched as the programmatic dependent of the
+// one before it in the stream may start while that one runs; pdl_wait() blocks until it
+// has completed and its memory is visible (it returns at once in a kernel launched
+// without the dependency), and pdl_trigger() in the primary lets the dependent launch
+// as soon as every primary block has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------------------------
 // Bounded TMA bulk copy of a global block into shared memory (cp.async.bulk +
 // mbarrier). Thread 0 issues; every thread waits with an iteration limit. Returns false

@@ -63,8 +63,11 @@ struct RolloutArgs {
 cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s);
 cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s);
 cudaError_t launch_rollout_warp_f64(const RolloutArgs<double>& a, int G, int block, cudaStream_t s);
+// pdl: launched as a programmatic dependent of the kernel before it in the stream (the
+// knot noise of a solve): its prologue overlaps that kernel; it waits for it before the
+// first knot read (griddepcontrol.wait)
 cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, bool paper, int axis_plan, int block,
-                                     cudaStream_t s);
+                                     cudaStream_t s, bool pdl = false);
 bool chain_mapping_supported(int topology);
 // FP64 check build of the lanes-per-chain kernels (128-thread blocks)
 cudaError_t launch_rollout_chain_f64(const RolloutArgs<double>& a, int topology, bool paper, int axis_plan,

@@ -19,6 +19,7 @@ constexpr int SAMPLE_THREADS = 256;
 
 __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs a) {
     extern __shared__ float eps[];  // [NOISE_SPB][E]
+    pdl_trigger();  // the solve's rollout may launch now; it waits for these knots
     NoiseParams p;
     p.nominal = a.nominal;
     p.sigma_row = a.sigma_row;
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs
 // 16 bytes each. Same counters, Box-Muller pairs and arithmetic as block_sample_knots,
 // so the knots are identical bit for bit to the batched path's.
 __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_j4_kernel(SampleArgs a) {
+    pdl_trigger();  // the solve's rollout may launch now; it waits for these knots
     const int nj = a.nj, nk = a.nk, E = nk * 2 * nj, G = nj / 4;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)a.N * nk * G) return;

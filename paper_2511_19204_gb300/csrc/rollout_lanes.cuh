@@ -734,6 +734,7 @@ __device__ __noinline__ R_T lanes_rollout(const DevModel<R_T>& M, int g, const d
     // by integer steps instead of a division per step; s = rem / H
     const R_T inv_H = R_C(1.0) / (R_T)H;
     int k = 0, rem = -(nk - 1);
+    pdl_wait();  // the knots (a solve's noise kernel may still be writing them)
     for (int h = 0; h < H; ++h) {
         rem += nk - 1;
         while (rem >= H) {
