@@ -454,7 +454,9 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
     sa.scale_v = (float)c->scale_v;
     sa.dtk = (float)c->dtk;
     sa.spline = c->spline;
-    cudaError_t e = launch_sample_knots(sa, s);
+    // the kernels of a solve after its first follow each other as programmatic dependents
+    // (not behind the profiling events, which sit between them)
+    cudaError_t e = launch_sample_knots(sa, s, it > 0 && !c->profile);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it], s, cudaEventRecordExternal);
     if (e == cudaSuccess) e = enqueue_rollout(c, c->d_x0, c->d_knots, c->N, c->d_costs, nullptr, s, true);
     if (e == cudaSuccess && c->profile) e = cudaEventRecordWithFlags(c->ev[2 * it + 1], s, cudaEventRecordExternal);
@@ -479,7 +481,7 @@ cudaError_t enqueue_iteration(mppi_ctx* c, int it, cudaStream_t s) {
         f.mean_out = c->d_mean;
         f.best_out = c->d_best;
         f.result = c->d_result;
-        e = launch_weights_finalize(f, c->N, c->lambda, c->normalize, s);
+        e = launch_weights_finalize(f, c->N, c->lambda, c->normalize, s, !c->profile);
     }
     return e;
 }

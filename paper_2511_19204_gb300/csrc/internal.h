@@ -60,7 +60,8 @@ struct RolloutArgs {
 };
 
 // launches (kernels.cu / rollout_*.cu)
-cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s);
+// pdl: a programmatic dependent of the kernel before it (the previous iteration's finalize)
+cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s, bool pdl = false);
 cudaError_t launch_rollout_warp_f32(const RolloutArgs<float>& a, int G, int block, cudaStream_t s);
 cudaError_t launch_rollout_warp_f64(const RolloutArgs<double>& a, int G, int block, cudaStream_t s);
 // pdl: launched as a programmatic dependent of the kernel before it in the stream (the
@@ -109,7 +110,8 @@ struct FinalizeArgs {
 };
 // chunk weights + partial sums, the group totals by the last chunk of each group and the
 // finalize by the last group to finish (one launch per iteration)
-cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda, int normalize, cudaStream_t s);
+cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda, int normalize, cudaStream_t s,
+                                    bool pdl = false);
 cudaError_t prepare_weights_kernels();   // co-residency of the cooperative finish, per device
 cudaError_t launch_solve_begin(DevSolve* solve, uint32_t* gcount, int ngroups, const float* nominal, float* best_out,
                                int E, cudaStream_t s);

@@ -20,6 +20,7 @@ constexpr int SAMPLE_THREADS = 256;
 __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs a) {
     extern __shared__ float eps[];  // [NOISE_SPB][E]
     pdl_trigger();  // the solve's rollout may launch now; it waits for these knots
+    pdl_wait();     // the nominal from the previous iteration's finalize
     NoiseParams p;
     p.nominal = a.nominal;
     p.sigma_row = a.sigma_row;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_kernel(SampleArgs
 // so the knots are identical bit for bit to the batched path's.
 __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_j4_kernel(SampleArgs a) {
     pdl_trigger();  // the solve's rollout may launch now; it waits for these knots
+    pdl_wait();     // the nominal from the previous iteration's finalize
     const int nj = a.nj, nk = a.nk, E = nk * 2 * nj, G = nj / 4;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)a.N * nk * G) return;
@@ -90,19 +92,44 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_j4_kernel(SampleA
     *reinterpret_cast<float4*>(kn + ev) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s) {
+// A launch with N attributes of cfg's stream, grid, block and dynamic shared memory.
+template <typename... P, typename... A>
+static cudaError_t launch_ex(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                             bool cooperative, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    if (cooperative) {
+        attr[n].id = cudaLaunchAttributeCooperative;
+        attr[n].val.cooperative = 1;
+        ++n;
+    }
+    if (pdl) {
+        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s, bool pdl) {
     const int E = a.nk * 2 * a.nj;
     if (a.nj % 4 == 0 && a.spline == MPPI_SPLINE_HERMITE && (reinterpret_cast<uintptr_t>(a.knots) & 15) == 0) {
         const long threads = (long)a.N * a.nk * (a.nj / 4);
         if (threads == 0) return cudaSuccess;
-        sample_knots_j4_kernel<<<(int)((threads + SAMPLE_THREADS - 1) / SAMPLE_THREADS), SAMPLE_THREADS, 0, s>>>(a);
-        return cudaGetLastError();
+        return launch_ex(sample_knots_j4_kernel, (int)((threads + SAMPLE_THREADS - 1) / SAMPLE_THREADS),
+                         SAMPLE_THREADS, 0, s, pdl, false, a);
     }
     const int grid = (a.N + NOISE_SPB - 1) / NOISE_SPB;
     if (grid == 0) return cudaSuccess;
     const size_t sm = (size_t)NOISE_SPB * E * sizeof(float);
-    sample_knots_kernel<<<grid, SAMPLE_THREADS, sm, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(sample_knots_kernel, grid, SAMPLE_THREADS, sm, s, pdl, false, a);
 }
 
 // ------------------------------------------------------------------------------------
@@ -193,12 +220,14 @@ constexpr int WF_THREADS = 1024;
 
 __global__ void __launch_bounds__(WF_THREADS) weights_finalize_kernel(FinalizeArgs f, int N, double lambda,
                                                                        int normalize) {
+    pdl_wait();  // the rollout's costs
     reduce_chunk(f, N, lambda, normalize, blockIdx.x);
 }
 
 // The single-level finish (reduce_chunk_grid) in a cooperative launch, one chunk per block.
 __global__ void __launch_bounds__(WF_THREADS) weights_grid_kernel(FinalizeArgs f, int N, double lambda,
                                                                    int normalize) {
+    pdl_wait();  // the rollout's costs
     reduce_chunk_grid(f, N, lambda, normalize);
 }
 
@@ -219,28 +248,17 @@ cudaError_t prepare_weights_kernels() {
 // One launch per iteration. When all chunks fit on the device at once (and in at most 16
 // groups) the cooperative single-level finish runs, else the two-level one; both give the
 // same bits.
-cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda, int normalize, cudaStream_t s) {
+cudaError_t launch_weights_finalize(const FinalizeArgs& a, int N, double lambda, int normalize, cudaStream_t s,
+                                    bool pdl) {
     const int grid = num_chunks(N);
     if (grid == 0) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const int cap = dev >= 0 && dev < 64 ? g_grid_capacity[dev] : 0;
-    if (grid <= cap && grid <= 16 * AVG_GROUP) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(WF_THREADS);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, weights_grid_kernel, a, N, lambda, normalize);
-    }
-    weights_finalize_kernel<<<grid, WF_THREADS, 0, s>>>(a, N, lambda, normalize);
-    return cudaGetLastError();
+    if (grid <= cap && grid <= 16 * AVG_GROUP)
+        return launch_ex(weights_grid_kernel, grid, WF_THREADS, 0, s, pdl, true, a, N, lambda, normalize);
+    return launch_ex(weights_finalize_kernel, grid, WF_THREADS, 0, s, pdl, false, a, N, lambda, normalize);
 }
 
 // Start of a solve: best tracking reset, the best knots start as the nominal, and the
