@@ -3,6 +3,8 @@
 // softmax_minmax, Eq. update-nominal) and the iteration's finalize (log-sum-exp, mean,
 // best tracking of Sec. III-D).
 #pragma once
+#include <utility>
+
 #include "internal.h"
 #include "noise.cuh"
 #include "reduce.cuh"
@@ -92,7 +94,8 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_j4_kernel(SampleA
     *reinterpret_cast<float4*>(kn + ev) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// A launch with N attributes of cfg's stream, grid, block and dynamic shared memory.
+// One launch through cudaLaunchKernelEx, optionally cooperative and/or as a programmatic
+// dependent of the kernel before it in the stream.
 template <typename... P, typename... A>
 static cudaError_t launch_ex(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
                              bool cooperative, A&&... args) {
