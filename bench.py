@@ -802,7 +802,7 @@ def run_ours(args, rank, world, local):
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "mean": statistics.mean(lat)},
         "e2e": ({"value": e2e_units / e2e_max, "unit": UNIT,
-                 "h2d_bytes_per_step": 8 * nx, "d2h_bytes_per_step": 4 * 2 * E + 48,
+                 "h2d_bytes_per_step": ctrl.io_bytes()[0], "d2h_bytes_per_step": ctrl.io_bytes()[1],
                  "ms_per_step": 1e3 * e2e_local / len(e2e_t)} if e2e_t else None),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,

@@ -516,6 +516,11 @@ mppi_status mppi_ctx_rollout_ms(mppi_ctx* ctx, float* h_ms);
  * [6] mapping, [7] block_size. */
 mppi_status mppi_ctx_info(const mppi_ctx* ctx, int32_t* h_out8);
 
+/* Bytes that one mppi_solve moves between host and device: h_out2[0] host -> device (the
+ * state; a warm start adds knots x 2 x nj x 4), h_out2[1] device -> host (the mean, the
+ * best knots and the result). */
+mppi_status mppi_ctx_io_bytes(const mppi_ctx* ctx, int64_t* h_out2);
+
 /* What the library derived from a model: h_out4 = (topology: 0 generic tree, 1 base + 4
  * chains of <= 3, 2 base + 2 chains + a branch body with 2 chains; axis plan of the
  * lanes-per-chain kernels: 0 any axes, 1 the quadruped layout (every chain turns about +x,

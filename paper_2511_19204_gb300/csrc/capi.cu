@@ -1127,6 +1127,13 @@ mppi_status mppi_ctx_info(const mppi_ctx* c, int32_t* o) {
     return MPPI_OK;
 }
 
+mppi_status mppi_ctx_io_bytes(const mppi_ctx* c, int64_t* o) {
+    if (!c || !o) return MPPI_ERR_INVALID_ARG;
+    o[0] = (int64_t)(sizeof(double) * c->nx);
+    o[1] = (int64_t)(sizeof(float) * 2 * c->E + sizeof(mppi_result));
+    return MPPI_OK;
+}
+
 mppi_status mppi_model_info(const mppi_model* m, int32_t* o) {
     if (!m || !o) return MPPI_ERR_INVALID_ARG;
     o[0] = m->topology;

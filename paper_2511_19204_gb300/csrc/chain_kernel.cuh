@@ -89,6 +89,9 @@ cudaError_t launch_rollout_chain_f32(const RolloutArgs<float>& a, int topology, 
     } else if (axis_plan == AXP_HUM) {
         if (block % 64 != 0) return cudaErrorInvalidValue;
         k = paper ? rollout_split_kernel<true> : rollout_split_kernel<false>;
+        // launched early, the split kernel's 32 whole-SM blocks take the SMs the noise
+        // kernel frees first; the instruction-fetch-bound launch ran 30 us longer that way
+        pdl = false;
     } else {
         k = paper ? rollout_lanes_kernel<6, true, true, AXP_GENERIC> : rollout_lanes_kernel<6, true, false, AXP_GENERIC>;
     }

@@ -176,7 +176,6 @@ __device__ __noinline__ R_T split_legs(const DevModel<R_T>& M, int side, const R
     get_pose(recB, B);  // the first base pose, from the arm warp
     const R_T inv_H = R_C(1.0) / (R_T)H;
     int k = 0, rem = -(nk - 1);
-    pdl_wait();  // the knots (a solve's noise kernel may still be writing them)
     for (int h = 0; h < H; ++h) {
         rem += nk - 1;
         while (rem >= H) {
@@ -340,7 +339,6 @@ __device__ __noinline__ R_T split_arms(const DevModel<R_T>& M, int side, R_T* re
     V3<R_T> aw, av;
     const R_T inv_H = R_C(1.0) / (R_T)H;
     int k = 0, rem = -(nk - 1);
-    pdl_wait();  // the knots (a solve's noise kernel may still be writing them)
     for (int h = 0; h < H; ++h) {
         rem += nk - 1;
         while (rem >= H) {

@@ -156,6 +156,7 @@ SIGNATURES = [
     ("mppi_ctx_profile", C.c_int32, [_P, C.c_int32]),
     ("mppi_ctx_rollout_ms", C.c_int32, [_P, _fp]),
     ("mppi_ctx_info", C.c_int32, [_P, _ip]),
+    ("mppi_ctx_io_bytes", C.c_int32, [_P, _i64p]),
     ("mppi_ctx_device_bytes", C.c_size_t, [_P]),
     ("mppi_ctx_kernels_per_solve", C.c_int32, [_P]),
     ("mppi_status_str", C.c_char_p, [C.c_int32]),
@@ -410,6 +411,12 @@ class Controller:
         ms = np.zeros(self.iters, np.float32)
         _check(load().mppi_ctx_rollout_ms(self.h, _pf(ms)), self.h)
         return ms
+
+    def io_bytes(self):
+        """(host -> device, device -> host) bytes of one solve() without a warm start."""
+        o = np.zeros(2, np.int64)
+        _check(load().mppi_ctx_io_bytes(self.h, o.ctypes.data_as(_i64p)), self.h)
+        return int(o[0]), int(o[1])
 
     def info(self):
         o = np.zeros(8, np.int32)
