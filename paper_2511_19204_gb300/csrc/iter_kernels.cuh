@@ -94,6 +94,43 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_j4_kernel(SampleA
     *reinterpret_cast<float4*>(kn + ev) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// The same knots for any joint count when the model has no joint limits (nothing couples a
+// knot's velocity to its clamped position): thread (n, b) draws Philox block b of sample n
+// and writes its 4 values, each with its own knot's sigma and its own position or velocity
+// scale; again the counters, pairs and arithmetic of block_sample_knots.
+__global__ void __launch_bounds__(SAMPLE_THREADS) sample_knots_flat_kernel(SampleArgs a) {
+    pdl_trigger();  // the solve's rollout may launch now; it waits for these knots
+    pdl_wait();     // the nominal from the previous iteration's finalize
+    const int nj = a.nj, E = a.nk * 2 * nj, B4 = (E + 3) / 4;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)a.N * B4) return;
+    const int n = (int)(t / B4), b = (int)(t - (long)n * B4);
+    const uint32_t it = (a.solve ? a.solve->iter_counter : a.iter_counter_override) + a.iter_offset;
+    float e4[4] = {0.f, 0.f, 0.f, 0.f};
+    if (n > 0) {
+        const U4 w = philox4x32_10(U4{(uint32_t)b, (uint32_t)n, it, a.inst}, a.seed_lo, a.seed_hi);
+        box_muller<float>(w.x, w.y, &e4[0], &e4[1]);
+        box_muller<float>(w.z, w.w, &e4[2], &e4[3]);
+    }
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int e = 4 * b + i;
+        const int ec = e < E ? e : E - 1;
+        const int k = ec / (2 * nj);
+        const bool vel = ec - 2 * nj * k >= nj;
+        v[i] = __fmaf_rn(__fmul_rn(a.sigma_row[k], vel ? a.scale_v : a.scale_q), e4[i], a.nominal[ec]);
+    }
+    float* kn = a.knots + (size_t)n * E;
+    if ((E & 3) == 0) {
+        *reinterpret_cast<float4*>(kn + 4 * b) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * b + i < E) kn[4 * b + i] = v[i];
+    }
+}
+
 // One launch through cudaLaunchKernelEx, optionally cooperative and/or as a programmatic
 // dependent of the kernel before it in the stream.
 template <typename... P, typename... A>
@@ -127,6 +164,12 @@ cudaError_t launch_sample_knots(const SampleArgs& a, cudaStream_t s, bool pdl) {
         const long threads = (long)a.N * a.nk * (a.nj / 4);
         if (threads == 0) return cudaSuccess;
         return launch_ex(sample_knots_j4_kernel, (int)((threads + SAMPLE_THREADS - 1) / SAMPLE_THREADS),
+                         SAMPLE_THREADS, 0, s, pdl, false, a);
+    }
+    if (!a.has_limits && a.spline == MPPI_SPLINE_HERMITE && (reinterpret_cast<uintptr_t>(a.knots) & 15) == 0) {
+        const long threads = (long)a.N * ((E + 3) / 4);
+        if (threads == 0) return cudaSuccess;
+        return launch_ex(sample_knots_flat_kernel, (int)((threads + SAMPLE_THREADS - 1) / SAMPLE_THREADS),
                          SAMPLE_THREADS, 0, s, pdl, false, a);
     }
     const int grid = (a.N + NOISE_SPB - 1) / NOISE_SPB;

@@ -72,9 +72,18 @@ def test_sample_knots_match_oracle(M, orc, name, nk, n):
         assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
 
 
-def test_sample_knots_clamp(M, orc):
-    lo, hi = np.array([-0.3, 0.2, -2.0]), np.array([0.3, 1.5, -0.8])
-    m = S.quadruped(limits=(lo, hi))
+@pytest.mark.parametrize("robot", ["quadruped", "humanoid"])
+def test_sample_knots_clamp(M, orc, robot):
+    # the clamp of Eq. (vel-clamp) on a joint count divisible by 4 (the quadruped's 12: the
+    # barrier-free noise kernel) and on one that is not (the humanoid's 21: the kernel that
+    # stages the normals in shared memory)
+    if robot == "quadruped":
+        lo, hi = np.array([-0.3, 0.2, -2.0]), np.array([0.3, 1.5, -0.8])
+        m = S.quadruped(limits=(lo, hi))
+    else:
+        h = S.humanoid()
+        q0 = h.q_stand
+        m = h.copy(q_min=q0 - 0.25 - 0.1 * np.arange(h.nj) / h.nj, q_max=q0 + 0.3)
     nk, n, H, dt = 5, 200, 100, 0.01
     sig = S.linear_sigma(nk, 1) * 4
     nom = S.nominal_knots(m, nk)
