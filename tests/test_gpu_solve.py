@@ -162,6 +162,29 @@ def test_counter_resident_warm_start_and_replay(M):
     np.testing.assert_array_equal(m2r, m2)
 
 
+@pytest.mark.parametrize("problem", ["scale", "humanoid"])
+def test_programmatic_launches_change_no_bit(M, problem):
+    # In a plain solve every lanes-per-chain rollout, weights kernel and later noise kernel
+    # starts as a programmatic dependent of the kernel before it and waits for it before
+    # reading its output; with profiling on, events sit between the kernels and every
+    # kernel waits for the previous one to finish. Both must give the same bits (3
+    # iterations, so the noise kernels of iterations 2 and 3 are dependents too).
+    p = S.scale_quadruped(n=2048) if problem == "scale" else S.humanoid_problem(n=512)
+    p.iters = 3
+    p.sigma = S.linear_sigma(p.nk, 3)
+    c = M.Controller.from_problem(M.Model(p.model), p, mapping=M.MPPI_MAP_CHAIN)
+    warm = p.nominal.astype(np.float32)
+    out = []
+    for prof in (False, True, False):
+        c.profile(prof)
+        c.iter_counter = 0
+        out.append(c.solve(p.state, warm=warm))
+    for m, b, info in out[1:]:
+        np.testing.assert_array_equal(m, out[0][0])
+        np.testing.assert_array_equal(b, out[0][1])
+        assert info["best_cost"] == out[0][2]["best_cost"]
+
+
 def test_warm_from_mean(M):
     p = S.plain_quadruped()
     c = M.Controller.from_problem(M.Model(p.model), p, mapping=0, warm_from=M.MPPI_WARM_MEAN)
