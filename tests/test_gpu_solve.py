@@ -213,6 +213,15 @@ def test_solve_device_matches_host(M):
     np.testing.assert_array_equal(best.cpu().numpy().reshape(best_h.shape), best_h)
 
 
+def test_io_bytes_are_the_copies_of_a_host_solve(M):
+    import ctypes as C
+    p = S.scale_quadruped(n=64)
+    c = M.Controller.from_problem(M.Model(p.model), p)
+    h2d, d2h = c.io_bytes()
+    assert h2d == 8 * p.model.nx
+    assert d2h == 4 * 2 * c.E + C.sizeof(M.mppi_result)
+
+
 def test_nonfinite_state_rejected(M):
     p = S.plain_quadruped()
     c = M.Controller.from_problem(M.Model(p.model), p, mapping=0)
