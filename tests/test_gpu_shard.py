@@ -102,3 +102,55 @@ def test_shards_on_a_caller_stream(M, orc):
     ranges, g, m = _sharded(M, torch, knots, costs, [0, 1500, 3000], 0.2, 0, stream=s.cuda_stream)
     st, w, info = orc.weights(costs.astype(np.float64), 0.2, 0)
     np.testing.assert_allclose(m[1:] / m[0], orc.average(knots.astype(np.float64), w).reshape(-1), rtol=1e-12, atol=1e-14)
+
+
+def _gpu_rank(rank, world, port, bounds, knots, costs, lam, q):
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import torch.distributed as dist
+    from paper_2511_19204_gb300 import mppi as M
+    from paper_2511_19204_gb300 import shard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    a, b = bounds[rank], bounds[rank + 1]
+    K, E = b - a, knots.shape[1]
+    d_k = torch.tensor(knots[a:b], device="cuda")
+    d_c = torch.tensor(costs[a:b], device="cuda")
+    st, mean, g, best = shard.sharded_update(lambda: M.shard_range_local(d_c.data_ptr(), K, a),
+                                             lambda gr: M.shard_moments(d_k.data_ptr(), d_c.data_ptr(), K, E, gr, lam),
+                                             lambda n: knots[a + n], a, K, E)
+    q.put((rank, st, mean.tobytes(), g.as_tuple(), best.tobytes()))
+    dist.destroy_process_group()
+
+
+def test_sharded_update_through_the_device_on_two_ranks(M, orc):
+    # The whole sharded iteration as two processes would run it on two GPUs: each rank's
+    # range and moments by the device entry points (both ranks on this one GPU; nothing on
+    # the device waits for the other rank), the two exchanges over gloo, against the FP64
+    # oracle's unsharded weights and average.
+    import socket
+    import torch.multiprocessing as mp
+    knots, costs = _case(K=8192, E=144, seed=23)
+    lam = 0.1
+    bounds = [0, 5000, 8192]
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_gpu_rank, args=(r, 2, port, bounds, knots, costs, lam, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=300) for _ in range(2))
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    st, w, info = orc.weights(costs.astype(np.float64), lam, 0)
+    ref = orc.average(knots.astype(np.float64), w).reshape(-1)
+    means = [np.frombuffer(o[2], np.float32) for o in out]
+    for (rank, st, _, g, best), mean in zip(out, means):
+        assert st == 0 and g[2] == info["best"] == 4500
+        np.testing.assert_array_equal(mean, means[0])
+        np.testing.assert_allclose(mean, ref, rtol=2.0 ** -23, atol=1e-30)
+        np.testing.assert_array_equal(np.frombuffer(best, np.float32), knots[info["best"]])
