@@ -637,10 +637,14 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
             owner[t] = i
             arrival[t] = t_arr
 
+        window_open = False
         while True:
             now = time.monotonic_ns()
             if now >= t_end and not owner:
                 break
+            if not window_open and now >= t_meas:
+                srv.reset_timing()       # the worker maxima below are the window's
+                window_open = True
             while heap and heap[0][0] <= now and now < t_end:
                 t_arr, i = heapq.heappop(heap)
                 heapq.heappush(heap, (t_arr + int(rng.exponential(1e9 / rate)), i))
@@ -682,7 +686,11 @@ def serving_extra(mppi, synth, loads=(5000, 15000, 25000), seconds=30.0, warm_s=
                  "saturated": done_in_window / seconds < 0.95 * load,
                  "rollout_steps_per_s": units / seconds, **_quantiles(lat),
                  **_quantiles(lat_sub, "submit_to_result_ms"),
-                 "mean_requests_per_launch": completed / max(launches, 1)}
+                 "mean_requests_per_launch": completed / max(launches, 1),
+                 # the server thread's longest host-side pauses inside the measurement window
+                 "server_max_worker_pass_ms": s1["max_worker_pass_ns"] / 1e6,
+                 "server_max_launch_call_ms": s1["max_launch_ns"] / 1e6,
+                 "server_max_unpack_ms": s1["max_unpack_ns"] / 1e6}
         gc.collect()
         entry["plain_launch"] = _plain_under_load(ctrls, states, work, rate, plain_seconds, plain_warm_s, rng)
         entry["plain_launch"]["window_s"] = plain_seconds

@@ -475,9 +475,14 @@ mppi_status mppi_server_set_deadline(mppi_server* server, int64_t deadline_us);
  * [3] peak device bytes charged to the budget (the slots' reservation plus the admitted
  * contexts' buffers), [4] admissions deferred by the memory budget. */
 mppi_status mppi_server_stats(mppi_server* server, int64_t* h_out5);
-/* The same counters and more: h_out[k] for k < n (n <= 8): [0..4] as above, [5] requests
- * shed by the deadline, [6] bytes reserved for the launch slots, [7] bytes per slot. */
+/* The same counters and more: h_out[k] for k < n (n <= 11): [0..4] as above, [5] requests
+ * shed by the deadline, [6] bytes reserved for the launch slots, [7] bytes per slot, and
+ * the worker thread's longest pass of its loop [8], longest launch call [9] and longest
+ * result unpacking [10] since creation or mppi_server_reset_timing, in ns (host time, where
+ * a request waited when the device was not busy). */
 mppi_status mppi_server_stats_ex(mppi_server* server, int64_t* h_out, int32_t n);
+/* Restart the maxima [8..10] of mppi_server_stats_ex. Errors: INVALID_ARG. */
+mppi_status mppi_server_reset_timing(mppi_server* server);
 
 /* ---------------------------------------------------------------------------------- */
 /* Autotuning and introspection                                                         */

@@ -102,6 +102,9 @@ struct mppi_server {
     size_t inflight_bytes = 0;
     uint64_t next_ticket = 1;
     int64_t n_submitted = 0, n_completed = 0, n_launches = 0, peak_bytes = 0, n_waited = 0, n_shed = 0;
+    // the worker's longest pass of its loop and its longest launch and unpack calls (ns):
+    // where a request's latency went when the device was not the reason
+    int64_t max_pass_ns = 0, max_launch_ns = 0, max_unpack_ns = 0;
     size_t smem = 0;
     int capacity = 1;
 };
@@ -207,7 +210,13 @@ static mppi_status unpack_slot(Slot& s, cudaError_t q, std::vector<mppi_result>&
 static void worker_loop(mppi_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
+    int64_t pass_start = mono_ns();
     while (!S->stop) {
+        {
+            const int64_t now = mono_ns();
+            S->max_pass_ns = std::max(S->max_pass_ns, now - pass_start);
+            pass_start = now;
+        }
         // 1. under the lock: finished slots, shedding, admission decisions
         std::vector<std::pair<Slot*, cudaError_t>> finished;
         for (Slot& s : S->slots) {
@@ -246,12 +255,22 @@ static void worker_loop(mppi_server* S) {
         lk.unlock();
         // 2. without the lock: launches and result unpacking
         std::vector<cudaError_t> launch_err(to_launch.size(), cudaSuccess);
-        for (size_t k = 0; k < to_launch.size(); ++k) launch_err[k] = launch_slot(S, *to_launch[k]);
+        int64_t t_launch = 0, t_unpack = 0;
+        for (size_t k = 0; k < to_launch.size(); ++k) {
+            const int64_t t0 = mono_ns();
+            launch_err[k] = launch_slot(S, *to_launch[k]);
+            t_launch = std::max(t_launch, mono_ns() - t0);
+        }
         std::vector<std::vector<mppi_result>> infos(finished.size());
         std::vector<mppi_status> fin_st(finished.size());
-        for (size_t k = 0; k < finished.size(); ++k)
+        for (size_t k = 0; k < finished.size(); ++k) {
+            const int64_t t0 = mono_ns();
             fin_st[k] = unpack_slot(*finished[k].first, finished[k].second, infos[k]);
+            t_unpack = std::max(t_unpack, mono_ns() - t0);
+        }
         lk.lock();
+        S->max_launch_ns = std::max(S->max_launch_ns, t_launch);
+        S->max_unpack_ns = std::max(S->max_unpack_ns, t_unpack);
         // 3. under the lock: publish
         const int64_t t_done = mono_ns();
         for (size_t k = 0; k < to_launch.size(); ++k) {
@@ -452,12 +471,20 @@ mppi_status mppi_next_completed(mppi_server* S, int64_t timeout_us, uint64_t* ti
 mppi_status mppi_server_stats_ex(mppi_server* S, int64_t* o, int32_t n) {
     if (!S || !o || n < 0) return MPPI_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
-    const int64_t v[8] = {S->n_submitted, S->n_completed, S->n_launches,  S->peak_bytes,
-                          S->n_waited,    S->n_shed,      (int64_t)S->reserved, (int64_t)S->slot_bytes};
-    for (int k = 0; k < n && k < 8; ++k) o[k] = v[k];
+    const int64_t v[11] = {S->n_submitted,   S->n_completed, S->n_launches,       S->peak_bytes,
+                           S->n_waited,      S->n_shed,      (int64_t)S->reserved, (int64_t)S->slot_bytes,
+                           S->max_pass_ns,   S->max_launch_ns, S->max_unpack_ns};
+    for (int k = 0; k < n && k < 11; ++k) o[k] = v[k];
     return MPPI_OK;
 }
 
 mppi_status mppi_server_stats(mppi_server* S, int64_t* o) { return mppi_server_stats_ex(S, o, 5); }
+
+mppi_status mppi_server_reset_timing(mppi_server* S) {
+    if (!S) return MPPI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->max_pass_ns = S->max_launch_ns = S->max_unpack_ns = 0;
+    return MPPI_OK;
+}
 
 }  // extern "C"

@@ -150,6 +150,7 @@ SIGNATURES = [
     ("mppi_server_stats", C.c_int32, [_P, _i64p]),
     ("mppi_server_stats_ex", C.c_int32, [_P, _i64p, C.c_int32]),
     ("mppi_server_set_deadline", C.c_int32, [_P, C.c_int64]),
+    ("mppi_server_reset_timing", C.c_int32, [_P]),
     ("mppi_autotune", C.c_int32, [_P, _ip, _ip, _fp]),
     ("mppi_ctx_set_mapping", C.c_int32, [_P, C.c_int32, C.c_int32]),
     ("mppi_ctx_set_fp64_check", C.c_int32, [_P, C.c_int32]),
@@ -620,10 +621,15 @@ class Server:
         _check(load().mppi_server_set_deadline(self.h, int(deadline_us)))
 
     def stats(self):
-        o = np.zeros(8, np.int64)
-        _check(load().mppi_server_stats_ex(self.h, o.ctypes.data_as(_i64p), 8))
+        o = np.zeros(11, np.int64)
+        _check(load().mppi_server_stats_ex(self.h, o.ctypes.data_as(_i64p), 11))
         return dict(submitted=int(o[0]), completed=int(o[1]), launches=int(o[2]), peak_bytes=int(o[3]),
-                    deferred=int(o[4]), shed=int(o[5]), reserved_bytes=int(o[6]), slot_bytes=int(o[7]))
+                    deferred=int(o[4]), shed=int(o[5]), reserved_bytes=int(o[6]), slot_bytes=int(o[7]),
+                    max_worker_pass_ns=int(o[8]), max_launch_ns=int(o[9]), max_unpack_ns=int(o[10]))
+
+    def reset_timing(self):
+        """Restart the worker-timing maxima reported by stats()."""
+        _check(load().mppi_server_reset_timing(self.h))
 
     def close(self):
         if getattr(self, "h", None):
